@@ -1,0 +1,31 @@
+"""CPU oracle for full-space Gauss-Newton FWI (Malovichko, Orazbayev & Khokhlov).
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, double-precision
+(complex128) restatement of the discretised problem of the paper: the PML
+Helmholtz operator (Sec. 2, eq. helmholtz_preliminary), the observation
+operator (Sec. 2), the reduced Gauss-Newton system (Sec. 3), the KKT system
+(Sec. 4, eq. KKT), the block-triangular preconditioners (Sec. 5, eqs. precond
+and precond_approx) and GMRES on the KKT matrix.  It uses scipy sparse LU for the
+Helmholtz blocks.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import it; the CUDA library shares no code with
+it (the two meet only in :mod:`fwi_inputs`, which describes problems and holds no
+arithmetic of the method).
+
+Modules
+-------
+grid       padded grid, PML stretching functions, model embedding
+helmholtz  sparse operator assembly, sources, receivers
+fwi        forward modelling, data residual, misfit, adjoint gradient
+kkt        scaled KKT matvec / RHS, exact and inexact preconditioners, direct
+           references (real-form sparse KKT, dense normal equations)
+krylov     flexible GMRES in the real inner product, BiCGStab
+mg         geometric multigrid for the shifted operator (the inner block solver)
+newton     one Newton step and the frequency loop
+
+Parity status: every function is pinned by a ``-m "not gpu"`` test against a
+closed form, a library routine, an invariant or brute force, except the
+multigrid V-cycle and the inner BiCGStab: the paper leaves the inner solver
+open (Sec. 5 names only "shifted Laplacian with multigrid"), so those two are
+the build's own design and their parity is "parity unpinned" beyond the
+convergence and linearity properties tested for them.
+"""

@@ -1,0 +1,158 @@
+"""Pins of the oracle's Gauss-Newton / KKT machinery (Sec. 3-5) against brute
+force, finite differences and the invariants the paper states.  CPU only."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.ndimage import gaussian_filter
+
+import fwi_inputs as FI
+from oracle import fwi, kkt, krylov
+
+
+def _micro(include=True, eps=1e-2, seed=0):
+    wl = FI.micro_workload(seed=seed)
+    prob = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    d = fwi.sample(prob, fwi.forward(prob, wl.gamma_true.ravel()))
+    return wl, prob, d, kkt.KKT(prob, wl.gamma_start.ravel(), d, eps, include_Ls_n=include)
+
+
+def test_gradient_matches_central_differences():
+    """Adjoint-state gradient (Sec. 3) against central differences of the misfit
+    along smooth random directions (Gaussian-filtered noise)."""
+    wl = FI.micro_workload(nx=25, nz=15)
+    prob = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    d = fwi.sample(prob, fwi.forward(prob, wl.gamma_true.ravel()))
+    s0 = wl.gamma_start.ravel()
+    phi, g = fwi.gradient(prob, s0, d)
+    assert phi > 0
+    for seed in range(4):
+        rng = np.random.default_rng(seed)
+        dirn = gaussian_filter(rng.standard_normal((wl.grid.nz, wl.grid.nx)), 2.0).ravel()
+        dirn *= 0.01 * np.mean(s0) / np.abs(dirn).max()
+        t = 1.0
+        fp = fwi.misfit(prob, fwi.residual(prob, fwi.forward(prob, s0 + t * dirn), d))
+        fm = fwi.misfit(prob, fwi.residual(prob, fwi.forward(prob, s0 - t * dirn), d))
+        fd = (fp - fm) / (2 * t)
+        an = float(np.dot(g, dirn))
+        assert abs(fd - an) <= 1e-3 * abs(an), (seed, fd, an)
+
+
+def test_taylor_remainder_second_order():
+    wl = FI.micro_workload(nx=25, nz=15)
+    prob = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    d = fwi.sample(prob, fwi.forward(prob, wl.gamma_true.ravel()))
+    s0 = wl.gamma_start.ravel()
+    phi, g = fwi.gradient(prob, s0, d)
+    dirn = gaussian_filter(np.random.default_rng(7).standard_normal((wl.grid.nz, wl.grid.nx)), 2.0).ravel()
+    dirn *= 0.02 * np.mean(s0) / np.abs(dirn).max()
+    rem = []
+    for t in (1.0, 0.5, 0.25):
+        f = fwi.misfit(prob, fwi.residual(prob, fwi.forward(prob, s0 + t * dirn), d))
+        rem.append(abs(f - phi - t * np.dot(g, dirn)))
+    assert 3.0 < rem[0] / rem[1] < 5.0 and 3.0 < rem[1] / rem[2] < 5.0, rem
+
+
+def test_kkt_matrix_symmetric_and_matches_matvec():
+    """eq. KKT is Hermitian (Sec. 4); with a real control its real form is a
+    symmetric matrix, and the matrix-free product equals the assembled one."""
+    _, _, _, K = _micro()
+    M = K.real_form()
+    assert abs(M - M.T).max() <= 1e-14 * abs(M).max()
+    x = np.random.default_rng(3).standard_normal(K.size)
+    np.testing.assert_allclose(K.matvec(x), M @ x, rtol=0, atol=1e-12 * np.abs(M @ x).max())
+
+
+@pytest.mark.parametrize("include", [True, False])
+def test_kkt_solution_equals_normal_equations(include):
+    """Sec. 4, eqs. tmp1-normal_system_discrete3: eliminating du and lambda
+    from the KKT system gives the reduced Gauss-Newton normal equations, so the
+    two model updates coincide; du = A^{-1} P ds and lambda solves row 1."""
+    _, prob, _, K = _micro(include=include)
+    x = K.solve_direct()
+    du, ds, lm = K.unpack(x)
+    Hm, g = K.normal_system()
+    ds_n = np.linalg.solve(Hm, g)
+    assert np.linalg.norm(ds - ds_n) <= 1e-10 * np.linalg.norm(ds_n)
+    for b in range(K.B):
+        np.testing.assert_allclose(K.Aop(b, du[b]), K.P_apply(b, ds), atol=1e-10 * np.abs(du[b]).max())
+    assert K.relres(x) < 1e-12
+
+
+def test_exact_preconditioner_inverts_its_matrix():
+    """P (eq. precond) applied to P^{-1} v returns v, with P assembled as the
+    KKT matrix with its F block removed."""
+    _, _, _, K = _micro()
+    M = K.real_form().tolil()
+    nU = 2 * K.B * K.N
+    Fd = np.repeat(K.Fd.ravel(), 2)
+    for i in np.nonzero(Fd)[0]:
+        M[i, i] = M[i, i] - Fd[i]
+    Pm = M.tocsr()
+    v = np.random.default_rng(5).standard_normal(K.size)
+    z = K.precond(v)
+    assert np.linalg.norm(Pm @ z - v) <= 1e-10 * np.linalg.norm(v)
+    assert nU > 0
+
+
+def test_exact_preconditioner_gmres_iteration_bound():
+    """M P^{-1} = I + diag(F, 0, 0) P^{-1}, so the preconditioned matrix minus
+    the identity has rank <= rank(F) and GMRES with exact P converges in at
+    most rank(F) + 1 iterations (Sec. 5; the U-factor remark of eq.
+    permuted-block-LU).  Micro grid: 2 sources x 3 receivers -> rank(F) = 12."""
+    _, _, _, K = _micro()
+    rankF = 2 * int(np.count_nonzero(K.Fd))
+    x, info = krylov.fgmres(K.matvec, K.rhs(), K.precond, restart=40, tol=1e-12, max_iter=40)
+    assert info["iters"] <= rankF + 1, (info["iters"], rankF)
+    assert info["true_relres"] < 1e-10
+
+
+def test_zero_residual_gives_zero_update():
+    """d = Q S(s_n) and no -L s_n term: r = 0 so b = 0 and ds = 0 exactly."""
+    wl = FI.micro_workload()
+    prob = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    s = wl.gamma_start.ravel()
+    d = fwi.sample(prob, fwi.forward(prob, s))
+    K = kkt.KKT(prob, s, d, 1e-2, include_Ls_n=False)
+    assert np.abs(K.rhs()).max() < 1e-14 * 1e3
+    x, info = krylov.fgmres(K.matvec, K.rhs(), K.precond)
+    assert np.all(K.unpack(x)[1] == 0.0)
+
+
+def test_fgmres_matches_direct_solve_tiny():
+    """The tiny workload (101x51, 4 sources, 5 Hz): GMRES with the exact
+    preconditioner (the paper's GMRes-full) reaches 1e-8 and its model update
+    matches the sparse direct solve of the whole KKT system."""
+    wl = FI.tiny_workload()
+    prob = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    d = fwi.sample(prob, fwi.forward(prob, wl.gamma_true.ravel()))
+    K = kkt.KKT(prob, wl.gamma_start.ravel(), d, 1e-2, include_Ls_n=True)
+    x, info = krylov.fgmres(K.matvec, K.rhs(), K.precond, restart=30, tol=1e-8, max_iter=300)
+    assert info["true_relres"] <= 1e-8
+    xd = K.solve_direct()
+    ds, dsd = K.unpack(x)[1], K.unpack(xd)[1]
+    assert np.linalg.norm(ds - dsd) <= 1e-6 * np.linalg.norm(dsd)
+
+
+def test_fgmres_and_bicgstab_on_small_dense_systems():
+    """The Krylov routines against numpy.linalg.solve (library routine)."""
+    rng = np.random.default_rng(11)
+    n = 60
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.3
+    b = rng.standard_normal(n)
+    x, info = krylov.fgmres(lambda v: A @ v, b, restart=10, tol=1e-12, max_iter=400)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-11)
+    Ac = A + 1j * rng.standard_normal((n, n)) * 0.2
+    bc = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    M = np.diag(1 / np.diag(Ac))
+    xc, hist = krylov.bicgstab(lambda v: Ac @ v, bc, lambda v: M @ v, iters=200, tol=1e-13)
+    np.testing.assert_allclose(xc, np.linalg.solve(Ac, bc), rtol=1e-9, atol=1e-10)
+
+
+def test_newton_step_reduces_misfit():
+    """Sanity (not a pin): one full Gauss-Newton step lowers the misfit."""
+    wl, prob, d, K = _micro(include=False, eps=1e-3)
+    x = K.solve_direct()
+    s1 = K.s_n + K.delta_s(x)
+    phi0 = fwi.misfit(prob, K.r)
+    phi1 = fwi.misfit(prob, fwi.residual(prob, fwi.forward(prob, s1), d))
+    assert phi1 < phi0
