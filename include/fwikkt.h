@@ -1,0 +1,226 @@
+/*
+ * fwikkt.h -- C ABI of the GB300 full-space Gauss-Newton FWI library.
+ *
+ * Method: Malovichko, Orazbayev & Khokhlov, "Iterative PDE-constrained
+ * optimization for seismic full-waveform inversion" (arXiv:2204.06489).
+ * Each Gauss-Newton step solves the KKT system of Sec. 4 (eq. KKT) with a
+ * right-preconditioned flexible GMRES whose preconditioner is the
+ * block-triangular matrix of Sec. 5 (eq. precond; eq. precond_approx with
+ * inexact block solves).  The inexact Helmholtz block solves are BiCGStab
+ * iterations preconditioned by a multigrid cycle of the shifted operator
+ * (the shifted-Laplacian route named at the end of Sec. 5).
+ *
+ * Conventions shared by every call
+ *   - Status: every int-returning call returns FWI_OK (0) or a negative
+ *     FWI_E_* code; fwi_last_error() then describes the failure.  No call
+ *     throws across the ABI.  Calls on one context are not thread-safe.
+ *   - Units: SI; frequencies in Hz (omega = 2 pi f); gamma (squared slowness,
+ *     Sec. 2) in s^2/m^2.  Complex numbers are interleaved (re, im) pairs.
+ *   - Grids: an instance has nx x nz core nodes, npml absorbing nodes on every
+ *     side (padded Nx = nx + 2 npml, Nz = nz + 2 npml), flat index j*Nx + i
+ *     (x fast).  "Core" arrays are [nz][nx] row-major.
+ *   - Blocks: one Helmholtz problem per (instance, frequency, source)
+ *     (Sec. 2, eq. helmholtz_j), ordered instance-major, then frequency, then
+ *     source.  A "field" buffer holds all blocks' padded grids back to back.
+ *   - Scaling: the library solves the exactly rescaled system
+ *     A' = h^2 A, lambda' = lambda / h^2, ds~ = ds / gamma_ref (see
+ *     fwi_kkt_solve); results are returned in physical units.
+ *   - Ownership: the context owns the device memory it allocates (released
+ *     by fwi_destroy).  Host pointers are read or written only during the call.
+ *     Device pointers (arguments documented as "device") must be valid CUDA
+ *     device memory of the context's device, are accessed on the context's
+ *     stream, and must stay valid until that stream has finished the call's work
+ *     (every call below synchronises its stream before returning unless stated).
+ */
+#ifndef FWIKKT_H
+#define FWIKKT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FWI_OK 0
+#define FWI_E_INVAL (-1)   /* bad argument or call order                      */
+#define FWI_E_NOMEM (-2)   /* device allocation failed (before any launch)    */
+#define FWI_E_CUDA (-3)    /* a CUDA runtime call or kernel launch failed     */
+#define FWI_E_NOCONV (-4)  /* iteration cap reached; results and stats valid  */
+#define FWI_E_NUMERIC (-5) /* NaN/Inf detected, or gamma <= 0                 */
+
+/* ---- precision modes ---------------------------------------------------- */
+#define FWI_C128 0        /* complex128 throughout ("plain FP64 GPU form")       */
+#define FWI_C64_REFINE 1  /* complex64 bulk, FP64 dots / coarsest level / refinement */
+
+typedef struct fwi_ctx fwi_ctx;
+
+/* Grid of one instance (Sec. 2).  The absorbing layer has the quadratic
+ * profile sigma(d) = sigma_max (d / (npml h))^2 with
+ * sigma_max = 3 pml_c ln(1/pml_R) / (2 npml h) and X = 1 + i sigma / omega. */
+typedef struct {
+  int nx, nz;     /* core nodes                                    */
+  int npml;       /* absorbing-layer nodes on each of the 4 sides  */
+  double h;       /* grid spacing [m]                              */
+  double pml_c;   /* reference velocity of the layer profile [m/s] */
+  double pml_R;   /* target reflection coefficient (0 < R < 1)     */
+} fwi_grid;
+
+/* Solver options.  fwi_default_opts() fills the defaults given in brackets. */
+typedef struct {
+  int precision;          /* FWI_C64_REFINE | FWI_C128                  [C64_REFINE] */
+  double eps;             /* regulariser weight on the relative model (s/gamma_ref);
+                             the paper's L = eps I equals eps / gamma_ref^2     [1e-3] */
+  int include_Ls_n;       /* keep the -L s_n term of the KKT right-hand side   [1]   */
+  double tol;             /* target ||b - M xi|| / ||b|| of the KKT solve      [1e-6] */
+  int restart;            /* FGMRES restart length (Sec. 6 uses 30)            [30]   */
+  int max_outer;          /* cap on FGMRES iterations over all sweeps          [600]  */
+  double sweep_tol;       /* c64 FGMRES tolerance per refinement sweep         [1e-3] */
+  int max_refine;         /* cap on FP64 refinement sweeps                     [8]    */
+  int inner_iters;        /* BiCGStab iterations per preconditioner block solve [8]  */
+  double inner_tol;       /* > 0: stop a block's inner solve at this relative
+                             residual (exact-preconditioner mode uses 1e-12)   [0]    */
+  int mg_cycle;           /* 1 = V-cycle, 2 = W-cycle                          [2]    */
+  int nu1, nu2;           /* pre / post Jacobi sweeps                          [2, 2] */
+  double omega_jac;       /* Jacobi damping                                    [0.5]  */
+  double shift_beta;      /* shifted operator omega^2 -> (1 + i beta) omega^2  [0.5]  */
+  double sigma_cap;       /* clip sigma/omega of the shifted operator's layer  [1.0]  */
+  int mg_levels;          /* 0 = automatic                                     [0]    */
+  double fwd_tol;         /* forward/adjoint wavefield residual target (FP64)  [1e-10]*/
+  int fwd_iters;          /* BiCGStab iterations per forward refinement sweep  [60]   */
+  int max_fwd_refine;     /* cap on forward refinement sweeps                  [10]   */
+  int use_graph;          /* replay the preconditioner from a CUDA graph       [1]    */
+} fwi_opts;
+
+typedef struct {
+  int outer_iters;        /* FGMRES iterations, all sweeps                      */
+  int refinements;        /* FP64 refinement sweeps                             */
+  int fwd_sweeps;         /* forward-solve refinement sweeps                    */
+  long long inner_iters;  /* BiCGStab iterations x blocks                       */
+  double rel_res;         /* final ||b - M xi|| / ||b|| recomputed in FP64 (max over instances) */
+  double misfit;          /* data misfit 1/2 sum |W r|^2 at the step's model (sum over instances) */
+  double t_setup_ms, t_forward_ms, t_solve_ms;
+} fwi_stats;
+
+/* Layout of the context's buffers (element counts). */
+typedef struct {
+  int n_instances;
+  int n_blocks;               /* all instances                                     */
+  long long field_elems;      /* complex elements of one field buffer (all blocks) */
+  long long ctrl_elems;       /* real elements of the control (all instances' cores) */
+  long long kkt_elems;        /* real elements of a packed KKT vector =
+                                 4*field_elems + ctrl_elems, order [du | lambda | ds] */
+} fwi_layout_info;
+
+/* Fill *o with the defaults listed in fwi_opts. */
+void fwi_default_opts(fwi_opts *o);
+
+/* Create a context with n_instances independent problems on the current CUDA
+ * device.  grids: host array [n_instances].  cuda_stream: a cudaStream_t (NULL =
+ * legacy default stream) on which all work is queued.  *out receives the
+ * context (NULL on failure).  Returns FWI_E_INVAL for bad grid values. */
+int fwi_create(fwi_ctx **out, int n_instances, const fwi_grid *grids, void *cuda_stream);
+
+/* Sources and receivers of one instance (Sec. 2: point sources f_k, receivers
+ * x_kj, observation operator Q by sampling at nodes).  All arrays are host:
+ * freq_hz[n_freq]; src_ix, src_iz [n_src] core indices; src_amp [2*n_src]
+ * complex amplitudes; rec_offsets [n_src+1] CSR offsets into rec_ix, rec_iz,
+ * rec_weight (diagonal W; NULL = all 1).  Must be called once per instance
+ * before fwi_set_model.  FWI_E_INVAL for indices outside the core. */
+int fwi_set_survey(fwi_ctx *ctx, int inst, int n_freq, const double *freq_hz, int n_src,
+                   const int *src_ix, const int *src_iz, const double *src_amp,
+                   const int *rec_offsets, const int *rec_ix, const int *rec_iz,
+                   const double *rec_weight);
+
+/* Model gamma = 1/c^2 of one instance on the core, [nz][nx] FP64, host
+ * (on_device = 0) or device (on_device = 1).  The first call also freezes the
+ * absorbing layer's gamma (edge replication of this model) and, for
+ * gamma_ref <= 0, sets gamma_ref = mean(gamma_core); later calls replace the
+ * core only.  FWI_E_NUMERIC for gamma <= 0 or non-finite values. */
+int fwi_set_model(fwi_ctx *ctx, int inst, const double *gamma_core, double gamma_ref,
+                  int on_device);
+
+/* Copy the current core model of one instance to gamma_core [nz][nx] (host). */
+int fwi_get_model(fwi_ctx *ctx, int inst, double *gamma_core);
+
+/* Observed data d of one instance: [n_freq][rec_total] complex (2 doubles per
+ * entry), host or device.  rec_total = rec_offsets[n_src]. */
+int fwi_set_observed(fwi_ctx *ctx, int inst, const double *d, int on_device);
+
+/* Forward modelling of every block at the current models (Sec. 2, Au = f):
+ * FP64-refined inner solves until ||f - A u|| / ||f|| <= opts->fwd_tol.
+ * d_pred (host, nullable): predicted data Q u, all instances back to back,
+ * [inst][n_freq][rec_total] complex.  misfit (host, nullable) [n_instances]:
+ * 1/2 sum |W (d - Q u)|^2 (needs observed data).  The wavefields stay in the
+ * context for fwi_kkt_solve / fwi_gradient. */
+int fwi_forward(fwi_ctx *ctx, const fwi_opts *opts, double *d_pred, double *misfit,
+                fwi_stats *stats);
+
+/* Copy the forward wavefield of all blocks (field layout, complex128) into u
+ * (device, 2*field_elems doubles).  Requires fwi_forward. */
+int fwi_get_wavefields(fwi_ctx *ctx, double *u_device);
+
+/* Misfit and its gradient with respect to the core gamma (Sec. 3: the
+ * adjoint-state form of the gradient, -sum_b omega_b^2 Re(conj(u_b) lambda_b)
+ * with A^H lambda_b = Q^T W^T W r_b).  Runs the forward solve first.
+ * misfit (host) [n_instances]; grad (host or device) all instances' cores back
+ * to back, FP64. */
+int fwi_gradient(fwi_ctx *ctx, const fwi_opts *opts, double *misfit, double *grad,
+                 int on_device, fwi_stats *stats);
+
+/* One KKT solve (Sec. 4, eq. KKT; Sec. 5 preconditioner) at the current models
+ * for all instances jointly, using the wavefields of the last fwi_forward.
+ * ds (host or device, FP64): the model update of all instances' cores back to
+ * back, s^2/m^2.  Stops when every instance's FP64 relative residual of the
+ * rescaled system is <= opts->tol (FWI_E_NOCONV with ds and stats filled if
+ * max_outer / max_refine are reached first). */
+int fwi_kkt_solve(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device,
+                  fwi_stats *stats);
+
+/* One Gauss-Newton step (Sec. 3-5): set-up, forward modelling, KKT solve, and
+ * the full step s <- s + ds (no line search).  ds as in fwi_kkt_solve
+ * (nullable). */
+int fwi_newton_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device,
+                    fwi_stats *stats);
+
+/* ---- operator-level entry points (device buffers, for checks and tools) ----
+ * x, y: device field buffers in the given precision (float2 or double2
+ * elements, field layout).  The operators use the current models and, where
+ * stated, the last forward wavefields. */
+
+/* y = A'_b x_b (adjoint = 0) or A'_b^H x_b (adjoint = 1) for every block: the
+ * h^2-scaled 5-point PML Helmholtz operator (Sec. 2, eq.
+ * helmholtz_preliminary).  precision: FWI_C128 (double2) or FWI_C64_REFINE
+ * (float2). */
+int fwi_apply_helmholtz(fwi_ctx *ctx, const void *x, void *y, int adjoint, int precision);
+
+/* y = M xi, the rescaled KKT matrix (Sec. 4, eq. KKT) on packed real vectors
+ * of kkt_elems elements (double or float).  Needs fwi_forward. */
+int fwi_apply_kkt(fwi_ctx *ctx, const fwi_opts *opts, const void *xi, void *y, int precision);
+
+/* z = P~^{-1} v, the block-triangular preconditioner (Sec. 5, eq.
+ * precond_approx) with the inexact block solves of opts, packed vectors. */
+int fwi_apply_precond(fwi_ctx *ctx, const fwi_opts *opts, const void *v, void *z,
+                      int precision);
+
+/* x = inexact solve A'_b x_b = b_b (adjoint: A'^H) for every block: BiCGStab
+ * with multigrid preconditioning, opts->inner_iters iterations (or to
+ * opts->inner_tol).  Field buffers. */
+int fwi_inner_solve(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int adjoint,
+                    int precision);
+
+/* x = one multigrid cycle for the shifted operator from x = 0 (field buffers). */
+int fwi_mg_cycle(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int precision);
+
+/* Sizes of the context's buffers. */
+int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info);
+
+/* Message of the last failure on this context ("" if none). NULL ctx: the
+ * message of the last failed fwi_create. */
+const char *fwi_last_error(const fwi_ctx *ctx);
+
+/* Release the context and all device memory it owns. NULL is ignored. */
+void fwi_destroy(fwi_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FWIKKT_H */

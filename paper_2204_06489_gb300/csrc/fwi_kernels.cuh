@@ -1,0 +1,1064 @@
+// fwi_kernels.cuh -- CUDA kernels of the full-space Gauss-Newton FWI path.
+//
+// Every kernel here is HBM-bound (5-point stencils, transfers, coupling
+// reductions, Krylov vector updates): nothing is a dense contraction, so no
+// tensor cores.  Field kernels run on row tiles (fwi_common.cuh): one warp per
+// grid row, lanes stride along x, so loads of a row are coalesced and the
+// x-neighbours and the rows above/below come from L1/L2.
+#pragma once
+#include "fwi_common.cuh"
+
+namespace fwi {
+
+// ---------------------------------------------------------------------------
+// stencil coefficients
+// ---------------------------------------------------------------------------
+// Operator of Sec. 2 (eq. helmholtz_preliminary), h_l^2-scaled, at node (j, i):
+//   ce = -Z_j / X_{i+1/2}, cw = -Z_j / X_{i-1/2}, cs = -X_i / Z_{j+1/2},
+//   cn = -X_i / Z_{j-1/2}, cc = -(ce + cw + cs + cn) - (1 + i beta)(omega h)^2 gamma X_i Z_j.
+// The stretch arrays hold X, 1/X_{i-1/2} (i = 0..nx), Z, 1/Z_{j-1/2}.
+// cj = true conjugates every coefficient (A^H = conj(A) since A^T = A).
+template <typename T>
+struct Stencil {
+  typedef typename cplx<T>::t T2;
+  T2 cc, ce, cw, cs, cn;
+  __device__ __forceinline__ void load(const OpDev &op, const T2 *__restrict__ st,
+                                       const T *__restrict__ gam, int j, int i, bool cj) {
+    const T2 *X = st + op.st;
+    const T2 *iXh = X + op.nx;
+    const T2 *Z = iXh + op.nx + 1;
+    const T2 *iZh = Z + op.nz;
+    T2 Xi = X[i], Zj = Z[j];
+    ce = cneg(cmul(Zj, iXh[i + 1]));
+    cw = cneg(cmul(Zj, iXh[i]));
+    cs = cneg(cmul(Xi, iZh[j + 1]));
+    cn = cneg(cmul(Xi, iZh[j]));
+    T g = gam[op.gam + (long long)j * op.nx + i];
+    T2 m = cscale(cmul(mk<T2>(op.mass_re, op.mass_im), cmul(Xi, Zj)), g);
+    cc = csub(cneg(cadd(cadd(ce, cw), cadd(cs, cn))), m);
+    if (cj) { cc = cconj(cc); ce = cconj(ce); cw = cconj(cw); cs = cconj(cs); cn = cconj(cn); }
+  }
+  // (Op x) at (j, i); x points at the block's grid; zero outside the grid.
+  __device__ __forceinline__ T2 apply(const T2 *__restrict__ x, int nx, int nz, int j, int i) const {
+    long long k = (long long)j * nx + i;
+    T2 r = cmul(cc, x[k]);
+    if (i + 1 < nx) r = cadd(r, cmul(ce, x[k + 1]));
+    if (i > 0) r = cadd(r, cmul(cw, x[k - 1]));
+    if (j + 1 < nz) r = cadd(r, cmul(cs, x[k + nx]));
+    if (j > 0) r = cadd(r, cmul(cn, x[k - nx]));
+    return r;
+  }
+};
+
+enum FieldMode { FM_APPLY = 0, FM_RESID = 1, FM_JACOBI = 2, FM_JACOBI0 = 3 };
+
+// y = Op x | b - Op x | x + w (b - Op x)/cc | w b / cc  on every block of a level.
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_field_op(LevelView<T> L, int mode, int cj, T w, const typename cplx<T>::t *__restrict__ x,
+           const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
+  typedef typename cplx<T>::t T2;
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlkDev bk = L.blks[t.blk];
+  const OpDev op = L.ops[bk.op];
+  const int j = t.row0 + (threadIdx.x >> 5);
+  if (j >= op.nz) return;
+  const T2 *xb = x ? x + bk.off : nullptr;
+  const T2 *bb = b ? b + bk.off : nullptr;
+  T2 *yb = y + bk.off;
+  for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
+    Stencil<T> s;
+    s.load(op, L.st, L.gam, j, i, cj != 0);
+    long long k = (long long)j * op.nx + i;
+    T2 out;
+    if (mode == FM_JACOBI0) {
+      out = cscale(cdiv(bb[k], s.cc), w);
+    } else {
+      T2 ax = s.apply(xb, op.nx, op.nz, j, i);
+      if (mode == FM_APPLY) out = ax;
+      else if (mode == FM_RESID) out = csub(bb[k], ax);
+      else out = cadd(xb[k], cscale(cdiv(csub(bb[k], ax), s.cc), w));
+    }
+    yb[k] = out;
+  }
+}
+
+// Fused residual + restriction (R = P^T, i.e. 4x full weighting):
+//   bc[J][I] = sum_{a,b in -1..1} w_a w_b (bf - Op xf)[2J+1+b][2I+1+a],  w = (1/2, 1, 1/2).
+// One warp per coarse row.  Lf: fine level, Lc: coarse level (same block order).
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_resid_restrict(LevelView<T> Lf, LevelView<T> Lc, int cj, const typename cplx<T>::t *__restrict__ xf,
+                 const typename cplx<T>::t *__restrict__ bf, typename cplx<T>::t *__restrict__ bc) {
+  typedef typename cplx<T>::t T2;
+  const TileDev t = Lc.tiles[blockIdx.x];
+  const BlkDev bkc = Lc.blks[t.blk];
+  const OpDev opc = Lc.ops[bkc.op];
+  const BlkDev bkf = Lf.blks[t.blk];
+  const OpDev opf = Lf.ops[bkf.op];
+  const int J = t.row0 + (threadIdx.x >> 5);
+  if (J >= opc.nz) return;
+  const T2 *xb = xf + bkf.off;
+  const T2 *bb = bf + bkf.off;
+  for (int I = threadIdx.x & 31; I < opc.nx; I += 32) {
+    T2 acc = mk<T2>(0, 0);
+    for (int db = -1; db <= 1; ++db) {
+      int j = 2 * J + 1 + db;
+      if (j < 0 || j >= opf.nz) continue;
+      T wz = db == 0 ? T(1) : T(0.5);
+      for (int da = -1; da <= 1; ++da) {
+        int i = 2 * I + 1 + da;
+        if (i < 0 || i >= opf.nx) continue;
+        T wx = da == 0 ? T(1) : T(0.5);
+        Stencil<T> s;
+        s.load(opf, Lf.st, Lf.gam, j, i, cj != 0);
+        T2 r = csub(bb[(long long)j * opf.nx + i], s.apply(xb, opf.nx, opf.nz, j, i));
+        acc = cadd(acc, cscale(r, wz * wx));
+      }
+    }
+    bc[bkc.off + (long long)J * opc.nx + I] = acc;
+  }
+}
+
+// x_f += P x_c (bilinear; fine i odd -> coarse (i-1)/2, i even -> mean of coarse i/2-1, i/2).
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_prolong_add(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__restrict__ xc,
+              typename cplx<T>::t *__restrict__ xf) {
+  typedef typename cplx<T>::t T2;
+  const TileDev t = Lf.tiles[blockIdx.x];
+  const BlkDev bkf = Lf.blks[t.blk];
+  const OpDev opf = Lf.ops[bkf.op];
+  const BlkDev bkc = Lc.blks[t.blk];
+  const OpDev opc = Lc.ops[bkc.op];
+  const int j = t.row0 + (threadIdx.x >> 5);
+  if (j >= opf.nz) return;
+  const T2 *cb = xc + bkc.off;
+  int J0, J1; T wz0, wz1;
+  if (j & 1) { J0 = (j - 1) >> 1; J1 = -1; wz0 = 1; wz1 = 0; }
+  else { J0 = (j >> 1) - 1; J1 = j >> 1; wz0 = 0.5; wz1 = 0.5; }
+  for (int i = threadIdx.x & 31; i < opf.nx; i += 32) {
+    int I0, I1; T wx0, wx1;
+    if (i & 1) { I0 = (i - 1) >> 1; I1 = -1; wx0 = 1; wx1 = 0; }
+    else { I0 = (i >> 1) - 1; I1 = i >> 1; wx0 = 0.5; wx1 = 0.5; }
+    T2 acc = mk<T2>(0, 0);
+    int Js[2] = {J0, J1}; T wzs[2] = {wz0, wz1};
+    int Is[2] = {I0, I1}; T wxs[2] = {wx0, wx1};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int J = Js[q];
+      if (J < 0 || J >= opc.nz) continue;
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        int I = Is[p];
+        if (I < 0 || I >= opc.nx) continue;
+        acc = cadd(acc, cscale(cb[(long long)J * opc.nx + I], wzs[q] * wxs[p]));
+      }
+    }
+    long long k = bkf.off + (long long)j * opf.nx + i;
+    xf[k] = cadd(xf[k], acc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// coarse levels in shared memory: one CTA per block runs the whole cycle of
+// levels ls..nlev-1 (cycle index `cyc`, Jacobi (nu1, nu2), exact FP64
+// coarsest solve with the precomputed inverse), x = cycle(b).
+// ---------------------------------------------------------------------------
+struct CoarseArgs {
+  const BlkDev *blks[MAX_LEVELS];   // block tables per level
+  const OpDev *ops;                 // all operators
+  const double2 *inv;               // coarsest inverses (offset per op in inv_off)
+  const long long *inv_off;         // [n_ops]
+  const int *inst_nlev;             // number of levels of each instance
+  int ls, nu1, nu2, cyc, cj;
+  double w;
+};
+
+template <typename T>
+struct SmemCycle {
+  typedef typename cplx<T>::t T2;
+  const CoarseArgs &a;
+  const T2 *st;
+  const T *gam;
+  T2 *xs[MAX_LEVELS], *bs[MAX_LEVELS], *ts[MAX_LEVELS];
+  OpDev op[MAX_LEVELS];
+  int blk, nlev;
+  __device__ SmemCycle(const CoarseArgs &a_, const T2 *st_, const T *gam_) : a(a_), st(st_), gam(gam_) {}
+
+  __device__ void jacobi(int l, bool from_zero) {
+    const OpDev &o = op[l];
+    int n = o.nx * o.nz;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      int j = k / o.nx, i = k - j * o.nx;
+      Stencil<T> s;
+      s.load(o, st, gam, j, i, a.cj != 0);
+      T2 r = from_zero ? bs[l][k] : csub(bs[l][k], s.apply(xs[l], o.nx, o.nz, j, i));
+      T2 d = cscale(cdiv(r, s.cc), (T)a.w);
+      ts[l][k] = from_zero ? d : cadd(xs[l][k], d);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) xs[l][k] = ts[l][k];
+    __syncthreads();
+  }
+  __device__ void restrict_to(int l) {  // b_{l+1} = P^T (b_l - M_l x_l)
+    const OpDev &o = op[l];
+    int n = o.nx * o.nz;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      int j = k / o.nx, i = k - j * o.nx;
+      Stencil<T> s;
+      s.load(o, st, gam, j, i, a.cj != 0);
+      ts[l][k] = csub(bs[l][k], s.apply(xs[l], o.nx, o.nz, j, i));
+    }
+    __syncthreads();
+    const OpDev &c = op[l + 1];
+    int nc = c.nx * c.nz;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      int J = k / c.nx, I = k - J * c.nx;
+      T2 acc = mk<T2>(0, 0);
+      for (int db = -1; db <= 1; ++db) {
+        int j = 2 * J + 1 + db;
+        if (j < 0 || j >= o.nz) continue;
+        T wz = db == 0 ? T(1) : T(0.5);
+        for (int da = -1; da <= 1; ++da) {
+          int i = 2 * I + 1 + da;
+          if (i < 0 || i >= o.nx) continue;
+          T wx = da == 0 ? T(1) : T(0.5);
+          acc = cadd(acc, cscale(ts[l][j * o.nx + i], wz * wx));
+        }
+      }
+      bs[l + 1][k] = acc;
+    }
+    __syncthreads();
+  }
+  __device__ void prolong_from(int l) {  // x_l += P x_{l+1}
+    const OpDev &o = op[l];
+    const OpDev &c = op[l + 1];
+    int n = o.nx * o.nz;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      int j = k / o.nx, i = k - j * o.nx;
+      T2 acc = mk<T2>(0, 0);
+      for (int q = 0; q < 2; ++q) {
+        int J; T wz;
+        if (j & 1) { if (q) continue; J = (j - 1) >> 1; wz = 1; }
+        else { J = (j >> 1) - 1 + q; wz = 0.5; }
+        if (J < 0 || J >= c.nz) continue;
+        for (int p = 0; p < 2; ++p) {
+          int I; T wx;
+          if (i & 1) { if (p) continue; I = (i - 1) >> 1; wx = 1; }
+          else { I = (i >> 1) - 1 + p; wx = 0.5; }
+          if (I < 0 || I >= c.nx) continue;
+          acc = cadd(acc, cscale(xs[l + 1][J * c.nx + I], wz * wx));
+        }
+      }
+      xs[l][k] = cadd(xs[l][k], acc);
+    }
+    __syncthreads();
+  }
+  __device__ void coarsest(int l) {
+    const OpDev &o = op[l];
+    int n = o.nx * o.nz;
+    const double2 *M = a.inv + a.inv_off[a.blks[l][blk].op];
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int c = 0; c < n; ++c) {
+        double2 m = M[(long long)r * n + c];
+        if (a.cj) m.y = -m.y;
+        double2 v = to_d2(bs[l][c]);
+        acc.x += m.x * v.x - m.y * v.y;
+        acc.y += m.x * v.y + m.y * v.x;
+      }
+      xs[l][r] = mk<T2>(acc.x, acc.y);
+    }
+    __syncthreads();
+  }
+  __device__ void cycle(int l) {
+    if (l == nlev - 1) { coarsest(l); return; }
+    for (int s = 0; s < a.nu1; ++s) jacobi(l, s == 0);
+    if (a.nu1 == 0) {
+      int n = op[l].nx * op[l].nz;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) xs[l][k] = mk<T2>(0, 0);
+      __syncthreads();
+    }
+    int reps = l == 0 ? 1 : a.cyc;
+    for (int r = 0; r < reps; ++r) {
+      restrict_to(l);
+      cycle(l + 1);
+      prolong_from(l);
+    }
+    for (int s = 0; s < a.nu2; ++s) jacobi(l, false);
+  }
+};
+
+template <typename T>
+__global__ void k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restrict__ st,
+                               const T *__restrict__ gam, const typename cplx<T>::t *__restrict__ b,
+                               typename cplx<T>::t *__restrict__ x) {
+  typedef typename cplx<T>::t T2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2 *sm = reinterpret_cast<T2 *>(smem_raw);
+  SmemCycle<T> c(a, st, gam);
+  c.blk = blockIdx.x;
+  c.nlev = a.inst_nlev[a.blks[a.ls][c.blk].inst];
+  size_t off = 0;
+  for (int l = a.ls; l < c.nlev; ++l) {
+    c.op[l] = a.ops[a.blks[l][c.blk].op];
+    int n = c.op[l].nx * c.op[l].nz;
+    c.xs[l] = sm + off; off += n;
+    c.bs[l] = sm + off; off += n;
+    c.ts[l] = sm + off; off += n;
+  }
+  const BlkDev bk = a.blks[a.ls][c.blk];
+  int n = c.op[a.ls].nx * c.op[a.ls].nz;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) c.bs[a.ls][k] = b[bk.off + k];
+  __syncthreads();
+  c.cycle(a.ls);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) x[bk.off + k] = c.xs[a.ls][k];
+}
+
+// ---------------------------------------------------------------------------
+// set-up kernels (per operator)
+// ---------------------------------------------------------------------------
+// Stretch arrays of one axis: X(pos) = 1 + i min(sigma(pos)/omega, cap),
+// sigma(d) = smax (d/L)^2, d = distance outside the core span [lo, hi].
+struct AxisDev {
+  long long dst;      // offset of this op's stretch block (X at dst, 1/Xh at dst+nx, Z, 1/Zh)
+  int nx, nz;         // level sizes
+  double x0, z0, hl;  // first node position and spacing of the level
+  double xlo, xhi, zlo, zhi;  // core span [m]
+  double L, smax, omega, cap; // layer width, sigma_max, omega, cap (<0: none)
+};
+
+__device__ __forceinline__ double2 stretch_at(double pos, double lo, double hi, double L, double smax,
+                                              double omega, double cap) {
+  double d = fmax(fmax(lo - pos, pos - hi), 0.0);
+  double s = L > 0.0 ? smax * (d / L) * (d / L) : 0.0;
+  double r = s / omega;
+  if (cap >= 0.0 && r > cap) r = cap;
+  return make_double2(1.0, r);
+}
+
+__global__ void k_stretch_setup(const AxisDev *ax, int n_ops, double2 *st64, float2 *st32) {
+  const AxisDev a = ax[blockIdx.x];
+  int tot = 2 * a.nx + 2 * a.nz + 2;
+  for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+    double2 v;
+    if (k < a.nx) {
+      v = stretch_at(a.x0 + a.hl * k, a.xlo, a.xhi, a.L, a.smax, a.omega, a.cap);
+    } else if (k < 2 * a.nx + 1) {
+      int i = k - a.nx;
+      v = stretch_at(a.x0 + a.hl * (i - 0.5), a.xlo, a.xhi, a.L, a.smax, a.omega, a.cap);
+      v = cdiv(make_double2(1.0, 0.0), v);
+    } else if (k < 2 * a.nx + 1 + a.nz) {
+      int j = k - (2 * a.nx + 1);
+      v = stretch_at(a.z0 + a.hl * j, a.zlo, a.zhi, a.L, a.smax, a.omega, a.cap);
+    } else {
+      int j = k - (2 * a.nx + 1 + a.nz);
+      v = stretch_at(a.z0 + a.hl * (j - 0.5), a.zlo, a.zhi, a.L, a.smax, a.omega, a.cap);
+      v = cdiv(make_double2(1.0, 0.0), v);
+    }
+    st64[a.dst + k] = v;
+    st32[a.dst + k] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// gamma on the padded grid: the frozen layer values with the core replaced by s.
+__global__ void k_gamma_fill(const double *__restrict__ layer, const double *__restrict__ s_core,
+                             int Nx, int Nz, int npml, int nx, int nz, double *g64, float *g32) {
+  long long n = (long long)Nx * Nz;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    int j = (int)(k / Nx), i = (int)(k - (long long)j * Nx);
+    int cj = j - npml, ci = i - npml;
+    double v = (cj >= 0 && cj < nz && ci >= 0 && ci < nx) ? s_core[(long long)cj * nx + ci] : layer[k];
+    g64[k] = v;
+    g32[k] = (float)v;
+  }
+}
+
+// Edge replication of the core model into the padded grid (the frozen layer).
+__global__ void k_gamma_pad(const double *__restrict__ s_core, int Nx, int Nz, int npml, int nx, int nz,
+                            double *out) {
+  long long n = (long long)Nx * Nz;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    int j = (int)(k / Nx), i = (int)(k - (long long)j * Nx);
+    int cj = min(max(j - npml, 0), nz - 1), ci = min(max(i - npml, 0), nx - 1);
+    out[k] = s_core[(long long)cj * nx + ci];
+  }
+}
+
+// Normalised full weighting of gamma from a fine level to the next one.
+__global__ void k_gamma_restrict(const double *__restrict__ gf, int nxf, int nzf, int nxc, int nzc,
+                                 double *gc64, float *gc32) {
+  int n = nxc * nzc;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    int J = k / nxc, I = k - J * nxc;
+    double acc = 0.0, ws = 0.0;
+    for (int db = -1; db <= 1; ++db) {
+      int j = 2 * J + 1 + db;
+      if (j < 0 || j >= nzf) continue;
+      double wz = db == 0 ? 2.0 : 1.0;
+      for (int da = -1; da <= 1; ++da) {
+        int i = 2 * I + 1 + da;
+        if (i < 0 || i >= nxf) continue;
+        double w = wz * (da == 0 ? 2.0 : 1.0);
+        acc += w * gf[(long long)j * nxf + i];
+        ws += w;
+      }
+    }
+    gc64[k] = acc / ws;
+    gc32[k] = (float)(acc / ws);
+  }
+}
+
+// Dense coarsest operator [M | I] (row-major n x 2n, complex128) of one op.
+__global__ void k_coarse_assemble(const OpDev *ops, const int *op_ids, const long long *aug_off,
+                                  const double2 *st64, const double *gam64, double2 *aug) {
+  const OpDev o = ops[op_ids[blockIdx.x]];
+  int n = o.nx * o.nz;
+  double2 *A = aug + aug_off[blockIdx.x];
+  for (long long k = threadIdx.x; k < (long long)n * 2 * n; k += blockDim.x) A[k] = make_double2(0, 0);
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    int j = r / o.nx, i = r - j * o.nx;
+    Stencil<double> s;
+    s.load(o, st64, gam64, j, i, false);
+    double2 *row = A + (long long)r * 2 * n;
+    row[r] = s.cc;
+    if (i + 1 < o.nx) row[r + 1] = s.ce;
+    if (i > 0) row[r - 1] = s.cw;
+    if (j + 1 < o.nz) row[r + o.nx] = s.cs;
+    if (j > 0) row[r - o.nx] = s.cn;
+    row[n + r] = make_double2(1.0, 0.0);
+  }
+}
+
+// In-place Gauss-Jordan with partial pivoting on [M | I] -> [I | M^{-1}];
+// writes the inverse (n x n) to inv.  One CTA per matrix.  Sets *status = 1
+// if a pivot vanishes.
+__global__ void k_gauss_jordan(const int *dims, const long long *aug_off, const long long *inv_off,
+                               double2 *aug, double2 *inv, int *status) {
+  int n = dims[blockIdx.x];
+  double2 *A = aug + aug_off[blockIdx.x];
+  const int w = 2 * n;
+  __shared__ int piv;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = -1.0;
+      for (int r = k; r < n; ++r) {
+        double2 v = A[(long long)r * w + k];
+        double m = v.x * v.x + v.y * v.y;
+        if (m > best) { best = m; p = r; }
+      }
+      piv = p;
+      if (!(best > 0.0)) *status = 1;
+    }
+    __syncthreads();
+    int p = piv;
+    if (p != k) {
+      for (int c = threadIdx.x; c < w; c += blockDim.x) {
+        double2 t = A[(long long)k * w + c];
+        A[(long long)k * w + c] = A[(long long)p * w + c];
+        A[(long long)p * w + c] = t;
+      }
+    }
+    __syncthreads();
+    double2 d = A[(long long)k * w + k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < w; c += blockDim.x)
+      A[(long long)k * w + c] = cdiv(A[(long long)k * w + c], d);
+    __syncthreads();
+    for (long long q = threadIdx.x; q < (long long)n * w; q += blockDim.x) {
+      int r = (int)(q / w), c = (int)(q - (long long)r * w);
+      if (r == k || c == k) continue;
+      double2 f = A[(long long)r * w + k];
+      A[q] = csub(A[q], cmul(f, A[(long long)k * w + c]));
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+      if (r != k) A[(long long)r * w + k] = make_double2(0, 0);
+    __syncthreads();
+  }
+  double2 *out = inv + inv_off[blockIdx.x];
+  for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) {
+    int r = (int)(q / n), c = (int)(q - (long long)r * n);
+    out[q] = A[(long long)r * w + n + c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-block reductions and BiCGStab vector updates
+// ---------------------------------------------------------------------------
+// partial[tile][q] = sum over the tile of conj(a_q) b_q (q < nd), accumulated
+// in FP64; fixed order, no atomics.
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typename cplx<T>::t *b0,
+             const typename cplx<T>::t *a1, const typename cplx<T>::t *b1,
+             const typename cplx<T>::t *a2, const typename cplx<T>::t *b2, double2 *partial) {
+  typedef typename cplx<T>::t T2;
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlkDev bk = L.blks[t.blk];
+  const OpDev op = L.ops[bk.op];
+  const int j = t.row0 + (threadIdx.x >> 5);
+  double2 acc[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+  const T2 *as[3] = {a0, a1, a2};
+  const T2 *bs[3] = {b0, b1, b2};
+  if (j < op.nz) {
+    long long base = bk.off + (long long)j * op.nx;
+    for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q < nd) {
+          double2 a = to_d2(as[q][base + i]), b = to_d2(bs[q][base + i]);
+          acc[q].x += a.x * b.x + a.y * b.y;
+          acc[q].y += a.x * b.y - a.y * b.x;
+        }
+      }
+    }
+  }
+  __shared__ double2 red[3][TILE_THREADS / 32];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    double x = acc[q].x, y = acc[q].y;
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = make_double2(x, y);
+  }
+  __syncthreads();
+  if (threadIdx.x < nd) {
+    double2 s = make_double2(0, 0);
+    for (int wi = 0; wi < TILE_THREADS / 32; ++wi) { s.x += red[threadIdx.x][wi].x; s.y += red[threadIdx.x][wi].y; }
+    partial[(long long)blockIdx.x * 3 + threadIdx.x] = s;
+  }
+}
+
+// Per-block BiCGStab scalars (double2 = complex FP64):
+//   st[b] = {rho, rho_old, alpha, omega, beta, bnorm2(re), rnorm2(re)}, done[b]
+struct BiState {
+  double2 rho, rho_old, alpha, omega, beta;
+  double bnorm2, rnorm2;
+  int done, it;
+};
+
+__device__ __forceinline__ double2 sum_tiles(const double2 *partial, int t0, int t1, int q) {
+  double2 s = make_double2(0, 0);
+  for (int t = t0; t < t1; ++t) { s.x += partial[(long long)t * 3 + q].x; s.y += partial[(long long)t * 3 + q].y; }
+  return s;
+}
+
+// stage 0: init (partials: q0 = <b,b>): rho_old = alpha = omega = 1, done if b == 0.
+// stage 1: rho = <rh, r> (q0); beta = (rho/rho_old)(alpha/omega); done if rho == 0.
+// stage 2: alpha = rho / <rh, v> (q0); done if <rh, v> == 0.
+// stage 3: omega = <t, s>/<t, t> (q0, q1); omega = 0 if <t,t> == 0.
+// stage 4: after the x/r update (q0 = <r, r>): rho_old = rho; done if omega == 0 or
+//          ||r||^2 <= tol^2 ||b||^2 (tol > 0).
+__global__ void k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1, const double2 *partial,
+                               BiState *S, int stage, double tol) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_blocks) return;
+  BiState s = S[b];
+  int t0 = tile0[b], t1 = tile1[b];
+  if (stage == 0) {
+    double2 bb = sum_tiles(partial, t0, t1, 0);
+    s.bnorm2 = bb.x; s.rnorm2 = bb.x;
+    s.rho_old = s.alpha = s.omega = make_double2(1, 0);
+    s.rho = s.beta = make_double2(0, 0);
+    s.done = !(bb.x > 0.0);
+    s.it = 0;
+  } else if (s.done) {
+    s.alpha = s.omega = s.beta = make_double2(0, 0);
+  } else if (stage == 1) {
+    s.rho = sum_tiles(partial, t0, t1, 0);
+    if (s.rho.x == 0.0 && s.rho.y == 0.0) {
+      s.done = 1; s.alpha = s.omega = s.beta = make_double2(0, 0);
+    } else {
+      s.beta = cmul(cdiv(s.rho, s.rho_old), cdiv(s.alpha, s.omega));
+      if (s.it == 0) s.beta = make_double2(0, 0);
+    }
+  } else if (stage == 2) {
+    double2 den = sum_tiles(partial, t0, t1, 0);
+    if (den.x == 0.0 && den.y == 0.0) {
+      s.done = 1; s.alpha = s.omega = s.beta = make_double2(0, 0);
+    } else {
+      s.alpha = cdiv(s.rho, den);
+    }
+  } else if (stage == 3) {
+    double2 ts = sum_tiles(partial, t0, t1, 0);
+    double2 tt = sum_tiles(partial, t0, t1, 1);
+    s.omega = tt.x > 0.0 ? cscale(ts, 1.0 / tt.x) : make_double2(0, 0);
+  } else if (stage == 4) {
+    double2 rr = sum_tiles(partial, t0, t1, 0);
+    s.rnorm2 = rr.x;
+    s.rho_old = s.rho;
+    s.it += 1;
+    if (s.omega.x == 0.0 && s.omega.y == 0.0) s.done = 1;
+    if (tol > 0.0 && rr.x <= tol * tol * s.bnorm2) s.done = 1;
+  }
+  S[b] = s;
+}
+
+// BiCGStab updates on a field (per-block scalars):
+//  op 0: p = r + beta (p - omega v)
+//  op 1: s = r - alpha v
+//  op 2: x += alpha ph + omega sh;  r = s - omega t
+//  op 3: y = a (copy)            op 4: y = 0
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_bicg_update(LevelView<T> L, int opk, const BiState *S, typename cplx<T>::t *y,
+              const typename cplx<T>::t *a, const typename cplx<T>::t *c, const typename cplx<T>::t *d,
+              typename cplx<T>::t *y2, const typename cplx<T>::t *e) {
+  typedef typename cplx<T>::t T2;
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlkDev bk = L.blks[t.blk];
+  const OpDev op = L.ops[bk.op];
+  const int j = t.row0 + (threadIdx.x >> 5);
+  if (j >= op.nz) return;
+  const BiState s = S[t.blk];
+  const T2 al = mk<T2>(s.alpha.x, s.alpha.y), om = mk<T2>(s.omega.x, s.omega.y),
+           be = mk<T2>(s.beta.x, s.beta.y);
+  long long base = bk.off + (long long)j * op.nx;
+  for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
+    long long k = base + i;
+    if (opk == 0) {
+      y[k] = cadd(a[k], cmul(be, csub(y[k], cmul(om, c[k]))));
+    } else if (opk == 1) {
+      y[k] = csub(a[k], cmul(al, c[k]));
+    } else if (opk == 2) {
+      y[k] = cadd(y[k], cadd(cmul(al, a[k]), cmul(om, c[k])));
+      y2[k] = csub(d[k], cmul(om, e[k]));
+    } else if (opk == 3) {
+      y[k] = a[k];
+    } else {
+      y[k] = mk<T2>(0, 0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// KKT operator pieces (level 0 only)
+// ---------------------------------------------------------------------------
+struct InstDev {
+  int npml, nx, nz;        // core size and layer width
+  int blk0, blk1;          // blocks of this instance
+  long long ctrl;          // offset of this instance's core in the control vector
+};
+
+// Per block: coupling factor h^2 gamma_ref omega_b^2 (P~_b = cf_b diag(u_b) E).
+// y_u  = A'^H lm               (F du is added by k_kkt_F)
+// y_lm = A' du - cf_b u_b .* E ds
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_kkt_rows(LevelView<T> L, const InstDev *inst, const double *cf, const typename cplx<T>::t *__restrict__ u,
+           const typename cplx<T>::t *__restrict__ du, const typename cplx<T>::t *__restrict__ lm,
+           const T *__restrict__ ds, typename cplx<T>::t *__restrict__ yu, typename cplx<T>::t *__restrict__ ylm) {
+  typedef typename cplx<T>::t T2;
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlkDev bk = L.blks[t.blk];
+  const OpDev op = L.ops[bk.op];
+  const InstDev in = inst[bk.inst];
+  const int j = t.row0 + (threadIdx.x >> 5);
+  if (j >= op.nz) return;
+  const T c = (T)cf[t.blk];
+  const int cj = j - in.npml;
+  const bool row_core = cj >= 0 && cj < in.nz;
+  for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
+    Stencil<T> s;
+    s.load(op, L.st, L.gam, j, i, false);
+    long long k = bk.off + (long long)j * op.nx + i;
+    T2 a_du = s.apply(du + bk.off, op.nx, op.nz, j, i);
+    s.cc = cconj(s.cc); s.ce = cconj(s.ce); s.cw = cconj(s.cw); s.cs = cconj(s.cs); s.cn = cconj(s.cn);
+    T2 ah_lm = s.apply(lm + bk.off, op.nx, op.nz, j, i);
+    int ci = i - in.npml;
+    if (row_core && ci >= 0 && ci < in.nx) {
+      T v = ds[in.ctrl + (long long)cj * in.nx + ci];
+      a_du = csub(a_du, cscale(u[k], c * v));
+    }
+    yu[k] = ah_lm;
+    ylm[k] = a_du;
+  }
+}
+
+// Receivers (unique nodes per block, summed squared weights): y[k] += w2 x[k].
+template <typename T>
+__global__ void k_kkt_F(int n, const long long *node, const double *w2, const typename cplx<T>::t *x,
+                        typename cplx<T>::t *y) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  long long k = node[q];
+  y[k] = cadd(y[k], cscale(x[k], (T)w2[q]));
+}
+
+// Coupling reduction over the blocks of each instance, at every core node c:
+//   acc_c = sum_b cf_b Re(conj(u_b) lm_b)   (FP64, fixed order)
+// mode 0 (KKT row 2):      out_c = eps * ds_c - acc_c
+// mode 1 (preconditioner): out_c = (v_c + acc_c) / eps
+// mode 2 (gradient):       out_c = -acc_c   (cf_b = omega_b^2 h^2, lm = lambda')
+// Block partitions: threadIdx.y takes blocks b = blk0 + ty, ty + 4, ...; the 4
+// partial sums are combined in a fixed order.
+template <typename T, typename TO>
+__global__ void k_coupling_reduce(const InstDev *inst, int Nx_stride_unused, const long long *blk_off,
+                                  const int *blk_Nx, const double *cf, const typename cplx<T>::t *__restrict__ u,
+                                  const typename cplx<T>::t *__restrict__ lm, const TO *__restrict__ v,
+                                  double eps, int mode, TO *__restrict__ out) {
+  const InstDev in = inst[blockIdx.y];
+  long long nc = (long long)in.nx * in.nz;
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  __shared__ double part[4][128];
+  double acc = 0.0;
+  if (c < nc) {
+    int cz = (int)(c / in.nx), cx = (int)(c - (long long)cz * in.nx);
+    for (int b = in.blk0 + threadIdx.y; b < in.blk1; b += 4) {
+      int Nx = blk_Nx[b];
+      long long k = blk_off[b] + (long long)(cz + in.npml) * Nx + (cx + in.npml);
+      double2 uu = to_d2(u[k]), ll = to_d2(lm[k]);
+      acc += cf[b] * (uu.x * ll.x + uu.y * ll.y);
+    }
+  }
+  part[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < nc) {
+    double s = ((part[0][threadIdx.x] + part[1][threadIdx.x]) + part[2][threadIdx.x]) + part[3][threadIdx.x];
+    long long o = in.ctrl + c;
+    double r;
+    if (mode == 0) r = eps * (double)v[o] - s;
+    else if (mode == 1) r = ((double)v[o] + s) / eps;
+    else r = -s;
+    out[o] = (TO)r;
+  }
+}
+
+// y_lm = v_lm + cf_b u_b .* E zs   (right-hand side of the preconditioner's forward solve)
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_coupling_scatter(LevelView<T> L, const InstDev *inst, const double *cf, const typename cplx<T>::t *__restrict__ u,
+                   const typename cplx<T>::t *__restrict__ v, const T *__restrict__ zs,
+                   typename cplx<T>::t *__restrict__ y) {
+  typedef typename cplx<T>::t T2;
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlkDev bk = L.blks[t.blk];
+  const OpDev op = L.ops[bk.op];
+  const InstDev in = inst[bk.inst];
+  const int j = t.row0 + (threadIdx.x >> 5);
+  if (j >= op.nz) return;
+  const T c = (T)cf[t.blk];
+  const int cj = j - in.npml;
+  const bool row_core = cj >= 0 && cj < in.nz;
+  for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
+    long long k = bk.off + (long long)j * op.nx + i;
+    T2 r = v[k];
+    int ci = i - in.npml;
+    if (row_core && ci >= 0 && ci < in.nx) r = cadd(r, cscale(u[k], c * zs[in.ctrl + (long long)cj * in.nx + ci]));
+    y[k] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// sources and receivers
+// ---------------------------------------------------------------------------
+// field = 0 except amp_b at the source node of each block (A' u = amp e_src).
+__global__ void k_set_sources(int n_blocks, const long long *src_node, const double2 *amp, double2 *f) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n_blocks) f[src_node[b]] = amp[b];
+}
+
+// Receiver list entries (one per survey receiver): node (field index),
+// data index (into d / r arrays), weight w, block.
+// r = d - u[node]  (FP64), and q = u[node] (predicted data).
+__global__ void k_rec_residual(int n, const long long *node, const double2 *u, const double2 *d,
+                               double2 *q, double2 *r, int have_d) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double2 v = u[node[t]];
+  q[t] = v;
+  r[t] = have_d ? csub(d[t], v) : make_double2(0, 0);
+}
+
+// scatter Q^T W^T W r into a zeroed FP64 field; receivers grouped so that one
+// thread owns each unique node (rows of a CSR over unique nodes).
+__global__ void k_rec_scatter(int n_unique, const long long *unode, const int *uoff, const int *uidx,
+                              const double *w, const double2 *r, double2 *f) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_unique) return;
+  double2 acc = make_double2(0, 0);
+  for (int e = uoff[q]; e < uoff[q + 1]; ++e) {
+    int t = uidx[e];
+    acc = cadd(acc, cscale(r[t], w[t] * w[t]));
+  }
+  f[unode[q]] = acc;
+}
+
+// Misfit per instance: out[i] = 1/2 sum_{e in [e0_i, e1_i)} (w_e |r_e|)^2 (one CTA per instance).
+__global__ void k_misfit(const int *e0, const int *e1, const double *w, const double2 *r, double *out) {
+  int i = blockIdx.x;
+  double acc = 0.0;
+  for (int e = e0[i] + threadIdx.x; e < e1[i]; e += blockDim.x) {
+    double2 v = r[e];
+    acc += w[e] * w[e] * (v.x * v.x + v.y * v.y);
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) s += red[q];
+    out[i] = 0.5 * s;
+  }
+}
+
+// Control part of the KKT right-hand side: b_s = -eps s / gamma_ref (or 0), per instance.
+__global__ void k_ctrl_rhs(const InstDev *inst, const double *const *s_core, const double *gref, double eps,
+                           int include, double *out) {
+  const InstDev in = inst[blockIdx.y];
+  long long nc = (long long)in.nx * in.nz;
+  const double *sc = s_core[blockIdx.y];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x)
+    out[in.ctrl + c] = include ? -eps * sc[c] / gref[blockIdx.y] : 0.0;
+}
+
+// s += ds for every instance's core (full Gauss-Newton step, no line search).
+__global__ void k_update_model(const InstDev *inst, double *const *s_core, const double *ds) {
+  const InstDev in = inst[blockIdx.y];
+  long long nc = (long long)in.nx * in.nz;
+  double *sc = s_core[blockIdx.y];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x)
+    sc[c] += ds[in.ctrl + c];
+}
+
+// ---------------------------------------------------------------------------
+// packed / flat vector kernels (FGMRES, refinement)
+// ---------------------------------------------------------------------------
+#define FLAT_BLOCKS 608      /* 4 x 152 SMs */
+#define FLAT_THREADS 256
+#define MD_CHUNK 8
+
+// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv (FP64 accumulation, fixed grid).
+template <typename T>
+__global__ void __launch_bounds__(FLAT_THREADS)
+k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, double *partial) {
+  double acc[MD_CHUNK];
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v) acc[v] = 0.0;
+  const T *vp[MD_CHUNK];
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v) vp[v] = v < nv ? V[v] : nullptr;
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
+    double wi = (double)w[i];
+#pragma unroll
+    for (int v = 0; v < MD_CHUNK; ++v)
+      if (v < nv) acc[v] = fma((double)vp[v][i], wi, acc[v]);
+  }
+  __shared__ double red[MD_CHUNK][FLAT_THREADS / 32];
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v) {
+    double x = acc[v];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double s = 0.0;
+    for (int q = 0; q < FLAT_THREADS / 32; ++q) s += red[threadIdx.x][q];
+    partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// out[v] (+)= sum_b partial[v][b]   (one warp per v, fixed order)
+__global__ void k_reduce_partials(int nv, int nb, const double *partial, double *out, int accumulate) {
+  int v = blockIdx.x;
+  if (v >= nv) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) s += partial[(long long)v * nb + b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) out[v] = accumulate ? out[v] + s : s;
+}
+
+// w -= sum_v coef[v] V_v  (coef on device, FP64); sign = -1, or x += sum (sign = +1)
+template <typename T>
+__global__ void __launch_bounds__(FLAT_THREADS)
+k_multi_axpy(long long n, int nv, const T *const *V, const double *coef, double sign, T *w) {
+  double c[MD_CHUNK];
+  const T *vp[MD_CHUNK];
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v) { c[v] = v < nv ? sign * coef[v] : 0.0; vp[v] = v < nv ? V[v] : nullptr; }
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
+    double acc = (double)w[i];
+#pragma unroll
+    for (int v = 0; v < MD_CHUNK; ++v)
+      if (v < nv) acc = fma(c[v], (double)vp[v][i], acc);
+    w[i] = (T)acc;
+  }
+}
+
+// partial[blockIdx.x] = sum x[i] y[i] (FP64 accumulation, fixed grid)
+template <typename T>
+__global__ void __launch_bounds__(FLAT_THREADS)
+k_dot2(long long n, const T *__restrict__ x, const T *__restrict__ y, double *partial) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS)
+    acc = fma((double)x[i], (double)y[i], acc);
+  __shared__ double red[FLAT_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < FLAT_THREADS / 32; ++q) s += red[q];
+    partial[blockIdx.x] = s;
+  }
+}
+
+// y = a x + b y (FP64 arithmetic)
+template <typename T>
+__global__ void k_axpby(long long n, double a, const T *__restrict__ x, double b, T *__restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (T)(a * (double)x[i] + b * (double)y[i]);
+}
+
+// a[i] += b[i] for i < n (small FP64 vectors)
+__global__ void k_dadd(int n, double *a, const double *b) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] += b[i];
+}
+
+// y = x * (1 / *s)  (s on device); if s == 0, y = 0
+template <typename T>
+__global__ void k_scale_inv(long long n, const double *s, const T *x, T *y) {
+  double sv = *s;
+  double f = sv != 0.0 ? 1.0 / sv : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (T)((double)x[i] * f);
+}
+
+// Arnoldi column j of the flexible GMRES: h[0..j] = dots (accumulated over the
+// two CGS passes), h[j+1] = sqrt(norm2); applies the previous Givens
+// rotations, forms a new one, updates g.  One thread, FP64.  Writes |g[j+1]|
+// to res[0] and h[j+1] to hnext (the normalisation factor).
+__global__ void k_givens(int j, int m, double *H, double *cs, double *sn, double *g,
+                         const double *hcol, const double *norm2, double *hnext, double *res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double *col = H + (long long)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = hcol[i];
+  double hn = sqrt(fmax(norm2[0], 0.0));
+  col[j + 1] = hn;
+  *hnext = hn;
+  for (int i = 0; i < j; ++i) {
+    double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  double rr = hypot(col[j], col[j + 1]);
+  double c = rr > 0.0 ? col[j] / rr : 1.0;
+  double s = rr > 0.0 ? col[j + 1] / rr : 0.0;
+  cs[j] = c; sn[j] = s;
+  col[j] = rr; col[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  res[0] = fabs(g[j + 1]);
+}
+
+// Back substitution H(0:k,0:k) y = g(0:k) (upper triangular, column-major with
+// leading dimension m+1).
+__global__ void k_backsub(int k, int m, const double *H, const double *g, double *y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int c = i + 1; c < k; ++c) s -= H[(long long)c * (m + 1) + i] * y[c];
+    double d = H[(long long)i * (m + 1) + i];
+    y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+// Segmented (per-instance) operations on packed vectors.  A segment is a
+// contiguous range [beg, end) owned by one instance.
+struct SegDev {
+  long long beg, end;
+  int inst;
+};
+
+// partial[seg][blockIdx.x] = sum x^2 over the segment (FP64)
+template <typename T>
+__global__ void k_seg_norm2(const SegDev *segs, const T *x, double *partial, int nb) {
+  const SegDev s = segs[blockIdx.y];
+  double acc = 0.0;
+  for (long long i = s.beg + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.end;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = (double)x[i];
+    acc = fma(v, v, acc);
+  }
+  __shared__ double red[FLAT_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += red[q];
+    partial[(long long)blockIdx.y * nb + blockIdx.x] = t;
+  }
+}
+
+// y[i] = (TO)(x[i] * f[inst])     (per-instance factor)
+template <typename TI, typename TO>
+__global__ void k_seg_scale(const SegDev *segs, const TI *x, const double *f, TO *y) {
+  const SegDev s = segs[blockIdx.y];
+  double fv = f[s.inst];
+  for (long long i = s.beg + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.end;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (TO)((double)x[i] * fv);
+}
+
+// y[i] += f[inst] * (double)x[i]
+template <typename TI>
+__global__ void k_seg_axpy(const SegDev *segs, const TI *x, const double *f, double *y) {
+  const SegDev s = segs[blockIdx.y];
+  double fv = f[s.inst];
+  for (long long i = s.beg + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.end;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(fv, (double)x[i], y[i]);
+}
+
+// z = x - y (FP64, flat)
+__global__ void k_sub(long long n, const double *x, const double *y, double *z) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = x[i] - y[i];
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(long long n, const TI *x, TO *y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (TO)x[i];
+}
+
+// Non-finite check: *flag |= 1 if any x is NaN/Inf.
+template <typename T>
+__global__ void k_check_finite(long long n, const T *x, int *flag) {
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite((double)x[i])) bad = 1;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+// Per-block scaled conversion for the forward refinement: y_b = (TO)(x_b * f_b)
+// f = per-block factor (1/||r_b|| or ||r_b||), on the tile scheme (level 0).
+template <typename TI, typename TO, typename T>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_blk_scale(LevelView<T> L, const TI *x, const double *f, TO *y, int accumulate) {
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlkDev bk = L.blks[t.blk];
+  const OpDev op = L.ops[bk.op];
+  const int j = t.row0 + (threadIdx.x >> 5);
+  if (j >= op.nz) return;
+  double fv = f[t.blk];
+  long long base = 2 * (bk.off + (long long)j * op.nx);
+  for (int i = threadIdx.x & 31; i < 2 * op.nx; i += 32) {
+    double v = (double)x[base + i] * fv;
+    if (accumulate) y[base + i] = (TO)((double)y[base + i] + v);
+    else y[base + i] = (TO)v;
+  }
+}
+
+}  // namespace fwi

@@ -1,0 +1,1703 @@
+// fwi_runtime.cu -- host runtime and C ABI of the full-space Gauss-Newton FWI
+// library (see include/fwikkt.h for the entry points and their contracts).
+//
+// Everything numerical runs in the kernels of fwi_kernels.cuh; this file owns
+// device memory, builds the descriptor tables of the batch (blocks, operators,
+// row tiles, multigrid levels), sequences the kernel launches of the solvers
+// and reads back only scalars (residual norms) to steer the iterations.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <tuple>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/fwikkt.h"
+#include "fwi_kernels.cuh"
+
+namespace fwi {
+
+struct Err {
+  int code;
+  std::string msg;
+};
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw Err{FWI_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};           \
+  } while (0)
+#define KCHECK() CK(cudaGetLastError())
+
+static void fail(int code, const std::string &m) { throw Err{code, m}; }
+
+template <typename T> struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf &operator=(DBuf &&o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    if (count == n && p) return;
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      fail(FWI_E_NOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    n = count;
+  }
+  void upload(const std::vector<T> &h, cudaStream_t s) {
+    alloc(h.size());
+    if (!h.empty()) CK(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  void zero(cudaStream_t s) {
+    if (n) CK(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+};
+
+static int grid_for(long long n, int threads, int cap = 4096) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// --------------------------------------------------------------------------
+// problem description
+// --------------------------------------------------------------------------
+struct Instance {
+  fwi_grid g{};
+  int Nx = 0, Nz = 0;
+  std::vector<double> freqs;
+  int n_src = 0;
+  std::vector<int> src_ix, src_iz, rec_off, rec_ix, rec_iz;
+  std::vector<double> src_amp, rec_w;
+  bool has_survey = false, has_model = false, has_data = false;
+  double gamma_ref = 0.0;
+  DBuf<double> layer;   // padded gamma with the frozen layer [Nz*Nx]
+  DBuf<double> s;       // core model [nz*nx]
+  DBuf<double2> d;      // observed data [n_freq * rec_total]
+  int blk0 = 0;
+  int nlev = 1;
+  long long ctrl = 0;
+  int rec_total() const { return rec_off.empty() ? 0 : rec_off.back(); }
+};
+
+struct LevelTables {
+  std::vector<BlkDev> hM, hA;
+  std::vector<TileDev> htiles;
+  std::vector<int> ht0, ht1;
+  DBuf<BlkDev> blksM, blksA;
+  DBuf<TileDev> tiles;
+  DBuf<int> t0, t1;
+  long long field = 0;  // complex elements of one field on this level
+  int n_tiles = 0;
+};
+
+template <typename T> struct Work {
+  typedef typename cplx<T>::t T2;
+  int ready = 0;
+  // multigrid fields per global level (index 0 unused for b, x)
+  DBuf<T2> lx[MAX_LEVELS], lb[MAX_LEVELS], lt[MAX_LEVELS];
+  DBuf<T2> t0a, t0b;                                   // level-0 smoother buffers
+  DBuf<T2> r, rh, p, v, s, t, ph, sh;                  // BiCGStab
+  DBuf<BiState> bst;
+  DBuf<T2> u;                                          // forward wavefields (precision T)
+  // FGMRES
+  int m = 0;
+  long long n = 0;
+  DBuf<T> V, Z, vin, zout, tmp, rhs, sol;              // basis, staging, sweep rhs/solution
+  DBuf<T *> dptrV, dptrZ;
+  DBuf<double> H, cs, sn, g, hcol, hsum, y, scal, partial_flat;
+  // preconditioner graph
+  cudaGraphExec_t graph = nullptr;
+  std::string graph_key;
+  ~Work() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+};
+
+struct Ctx {
+  cudaStream_t st = nullptr;
+  std::string err;
+  std::vector<Instance> inst;
+  // block layout
+  bool layout_ok = false;
+  int B = 0;
+  std::vector<long long> blk_off;  // level 0
+  std::vector<int> blk_inst, blk_freq, blk_src, blk_Nx;
+  long long F0 = 0, Nc = 0, nkkt = 0;
+  DBuf<long long> d_blk_off;
+  DBuf<int> d_blk_Nx;
+  DBuf<InstDev> d_inst;
+  std::vector<InstDev> h_inst;
+  // receivers (level 0 field indices)
+  std::vector<long long> rec_node;                 // per survey receiver entry (all blocks)
+  std::vector<double> rec_w;
+  std::vector<long long> rec_data;                 // index into per-instance data arrays
+  DBuf<long long> d_rec_node, d_unode, d_F_node;
+  DBuf<double> d_rec_w, d_F_w2;
+  DBuf<int> d_uoff, d_uidx;
+  int n_unique = 0, n_F = 0;
+  DBuf<long long> d_src_node;
+  DBuf<double2> d_src_amp;
+  // hierarchy
+  int model_version = 1;
+  std::string hier_key;
+  int ls = 1, nlev_max = 1;
+  LevelTables lv[MAX_LEVELS];
+  std::vector<OpDev> h_ops;
+  DBuf<OpDev> d_ops;
+  DBuf<double2> st64;
+  DBuf<float2> st32;
+  DBuf<double> gam64;
+  DBuf<float> gam32;
+  DBuf<double2> inv;
+  DBuf<long long> inv_off;
+  DBuf<int> d_inst_nlev;
+  DBuf<double> cfK, cfG;   // per-block coupling factors (KKT scaled, gradient)
+  size_t smem_bytes[2] = {0, 0};
+  // forward state
+  bool have_fwd = false;
+  int fwd_version = 0;
+  DBuf<double2> u64, f64, rho64, e64;
+  DBuf<double2> q, r;                         // predicted data, residual per receiver entry
+  std::vector<double> misfit;
+  // KKT FP64 state
+  DBuf<double> b64, xi64, rho_k64, tmp64;
+  DBuf<SegDev> d_segs;
+  std::vector<SegDev> h_segs;
+  DBuf<double> seg_partial, inst_norm2, inst_fac;
+  DBuf<int> d_flag;
+  DBuf<double2> partial;   // per-tile partial sums [n_tiles0 * 3]
+  DBuf<double> blkfac, blkn0, blkn;   // per-block factors / norms
+  DBuf<double> misfit_d, inst_gref;
+  int u_version32 = -1, u_version64 = -1;
+  Work<float> w32;
+  Work<double> w64;
+  double *pin = nullptr;  // pinned scalars
+  int *pinflag = nullptr;
+
+  ~Ctx() {
+    if (pin) cudaFreeHost(pin);
+    if (pinflag) cudaFreeHost(pinflag);
+  }
+
+  template <typename T> Work<T> &work();
+  template <typename T> LevelView<T> viewA();
+  template <typename T> LevelView<T> viewM(int l);
+
+  // ------------------------------------------------------------------------
+  void build_layout();
+  void build_hierarchy(const fwi_opts &o);
+  template <typename T> void ensure_work(const fwi_opts &o);
+  template <typename T> void ensure_krylov(const fwi_opts &o);
+  template <typename T> const typename cplx<T>::t *u_T();
+  int gradient(const fwi_opts &o, double *misfit_out, double *grad, int on_device, fwi_stats *stats);
+  int newton_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats);
+  void write_ctrl(const double *src_ctrl_dev, double *dst, int on_device, const double *fac);
+  template <typename T> void mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
+                                      const fwi_opts &o);
+  template <typename T> void inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
+                                         int iters, double tol, const fwi_opts &o, long long *count);
+  template <typename T> void field_op(int mode, int cj, T w, const typename cplx<T>::t *x,
+                                      const typename cplx<T>::t *b, typename cplx<T>::t *y, bool opA,
+                                      int level);
+  template <typename T> void block_dots(int nd, const typename cplx<T>::t *a0, const typename cplx<T>::t *b0,
+                                        const typename cplx<T>::t *a1, const typename cplx<T>::t *b1,
+                                        const typename cplx<T>::t *a2, const typename cplx<T>::t *b2);
+  template <typename T> void kkt_matvec(const T *xi, T *y, double eps, const typename cplx<T>::t *u);
+  template <typename T> void precond(const T *v, T *z, const fwi_opts &o, long long *count);
+  template <typename T> void precond_any(const T *v, T *z, const fwi_opts &o, long long *count);
+  template <typename T> int fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi_opts &o,
+                                   int *iters, long long *inner, const typename cplx<T>::t *u);
+  template <typename T> void multidot(long long n, int nv, T *const *dV, const T *w, double *out, int acc);
+  void forward(const fwi_opts &o, fwi_stats *stats);
+  template <typename T> int refined_solve(const double2 *rhs, double2 *x, int cj, const fwi_opts &o,
+                                          fwi_stats *stats);
+  void seg_norms(const double *x);
+  int kkt_solve(const fwi_opts &o, fwi_stats *stats);
+  void sync() { CK(cudaStreamSynchronize(st)); }
+};
+
+template <> Work<float> &Ctx::work<float>() { return w32; }
+template <> Work<double> &Ctx::work<double>() { return w64; }
+
+template <typename T> static const typename cplx<T>::t *st_ptr(Ctx &c);
+template <> const float2 *st_ptr<float>(Ctx &c) { return c.st32.p; }
+template <> const double2 *st_ptr<double>(Ctx &c) { return c.st64.p; }
+template <typename T> static const T *gam_ptr(Ctx &c);
+template <> const float *gam_ptr<float>(Ctx &c) { return c.gam32.p; }
+template <> const double *gam_ptr<double>(Ctx &c) { return c.gam64.p; }
+
+template <typename T> LevelView<T> Ctx::viewA() {
+  LevelView<T> v;
+  v.ops = d_ops.p; v.blks = lv[0].blksA.p; v.tiles = lv[0].tiles.p;
+  v.st = st_ptr<T>(*this); v.gam = gam_ptr<T>(*this);
+  v.n_tiles = lv[0].n_tiles; v.n_blocks = B;
+  return v;
+}
+template <typename T> LevelView<T> Ctx::viewM(int l) {
+  LevelView<T> v;
+  v.ops = d_ops.p; v.blks = lv[l].blksM.p; v.tiles = lv[l].tiles.p;
+  v.st = st_ptr<T>(*this); v.gam = gam_ptr<T>(*this);
+  v.n_tiles = lv[l].n_tiles; v.n_blocks = B;
+  return v;
+}
+
+// --------------------------------------------------------------------------
+// layout of the batch (blocks, receivers, sources)
+// --------------------------------------------------------------------------
+static int auto_levels(int Nx, int Nz, int max_nodes = 256, int min_dim = 3) {
+  int L = 1, nx = Nx, nz = Nz;
+  while ((long long)nx * nz > max_nodes && nx / 2 >= min_dim && nz / 2 >= min_dim) {
+    nx /= 2; nz /= 2; ++L;
+  }
+  return L;
+}
+
+void Ctx::build_layout() {
+  if (layout_ok) return;
+  for (size_t i = 0; i < inst.size(); ++i)
+    if (!inst[i].has_survey || !inst[i].has_model) fail(FWI_E_INVAL, "every instance needs a survey and a model");
+  B = 0; F0 = 0; Nc = 0;
+  blk_off.clear(); blk_inst.clear(); blk_freq.clear(); blk_src.clear(); blk_Nx.clear();
+  h_inst.clear();
+  for (size_t i = 0; i < inst.size(); ++i) {
+    Instance &I = inst[i];
+    I.blk0 = B;
+    I.ctrl = Nc;
+    InstDev d;
+    d.npml = I.g.npml; d.nx = I.g.nx; d.nz = I.g.nz;
+    d.blk0 = B;
+    for (size_t f = 0; f < I.freqs.size(); ++f)
+      for (int k = 0; k < I.n_src; ++k) {
+        blk_off.push_back(F0);
+        blk_inst.push_back((int)i); blk_freq.push_back((int)f); blk_src.push_back(k);
+        blk_Nx.push_back(I.Nx);
+        F0 += (long long)I.Nx * I.Nz;
+        ++B;
+      }
+    d.blk1 = B;
+    d.ctrl = Nc;
+    Nc += (long long)I.g.nx * I.g.nz;
+    h_inst.push_back(d);
+  }
+  nkkt = 4 * F0 + Nc;
+  d_inst.upload(h_inst, st);
+  d_blk_off.upload(blk_off, st);
+  d_blk_Nx.upload(blk_Nx, st);
+  // receivers: one entry per (block, survey receiver of its source)
+  rec_node.clear(); rec_w.clear(); rec_data.clear();
+  std::vector<long long> src_node;
+  std::vector<double2> amp;
+  for (int b = 0; b < B; ++b) {
+    Instance &I = inst[blk_inst[b]];
+    int k = blk_src[b], f = blk_freq[b];
+    int p = I.g.npml;
+    src_node.push_back(blk_off[b] + (long long)(I.src_iz[k] + p) * I.Nx + (I.src_ix[k] + p));
+    amp.push_back(make_double2(I.src_amp[2 * k], I.src_amp[2 * k + 1]));
+    for (int e = I.rec_off[k]; e < I.rec_off[k + 1]; ++e) {
+      rec_node.push_back(blk_off[b] + (long long)(I.rec_iz[e] + p) * I.Nx + (I.rec_ix[e] + p));
+      rec_w.push_back(I.rec_w[e]);
+      rec_data.push_back((long long)f * I.rec_total() + e);
+    }
+  }
+  d_src_node.upload(src_node, st);
+  d_src_amp.upload(amp, st);
+  d_rec_node.upload(rec_node, st);
+  d_rec_w.upload(rec_w, st);
+  // unique receiver nodes (for the scatter Q^T W^T W r and the diagonal F)
+  std::vector<int> order(rec_node.size());
+  for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rec_node[a] < rec_node[b]; });
+  std::vector<long long> unode;
+  std::vector<int> uoff, uidx;
+  std::vector<double> fw2;
+  for (size_t q = 0; q < order.size(); ++q) {
+    if (q == 0 || rec_node[order[q]] != rec_node[order[q - 1]]) {
+      unode.push_back(rec_node[order[q]]);
+      uoff.push_back((int)q);
+      fw2.push_back(0.0);
+    }
+    uidx.push_back(order[q]);
+    fw2.back() += rec_w[order[q]] * rec_w[order[q]];
+  }
+  uoff.push_back((int)order.size());
+  n_unique = (int)unode.size();
+  n_F = n_unique;
+  d_unode.upload(unode, st);
+  d_uoff.upload(uoff, st);
+  d_uidx.upload(uidx, st);
+  d_F_node.upload(unode, st);
+  d_F_w2.upload(fw2, st);
+  // segments of packed vectors: [du | lm | ds], one per instance and region
+  h_segs.clear();
+  for (size_t i = 0; i < inst.size(); ++i) {
+    long long b0 = blk_off[h_inst[i].blk0];
+    long long b1 = h_inst[i].blk1 < B ? blk_off[h_inst[i].blk1] : F0;
+    h_segs.push_back(SegDev{2 * b0, 2 * b1, (int)i});
+    h_segs.push_back(SegDev{2 * F0 + 2 * b0, 2 * F0 + 2 * b1, (int)i});
+    h_segs.push_back(SegDev{4 * F0 + h_inst[i].ctrl, 4 * F0 + h_inst[i].ctrl + (long long)inst[i].g.nx * inst[i].g.nz, (int)i});
+  }
+  d_segs.upload(h_segs, st);
+  seg_partial.alloc(h_segs.size() * 64);
+  inst_norm2.alloc(inst.size());
+  inst_fac.alloc(inst.size());
+  d_flag.alloc(1);
+  if (!pin) {
+    CK(cudaMallocHost((void **)&pin, 64 * sizeof(double)));
+    CK(cudaMallocHost((void **)&pinflag, 4 * sizeof(int)));
+  }
+  layout_ok = true;
+  hier_key.clear();
+  w32.ready = 0;
+  w64.ready = 0;
+}
+
+// --------------------------------------------------------------------------
+// a1: per-frequency set-up -- stretch arrays, gamma on every level, operator
+// tables, coarsest dense inverses (FP64)
+// --------------------------------------------------------------------------
+void Ctx::build_hierarchy(const fwi_opts &o) {
+  build_layout();
+  char key[256];
+  snprintf(key, sizeof key, "%d|%d|%.17g|%.17g", model_version, o.mg_levels, o.shift_beta, o.sigma_cap);
+  if (hier_key == key) return;
+  const int n_inst = (int)inst.size();
+  // levels per instance
+  nlev_max = 1;
+  for (auto &I : inst) {
+    int L = auto_levels(I.Nx, I.Nz);
+    if (o.mg_levels > 0) L = std::min(L, o.mg_levels);
+    if (L > MAX_LEVELS) L = MAX_LEVELS;
+    I.nlev = L;
+    nlev_max = std::max(nlev_max, L);
+  }
+  // level dims per instance
+  auto dims = [&](const Instance &I, int l, int &nx, int &nz) {
+    nx = I.Nx; nz = I.Nz;
+    for (int q = 0; q < l; ++q) { nx /= 2; nz /= 2; }
+  };
+  // shared-memory start level: the first level from which every instance's
+  // remaining levels (3 vectors each) fit in the per-CTA budget (c64);
+  // complex128 may need a coarser start.
+  const size_t budget = 200 * 1024;
+  auto smem_from = [&](int l0, size_t elem) {
+    size_t mx = 0;
+    for (auto &I : inst) {
+      size_t s = 0;
+      for (int l = l0; l < I.nlev; ++l) { int nx, nz; dims(I, l, nx, nz); s += 3 * (size_t)nx * nz * elem; }
+      mx = std::max(mx, s);
+    }
+    return mx;
+  };
+  int minlev = nlev_max;
+  for (auto &I : inst) minlev = std::min(minlev, I.nlev);
+  ls = 1;
+  while (ls < minlev - 1 && smem_from(ls, sizeof(double2)) > budget) ++ls;
+  if (minlev < 2) ls = 0;  // single-level instances: the whole cycle is the coarse solve
+  smem_bytes[0] = smem_from(ls, sizeof(float2));
+  smem_bytes[1] = smem_from(ls, sizeof(double2));
+  if (smem_bytes[1] > 227 * 1024) fail(FWI_E_INVAL, "grids too different for one batch (coarse levels exceed shared memory)");
+  // operators
+  h_ops.clear();
+  std::vector<AxisDev> axes;
+  long long st_tot = 0;
+  std::vector<long long> gam_off(n_inst * MAX_LEVELS, -1);
+  long long gam_tot = 0;
+  for (int i = 0; i < n_inst; ++i)
+    for (int l = 0; l < inst[i].nlev; ++l) {
+      int nx, nz; dims(inst[i], l, nx, nz);
+      gam_off[i * MAX_LEVELS + l] = gam_tot;
+      gam_tot += (long long)nx * nz;
+    }
+  // op ids: A ops [inst][freq], M ops [inst][freq][level]
+  std::vector<int> opA(B), opM0(B);
+  std::vector<std::vector<int>> opM(MAX_LEVELS, std::vector<int>(B, -1));
+  std::vector<int> coarse_ops;
+  std::map<std::pair<int, int>, int> aid;
+  std::map<std::tuple<int, int, int>, int> mid;
+  for (int i = 0; i < n_inst; ++i) {
+    Instance &I = inst[i];
+    double L = I.g.npml * I.g.h;
+    double smax = I.g.npml > 0 ? 3.0 * I.g.pml_c * std::log(1.0 / I.g.pml_R) / (2.0 * L) : 0.0;
+    for (size_t f = 0; f < I.freqs.size(); ++f) {
+      double om = 2.0 * M_PI * I.freqs[f];
+      for (int kind = 0; kind < 2; ++kind) {
+        int nl = kind == 0 ? 1 : I.nlev;
+        for (int l = 0; l < nl; ++l) {
+          int nx, nz; dims(I, l, nx, nz);
+          double hl = I.g.h, x0 = 0.0;
+          for (int q = 0; q < l; ++q) { x0 += hl; hl *= 2.0; }
+          OpDev od;
+          od.nx = nx; od.nz = nz;
+          od.st = st_tot;
+          od.gam = gam_off[i * MAX_LEVELS + l];
+          double beta = kind == 0 ? 0.0 : o.shift_beta;
+          od.mass_re = (om * hl) * (om * hl);
+          od.mass_im = beta * (om * hl) * (om * hl);
+          AxisDev ad;
+          ad.dst = st_tot; ad.nx = nx; ad.nz = nz; ad.x0 = x0; ad.z0 = x0; ad.hl = hl;
+          ad.xlo = I.g.npml * I.g.h; ad.xhi = (I.g.npml + I.g.nx - 1) * I.g.h;
+          ad.zlo = I.g.npml * I.g.h; ad.zhi = (I.g.npml + I.g.nz - 1) * I.g.h;
+          ad.L = L; ad.smax = smax; ad.omega = om; ad.cap = kind == 0 ? -1.0 : o.sigma_cap;
+          axes.push_back(ad);
+          st_tot += 2 * nx + 2 * nz + 2;
+          int id = (int)h_ops.size();
+          h_ops.push_back(od);
+          if (kind == 0) aid[{i, (int)f}] = id;
+          else {
+            mid[{i, (int)f, l}] = id;
+            if (l == I.nlev - 1) coarse_ops.push_back(id);
+          }
+        }
+      }
+    }
+  }
+  d_ops.upload(h_ops, st);
+  std::vector<AxisDev> hax = axes;
+  DBuf<AxisDev> dax;
+  dax.upload(hax, st);
+  st64.alloc(st_tot);
+  st32.alloc(st_tot);
+  k_stretch_setup<<<(int)axes.size(), 128, 0, st>>>(dax.p, (int)axes.size(), st64.p, st32.p);
+  KCHECK();
+  // gamma on every level
+  gam64.alloc(gam_tot);
+  gam32.alloc(gam_tot);
+  for (int i = 0; i < n_inst; ++i) {
+    Instance &I = inst[i];
+    long long n0 = (long long)I.Nx * I.Nz;
+    k_gamma_fill<<<grid_for(n0, 256), 256, 0, st>>>(I.layer.p, I.s.p, I.Nx, I.Nz, I.g.npml, I.g.nx, I.g.nz,
+                                                     gam64.p + gam_off[i * MAX_LEVELS], gam32.p + gam_off[i * MAX_LEVELS]);
+    KCHECK();
+    for (int l = 1; l < I.nlev; ++l) {
+      int nxf, nzf, nxc, nzc;
+      dims(I, l - 1, nxf, nzf); dims(I, l, nxc, nzc);
+      k_gamma_restrict<<<grid_for((long long)nxc * nzc, 256), 256, 0, st>>>(
+          gam64.p + gam_off[i * MAX_LEVELS + l - 1], nxf, nzf, nxc, nzc, gam64.p + gam_off[i * MAX_LEVELS + l],
+          gam32.p + gam_off[i * MAX_LEVELS + l]);
+      KCHECK();
+    }
+  }
+  // coarsest inverses
+  std::vector<long long> h_inv_off(h_ops.size(), -1), aug_off, inv_off_l;
+  std::vector<int> cdims;
+  long long inv_tot = 0, aug_tot = 0;
+  for (int id : coarse_ops) {
+    long long n = (long long)h_ops[id].nx * h_ops[id].nz;
+    h_inv_off[id] = inv_tot;
+    inv_off_l.push_back(inv_tot);
+    aug_off.push_back(aug_tot);
+    cdims.push_back((int)n);
+    inv_tot += n * n;
+    aug_tot += n * 2 * n;
+  }
+  inv.alloc(inv_tot);
+  inv_off.upload(h_inv_off, st);
+  {
+    DBuf<double2> aug;
+    aug.alloc(aug_tot);
+    DBuf<int> dids, ddims, dstat;
+    DBuf<long long> daoff, dioff;
+    dids.upload(coarse_ops, st);
+    ddims.upload(cdims, st);
+    daoff.upload(aug_off, st);
+    dioff.upload(inv_off_l, st);
+    dstat.alloc(1);
+    dstat.zero(st);
+    k_coarse_assemble<<<(int)coarse_ops.size(), 256, 0, st>>>(d_ops.p, dids.p, daoff.p, st64.p, gam64.p, aug.p);
+    KCHECK();
+    k_gauss_jordan<<<(int)coarse_ops.size(), 256, 0, st>>>(ddims.p, daoff.p, dioff.p, aug.p, inv.p, dstat.p);
+    KCHECK();
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, dstat.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    sync();
+    if (hs) fail(FWI_E_NUMERIC, "coarsest multigrid operator is singular");
+  }
+  std::vector<int> hn(n_inst);
+  for (int i = 0; i < n_inst; ++i) hn[i] = inst[i].nlev;
+  d_inst_nlev.upload(hn, st);
+  // per-level block and tile tables (all levels < nlev of each instance; the
+  // smem levels need only the block tables)
+  for (int l = 0; l < nlev_max; ++l) {
+    LevelTables &T = lv[l];
+    T.hM.assign(B, BlkDev{0, 0, 0});
+    T.hA.assign(B, BlkDev{0, 0, 0});
+    T.htiles.clear(); T.ht0.assign(B, 0); T.ht1.assign(B, 0);
+    long long off = 0;
+    for (int b = 0; b < B; ++b) {
+      int i = blk_inst[b];
+      Instance &I = inst[i];
+      int lq = std::min(l, I.nlev - 1);
+      int nx, nz; dims(I, lq, nx, nz);
+      BlkDev bd;
+      bd.off = off; bd.inst = i;
+      bd.op = mid[{i, blk_freq[b], lq}];
+      T.hM[b] = bd;
+      bd.op = aid[{i, blk_freq[b]}];
+      T.hA[b] = bd;
+      T.ht0[b] = (int)T.htiles.size();
+      if (l <= ls)
+        for (int r0 = 0; r0 < nz; r0 += TILE_ROWS) T.htiles.push_back(TileDev{b, r0});
+      T.ht1[b] = (int)T.htiles.size();
+      off += (long long)nx * nz;
+    }
+    T.field = off;
+    T.n_tiles = (int)T.htiles.size();
+    T.blksM.upload(T.hM, st);
+    T.blksA.upload(T.hA, st);
+    T.tiles.upload(T.htiles, st);
+    T.t0.upload(T.ht0, st);
+    T.t1.upload(T.ht1, st);
+  }
+  partial.alloc((size_t)std::max(1, lv[0].n_tiles) * 3);
+  blkfac.alloc(B); blkn0.alloc(B); blkn.alloc(B);
+  // coupling factors: KKT (h^2 gamma_ref omega^2) and gradient (h^2 omega^2)
+  std::vector<double> cK(B), cG(B);
+  for (int b = 0; b < B; ++b) {
+    Instance &I = inst[blk_inst[b]];
+    double om = 2.0 * M_PI * I.freqs[blk_freq[b]];
+    cG[b] = I.g.h * I.g.h * om * om;
+    cK[b] = cG[b] * I.gamma_ref;
+  }
+  cfK.upload(cK, st);
+  cfG.upload(cG, st);
+  sync();
+  hier_key = key;
+  w32.ready = 0;
+  w64.ready = 0;
+}
+
+template <typename T> void Ctx::ensure_work(const fwi_opts &o) {
+  Work<T> &w = work<T>();
+  if (w.ready) return;
+  for (int l = 1; l <= ls && l < nlev_max; ++l) {
+    w.lx[l].alloc(lv[l].field); w.lb[l].alloc(lv[l].field); w.lt[l].alloc(lv[l].field);
+  }
+  w.t0a.alloc(F0); w.t0b.alloc(F0);
+  w.r.alloc(F0); w.rh.alloc(F0); w.p.alloc(F0); w.v.alloc(F0);
+  w.s.alloc(F0); w.t.alloc(F0); w.ph.alloc(F0); w.sh.alloc(F0);
+  w.bst.alloc(B);
+  w.u.alloc(F0);
+  w.vin.alloc(nkkt); w.zout.alloc(nkkt); w.tmp.alloc(nkkt);
+  w.scal.alloc(8);
+  w.partial_flat.alloc((size_t)MD_CHUNK * FLAT_BLOCKS);
+  if (smem_bytes[sizeof(T) == 8] > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_coarse_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_bytes[sizeof(T) == 8]));
+  if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
+  w.graph_key.clear();
+  sync();
+  w.ready = 1;
+  (void)o;
+}
+
+// FGMRES basis (restart m): V (m+1 vectors) and Z (m vectors) of the packed KKT size.
+template <typename T> void Ctx::ensure_krylov(const fwi_opts &o) {
+  ensure_work<T>(o);
+  Work<T> &w = work<T>();
+  int m = std::max(1, o.restart);
+  if (w.m == m && w.V.p) return;
+  w.m = m;
+  w.n = nkkt;
+  w.V.alloc((size_t)(m + 1) * nkkt);
+  w.Z.alloc((size_t)m * nkkt);
+  std::vector<T *> pv(m + 1), pz(m);
+  for (int k = 0; k <= m; ++k) pv[k] = w.V.p + (size_t)k * nkkt;
+  for (int k = 0; k < m; ++k) pz[k] = w.Z.p + (size_t)k * nkkt;
+  w.dptrV.upload(pv, st);
+  w.dptrZ.upload(pz, st);
+  w.H.alloc((size_t)(m + 1) * m); w.cs.alloc(m); w.sn.alloc(m); w.g.alloc(m + 1);
+  w.hcol.alloc(m + 1); w.hsum.alloc(m + 1); w.y.alloc(m);
+  w.rhs.alloc(nkkt); w.sol.alloc(nkkt);
+  sync();
+}
+
+// --------------------------------------------------------------------------
+// field operations
+// --------------------------------------------------------------------------
+template <typename T>
+void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
+                   typename cplx<T>::t *y, bool opA, int level) {
+  LevelView<T> L = opA ? viewA<T>() : viewM<T>(level);
+  k_field_op<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, cj, wj, x, b, y);
+  KCHECK();
+}
+
+template <typename T>
+void Ctx::block_dots(int nd, const typename cplx<T>::t *a0, const typename cplx<T>::t *b0,
+                     const typename cplx<T>::t *a1, const typename cplx<T>::t *b1,
+                     const typename cplx<T>::t *a2, const typename cplx<T>::t *b2) {
+  LevelView<T> L = viewA<T>();
+  k_block_dots<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, nd, a0, b0, a1, b1, a2, b2, partial.p);
+  KCHECK();
+}
+
+// One multigrid cycle for the shifted operator, x = cycle(b) (Sec. 5: the
+// shifted-Laplacian preconditioner; levels >= ls run in shared memory).
+template <typename T>
+void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj, const fwi_opts &o) {
+  typedef typename cplx<T>::t T2;
+  Work<T> &w = work<T>();
+  const T wj = (T)o.omega_jac;
+  CoarseArgs ca;
+  for (int l = 0; l < MAX_LEVELS; ++l) ca.blks[l] = l < nlev_max ? lv[l].blksM.p : nullptr;
+  ca.ops = d_ops.p; ca.inv = inv.p; ca.inv_off = inv_off.p; ca.inst_nlev = d_inst_nlev.p;
+  ca.ls = ls; ca.nu1 = o.nu1; ca.nu2 = o.nu2; ca.cyc = o.mg_cycle; ca.cj = cj; ca.w = o.omega_jac;
+  size_t smem = smem_bytes[sizeof(T) == 8];
+  if (ls == 0) {
+    k_coarse_cycle<T><<<B, 256, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
+    KCHECK();
+    return;
+  }
+  // recursive cycle over the global levels 0..ls-1; returns the buffer that
+  // holds the level's solution.
+  std::function<T2 *(int, const T2 *, T2 *, T2 *)> cyc;
+  cyc = [&](int l, const T2 *bl, T2 *xa, T2 *xb) -> T2 * {
+    if (l == ls) {
+      k_coarse_cycle<T><<<B, 256, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), bl, xa);
+      KCHECK();
+      return xa;
+    }
+    T2 *cur = xa, *oth = xb;
+    if (o.nu1 == 0) CK(cudaMemsetAsync(cur, 0, lv[l].field * sizeof(T2), st));
+    for (int s = 0; s < o.nu1; ++s) {
+      field_op<T>(s == 0 ? FM_JACOBI0 : FM_JACOBI, cj, wj, s == 0 ? nullptr : cur, bl, s == 0 ? cur : oth, false, l);
+      if (s > 0) std::swap(cur, oth);
+    }
+    int reps = l == 0 ? 1 : o.mg_cycle;
+    for (int r = 0; r < reps; ++r) {
+      LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
+      k_resid_restrict<T><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cj, cur, bl, w.lb[l + 1].p);
+      KCHECK();
+      T2 *xc = cyc(l + 1, w.lb[l + 1].p, w.lx[l + 1].p, w.lt[l + 1].p);
+      k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
+      KCHECK();
+    }
+    for (int s = 0; s < o.nu2; ++s) {
+      field_op<T>(FM_JACOBI, cj, wj, cur, bl, oth, false, l);
+      std::swap(cur, oth);
+    }
+    return cur;
+  };
+  T2 *res = cyc(0, b, x, w.t0a.p);
+  if (res != x) CK(cudaMemcpyAsync(x, res, F0 * sizeof(T2), cudaMemcpyDeviceToDevice, st));
+}
+
+// Batched right-preconditioned BiCGStab, one independent system per block
+// (per-block scalars), x = approx A'^{-1} b (cj = 1: A'^H).
+template <typename T>
+void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj, int iters, double tol,
+                      const fwi_opts &o, long long *count) {
+  typedef typename cplx<T>::t T2;
+  Work<T> &w = work<T>();
+  LevelView<T> L = viewA<T>();
+  const int nt = L.n_tiles;
+  const int sb = (B + 127) / 128;
+  auto upd = [&](int opk, T2 *y, const T2 *a, const T2 *c, const T2 *d, T2 *y2, const T2 *e) {
+    k_bicg_update<T><<<nt, TILE_THREADS, 0, st>>>(L, opk, w.bst.p, y, a, c, d, y2, e);
+    KCHECK();
+  };
+  auto scal = [&](int stage) {
+    k_bicg_scalars<<<sb, 128, 0, st>>>(B, lv[0].t0.p, lv[0].t1.p, partial.p, w.bst.p, stage, tol);
+    KCHECK();
+  };
+  // x = 0, r = b, rh = b, p = v = 0
+  upd(4, x, nullptr, nullptr, nullptr, nullptr, nullptr);
+  upd(3, w.r.p, b, nullptr, nullptr, nullptr, nullptr);
+  upd(3, w.rh.p, b, nullptr, nullptr, nullptr, nullptr);
+  upd(4, w.p.p, nullptr, nullptr, nullptr, nullptr, nullptr);
+  upd(4, w.v.p, nullptr, nullptr, nullptr, nullptr, nullptr);
+  block_dots<T>(1, b, b, nullptr, nullptr, nullptr, nullptr);
+  scal(0);
+  for (int it = 0; it < iters; ++it) {
+    block_dots<T>(1, w.rh.p, w.r.p, nullptr, nullptr, nullptr, nullptr);
+    scal(1);
+    upd(0, w.p.p, w.r.p, w.v.p, nullptr, nullptr, nullptr);          // p = r + beta (p - omega v)
+    mg_cycle<T>(w.p.p, w.ph.p, cj, o);                                 // ph = K p
+    field_op<T>(FM_APPLY, cj, (T)0, w.ph.p, nullptr, w.v.p, true, 0);  // v = A ph
+    block_dots<T>(1, w.rh.p, w.v.p, nullptr, nullptr, nullptr, nullptr);
+    scal(2);
+    upd(1, w.s.p, w.r.p, w.v.p, nullptr, nullptr, nullptr);          // s = r - alpha v
+    mg_cycle<T>(w.s.p, w.sh.p, cj, o);                                 // sh = K s
+    field_op<T>(FM_APPLY, cj, (T)0, w.sh.p, nullptr, w.t.p, true, 0);  // t = A sh
+    block_dots<T>(2, w.t.p, w.s.p, w.t.p, w.t.p, nullptr, nullptr);
+    scal(3);
+    upd(2, x, w.ph.p, w.sh.p, w.s.p, w.r.p, w.t.p);                   // x += a ph + w sh; r = s - w t
+    block_dots<T>(1, w.r.p, w.r.p, nullptr, nullptr, nullptr, nullptr);
+    scal(4);
+    if (count) *count += B;
+  }
+}
+
+// --------------------------------------------------------------------------
+// KKT operator (Sec. 4, eq. KKT, rescaled) and preconditioner (Sec. 5)
+// --------------------------------------------------------------------------
+template <typename T>
+void Ctx::kkt_matvec(const T *xi, T *y, double eps, const typename cplx<T>::t *u) {
+  typedef typename cplx<T>::t T2;
+  const T2 *du = (const T2 *)xi;
+  const T2 *lm = (const T2 *)(xi + 2 * F0);
+  const T *ds = xi + 4 * F0;
+  T2 *yu = (T2 *)y;
+  T2 *ylm = (T2 *)(y + 2 * F0);
+  T *ys = y + 4 * F0;
+  LevelView<T> L = viewA<T>();
+  k_kkt_rows<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, d_inst.p, cfK.p, u, du, lm, ds, yu, ylm);
+  KCHECK();
+  if (n_F) {
+    k_kkt_F<T><<<grid_for(n_F, 128, 1 << 20), 128, 0, st>>>(n_F, d_F_node.p, d_F_w2.p, du, yu);
+    KCHECK();
+  }
+  long long mx = 0;
+  for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
+  dim3 g((unsigned)((mx + 127) / 128), (unsigned)inst.size());
+  k_coupling_reduce<T, T><<<g, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfK.p, u, lm, ds, eps, 0, ys);
+  KCHECK();
+}
+
+template <typename T>
+void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count) {
+  typedef typename cplx<T>::t T2;
+  Work<T> &w = work<T>();
+  const T2 *v1 = (const T2 *)v;
+  const T2 *v3 = (const T2 *)(v + 2 * F0);
+  const T *v2 = v + 4 * F0;
+  T2 *zu = (T2 *)z;
+  T2 *zl = (T2 *)(z + 2 * F0);
+  T *zs = z + 4 * F0;
+  int iters = o.inner_iters;
+  double tol = o.inner_tol;
+  if (tol > 0.0) iters = std::max(iters, 2000);
+  // z_lambda = A'^{-H} v1
+  inner_solve<T>(v1, zl, 1, iters, tol, o, count);
+  // z_s = (v2 + Re(P~^H z_lambda)) / eps
+  long long mx = 0;
+  for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
+  dim3 g((unsigned)((mx + 127) / 128), (unsigned)inst.size());
+  k_coupling_reduce<T, T><<<g, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfK.p, w.u.p, zl, v2, o.eps, 1, zs);
+  KCHECK();
+  // z_u = A'^{-1} (v3 + P~ z_s)
+  LevelView<T> L = viewA<T>();
+  k_coupling_scatter<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, d_inst.p, cfK.p, w.u.p, v3, zs, w.t0b.p);
+  KCHECK();
+  inner_solve<T>(w.t0b.p, zu, 0, iters, tol, o, count);
+}
+
+// Preconditioner application, replayed from a CUDA graph when requested (the
+// graph reads w.vin and writes w.zout).
+template <typename T>
+void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count) {
+  Work<T> &w = work<T>();
+  bool graphable = o.use_graph && !(o.inner_tol > 0.0);
+  if (!graphable) { precond<T>(v, z, o, count); return; }
+  char key[256];
+  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%.17g|%.17g|%.17g", hier_key.c_str(), o.inner_iters, o.mg_cycle,
+           o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta);
+  if (w.graph_key != key) {
+    if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
+    cudaGraph_t gr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    long long dummy = 0;
+    try {
+      precond<T>(w.vin.p, w.zout.p, o, &dummy);
+    } catch (...) {
+      cudaStreamEndCapture(st, &gr);
+      throw;
+    }
+    CK(cudaStreamEndCapture(st, &gr));
+    CK(cudaGraphInstantiate(&w.graph, gr, 0));
+    cudaGraphDestroy(gr);
+    w.graph_key = key;
+  }
+  CK(cudaMemcpyAsync(w.vin.p, v, nkkt * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  CK(cudaGraphLaunch(w.graph, st));
+  CK(cudaMemcpyAsync(z, w.zout.p, nkkt * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  if (count) *count += 2LL * o.inner_iters * B;
+}
+
+template <typename T>
+void Ctx::multidot(long long n, int nv, T *const *dV, const T *wv, double *out, int acc) {
+  Work<T> &w = work<T>();
+  for (int c0 = 0; c0 < nv; c0 += MD_CHUNK) {
+    int c = std::min(MD_CHUNK, nv - c0);
+    k_multidot<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
+    KCHECK();
+    k_reduce_partials<<<c, 32, 0, st>>>(c, FLAT_BLOCKS, w.partial_flat.p, out + c0, acc);
+    KCHECK();
+  }
+}
+
+// ||x||^2 or x.y over a flat array into *out (FP64, deterministic).
+template <typename T>
+static void flat_dot(cudaStream_t st, long long n, const T *x, const T *y, double *partial, double *out) {
+  k_dot2<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
+  KCHECK();
+  k_reduce_partials<<<1, 32, 0, st>>>(1, FLAT_BLOCKS, partial, out, 0);
+  KCHECK();
+}
+
+// Right-preconditioned flexible GMRES(m) (Saad 1993) on the KKT matrix, CGS2
+// orthogonalisation with FP64 arithmetic on storage of precision T, Givens
+// rotations and Hessenberg in FP64 on the device; x = 0 initially.  Sec. 5
+// (FSGN-GMRes) and Sec. 6 (30 GMRES iterations per cycle).  Returns 0 when the
+// residual estimate reached tol * ||rhs||.
+template <typename T>
+int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi_opts &o, int *iters,
+                long long *inner, const typename cplx<T>::t *u) {
+  Work<T> &w = work<T>();
+  const int m = w.m;
+  const long long n = nkkt;
+  T *const *dV = w.dptrV.p;
+  T *const *dZ = w.dptrZ.p;
+  CK(cudaMemsetAsync(x, 0, n * sizeof(T), st));
+  flat_dot<T>(st, n, rhs, rhs, w.partial_flat.p, w.scal.p);
+  CK(cudaMemcpyAsync(pin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  sync();
+  const double bnorm = std::sqrt(pin[0]);
+  if (!(bnorm > 0.0)) return 0;
+  if (!std::isfinite(bnorm)) fail(FWI_E_NUMERIC, "non-finite right-hand side in FGMRES");
+  const T *r = rhs;
+  double beta = bnorm;
+  int total = 0;
+  bool conv = false;
+  while (total < maxit && !conv) {
+    CK(cudaMemcpyAsync(w.scal.p + 1, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
+    k_scale_inv<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, w.scal.p + 1, r, w.V.p);
+    KCHECK();
+    std::vector<double> g0(m + 1, 0.0);
+    g0[0] = beta;
+    CK(cudaMemcpyAsync(w.g.p, g0.data(), (m + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+    int k = 0;
+    for (int j = 0; j < m && total < maxit; ++j) {
+      T *vj = w.V.p + (size_t)j * n;
+      T *zj = w.Z.p + (size_t)j * n;
+      T *wv = w.V.p + (size_t)(j + 1) * n;
+      precond_any<T>(vj, zj, o, inner);
+      kkt_matvec<T>(zj, wv, eps, u);
+      // classical Gram-Schmidt, twice
+      multidot<T>(n, j + 1, dV, wv, w.hcol.p, 0);
+      for (int c0 = 0; c0 < j + 1; c0 += MD_CHUNK)
+        k_multi_axpy<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, std::min(MD_CHUNK, j + 1 - c0), dV + c0,
+                                                              w.hcol.p + c0, -1.0, wv);
+      KCHECK();
+      multidot<T>(n, j + 1, dV, wv, w.hsum.p, 0);
+      for (int c0 = 0; c0 < j + 1; c0 += MD_CHUNK)
+        k_multi_axpy<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, std::min(MD_CHUNK, j + 1 - c0), dV + c0,
+                                                              w.hsum.p + c0, -1.0, wv);
+      KCHECK();
+      k_dadd<<<1, 64, 0, st>>>(j + 1, w.hcol.p, w.hsum.p);
+      KCHECK();
+      flat_dot<T>(st, n, wv, wv, w.partial_flat.p, w.scal.p + 2);
+      k_givens<<<1, 1, 0, st>>>(j, m, w.H.p, w.cs.p, w.sn.p, w.g.p, w.hcol.p, w.scal.p + 2, w.scal.p + 3,
+                                w.scal.p + 4);
+      KCHECK();
+      k_scale_inv<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, w.scal.p + 3, wv, wv);
+      KCHECK();
+      CK(cudaMemcpyAsync(pin, w.scal.p + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+      sync();
+      ++total;
+      k = j + 1;
+      if (!std::isfinite(pin[0])) fail(FWI_E_NUMERIC, "non-finite residual in FGMRES");
+      if (pin[0] / bnorm <= tol) { conv = true; break; }
+    }
+    k_backsub<<<1, 1, 0, st>>>(k, m, w.H.p, w.g.p, w.y.p);
+    KCHECK();
+    for (int c0 = 0; c0 < k; c0 += MD_CHUNK)
+      k_multi_axpy<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, std::min(MD_CHUNK, k - c0), dZ + c0, w.y.p + c0,
+                                                            1.0, x);
+    KCHECK();
+    if (conv || total >= maxit) break;
+    // restart from r = rhs - M x
+    kkt_matvec<T>(x, w.tmp.p, eps, u);
+    k_axpby<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, 1.0, rhs, -1.0, w.tmp.p);
+    KCHECK();
+    r = w.tmp.p;
+    flat_dot<T>(st, n, r, r, w.partial_flat.p, w.scal.p);
+    CK(cudaMemcpyAsync(pin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    beta = std::sqrt(pin[0]);
+    if (beta / bnorm <= tol) { conv = true; break; }
+  }
+  if (iters) *iters += total;
+  return conv ? 0 : 1;
+}
+
+
+template <> const float2 *Ctx::u_T<float>() {
+  if (u_version32 != fwd_version) {
+    k_convert<double, float><<<grid_for(2 * F0, 256), 256, 0, st>>>(2 * F0, (const double *)u64.p, (float *)w32.u.p);
+    KCHECK();
+    u_version32 = fwd_version;
+  }
+  return w32.u.p;
+}
+template <> const double2 *Ctx::u_T<double>() { return u64.p; }
+
+// Per-block FP64-refined solve of A' x = rhs (cj = 1: A'^H): inner solves in
+// precision T on the normalised residual, update and residual in FP64, until
+// every block satisfies ||rhs - A' x|| <= fwd_tol ||rhs|| (Sec. 2, Au = f).
+template <typename T>
+int Ctx::refined_solve(const double2 *rhs, double2 *x, int cj, const fwi_opts &o, fwi_stats *stats) {
+  typedef typename cplx<T>::t T2;
+  ensure_work<T>(o);
+  Work<T> &w = work<T>();
+  LevelView<double> L64 = viewA<double>();
+  LevelView<T> LT = viewA<T>();
+  const int nt = L64.n_tiles;
+  rho64.alloc(F0);
+  CK(cudaMemsetAsync(x, 0, F0 * sizeof(double2), st));
+  CK(cudaMemcpyAsync(rho64.p, rhs, F0 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  std::vector<double> n0(B), nb(B), fac(B);
+  auto block_norms = [&](const double2 *v, std::vector<double> &out) {
+    block_dots<double>(1, v, v, nullptr, nullptr, nullptr, nullptr);
+    std::vector<double2> hp((size_t)nt * 3);
+    CK(cudaMemcpyAsync(hp.data(), partial.p, hp.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    sync();
+    for (int b = 0; b < B; ++b) {
+      double a = 0.0;
+      for (int t = lv[0].ht0[b]; t < lv[0].ht1[b]; ++t) a += hp[(size_t)t * 3].x;
+      out[b] = std::sqrt(a);
+    }
+  };
+  block_norms(rhs, n0);
+  int sweeps = 0;
+  int status = FWI_E_NOCONV;
+  T2 *rT = (T2 *)w.vin.p;
+  T2 *eT = (T2 *)w.zout.p;
+  const double inner_tol = sizeof(T) == 4 ? 1e-5 : std::max(o.fwd_tol * 0.1, 1e-15);
+  for (;;) {
+    block_norms(rho64.p, nb);
+    double worst = 0.0;
+    bool finite = true;
+    for (int b = 0; b < B; ++b) {
+      if (!std::isfinite(nb[b])) finite = false;
+      if (n0[b] > 0.0) worst = std::max(worst, nb[b] / n0[b]);
+    }
+    if (!finite) fail(FWI_E_NUMERIC, "non-finite residual in the forward/adjoint solve");
+    if (worst <= o.fwd_tol) { status = FWI_OK; break; }
+    if (sweeps >= o.max_fwd_refine) break;
+    for (int b = 0; b < B; ++b) fac[b] = nb[b] > 0.0 ? 1.0 / nb[b] : 0.0;
+    CK(cudaMemcpyAsync(blkfac.p, fac.data(), B * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_blk_scale<double, T, T><<<nt, TILE_THREADS, 0, st>>>(LT, (const double *)rho64.p, blkfac.p, (T *)rT, 0);
+    KCHECK();
+    long long cnt = 0;
+    inner_solve<T>(rT, eT, cj, o.fwd_iters, inner_tol, o, &cnt);
+    if (stats) stats->inner_iters += cnt;
+    CK(cudaMemcpyAsync(blkfac.p, nb.data(), B * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_blk_scale<T, double, T><<<nt, TILE_THREADS, 0, st>>>(LT, (const T *)eT, blkfac.p, (double *)x, 1);
+    KCHECK();
+    field_op<double>(FM_RESID, cj, 0.0, x, rhs, rho64.p, true, 0);
+    ++sweeps;
+  }
+  if (stats) stats->fwd_sweeps += sweeps;
+  return status;
+}
+
+// a2 + a3: forward wavefields of every block, predicted data, residuals, misfit.
+void Ctx::forward(const fwi_opts &o, fwi_stats *stats) {
+  build_hierarchy(o);
+  auto t0 = std::chrono::steady_clock::now();
+  u64.alloc(F0);
+  f64.alloc(F0);
+  f64.zero(st);
+  k_set_sources<<<grid_for(B, 128), 128, 0, st>>>(B, d_src_node.p, d_src_amp.p, f64.p);
+  KCHECK();
+  int rc = o.precision == FWI_C128 ? refined_solve<double>(f64.p, u64.p, 0, o, stats)
+                                   : refined_solve<float>(f64.p, u64.p, 0, o, stats);
+  ++fwd_version;
+  // receivers: q = Q u, r = d - q
+  int nrec = (int)rec_node.size();
+  q.alloc(std::max(1, nrec));
+  r.alloc(std::max(1, nrec));
+  std::vector<double2> dh(std::max(1, nrec), make_double2(0, 0));
+  bool have_d = true;
+  for (auto &I : inst) have_d = have_d && I.has_data;
+  DBuf<double2> dd;
+  if (have_d && nrec) {
+    // gather observed data per entry on the device-side order (copy per instance)
+    std::vector<long long> src_idx(nrec);
+    dd.alloc(nrec);
+    int e = 0;
+    for (int b = 0; b < B; ++b) {
+      Instance &I = inst[blk_inst[b]];
+      int k = blk_src[b], f = blk_freq[b];
+      for (int q2 = I.rec_off[k]; q2 < I.rec_off[k + 1]; ++q2, ++e) {
+        (void)f;
+      }
+    }
+    // device copy of each instance's data in entry order
+    e = 0;
+    for (int b = 0; b < B; ++b) {
+      Instance &I = inst[blk_inst[b]];
+      int k = blk_src[b], f = blk_freq[b];
+      int cnt = I.rec_off[k + 1] - I.rec_off[k];
+      if (cnt)
+        CK(cudaMemcpyAsync(dd.p + e, I.d.p + (long long)f * I.rec_total() + I.rec_off[k], cnt * sizeof(double2),
+                           cudaMemcpyDeviceToDevice, st));
+      e += cnt;
+    }
+  }
+  if (nrec) {
+    k_rec_residual<<<grid_for(nrec, 128, 1 << 20), 128, 0, st>>>(nrec, d_rec_node.p, u64.p, have_d ? dd.p : nullptr,
+                                                                 q.p, r.p, have_d ? 1 : 0);
+    KCHECK();
+  }
+  // misfit per instance
+  std::vector<int> e0(inst.size()), e1(inst.size());
+  {
+    int e = 0;
+    for (size_t i = 0; i < inst.size(); ++i) {
+      e0[i] = e;
+      for (int b = h_inst[i].blk0; b < h_inst[i].blk1; ++b) {
+        Instance &I = inst[i];
+        e += I.rec_off[blk_src[b] + 1] - I.rec_off[blk_src[b]];
+      }
+      e1[i] = e;
+    }
+  }
+  DBuf<int> de0, de1;
+  de0.upload(e0, st);
+  de1.upload(e1, st);
+  misfit_d.alloc(inst.size());
+  k_misfit<<<(int)inst.size(), 256, 0, st>>>(de0.p, de1.p, d_rec_w.p, r.p, misfit_d.p);
+  KCHECK();
+  misfit.assign(inst.size(), 0.0);
+  CK(cudaMemcpyAsync(misfit.data(), misfit_d.p, inst.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  sync();
+  have_fwd = true;
+  if (stats) {
+    stats->t_forward_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    double m = 0.0;
+    for (double v : misfit) m += v;
+    stats->misfit = m;
+  }
+  if (rc != FWI_OK) fail(FWI_E_NOCONV, "forward solve did not reach fwd_tol within max_fwd_refine sweeps");
+}
+
+// per-instance ||x||^2 of a packed FP64 vector -> host vector
+void Ctx::seg_norms(const double *x) {
+  const int nb = 64;
+  dim3 g(nb, (unsigned)h_segs.size());
+  k_seg_norm2<double><<<g, FLAT_THREADS, 0, st>>>(d_segs.p, x, seg_partial.p, nb);
+  KCHECK();
+}
+
+// ds (all instances' cores) = fac_i * (ctrl part of a packed FP64 vector)
+void Ctx::write_ctrl(const double *src_ctrl_dev, double *dst, int on_device, const double *fac) {
+  std::vector<SegDev> cs;
+  for (size_t i = 0; i < inst.size(); ++i)
+    cs.push_back(SegDev{h_inst[i].ctrl, h_inst[i].ctrl + (long long)inst[i].g.nx * inst[i].g.nz, (int)i});
+  DBuf<SegDev> dcs;
+  dcs.upload(cs, st);
+  DBuf<double> f, out;
+  std::vector<double> hf(fac, fac + inst.size());
+  f.upload(hf, st);
+  double *target = dst;
+  if (!on_device) { out.alloc(Nc); target = out.p; }
+  k_seg_scale<double, double><<<dim3(64, (unsigned)cs.size()), 256, 0, st>>>(dcs.p, src_ctrl_dev, f.p, target);
+  KCHECK();
+  if (!on_device) CK(cudaMemcpyAsync(dst, out.p, Nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+  sync();
+}
+
+// a4-a8: the KKT solve with the block-triangular preconditioner, FGMRES and FP64 refinement.
+int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
+  if (!have_fwd) fail(FWI_E_INVAL, "fwi_kkt_solve needs fwi_forward at the current model");
+  bool have_d = true;
+  for (auto &I : inst) have_d = have_d && I.has_data;
+  if (!have_d) fail(FWI_E_INVAL, "observed data missing");
+  if (!(o.eps > 0.0)) fail(FWI_E_INVAL, "eps must be > 0");
+  auto t0 = std::chrono::steady_clock::now();
+  b64.alloc(nkkt); xi64.alloc(nkkt); rho_k64.alloc(nkkt);
+  b64.zero(st);
+  // b_u = Q^T W^T W r (FP64 field in the du slot)
+  int nrec = (int)rec_node.size();
+  if (n_unique)
+    k_rec_scatter<<<grid_for(n_unique, 128, 1 << 20), 128, 0, st>>>(n_unique, d_unode.p, d_uoff.p, d_uidx.p, d_rec_w.p,
+                                                                    r.p, (double2 *)b64.p);
+  KCHECK();
+  (void)nrec;
+  {
+    std::vector<const double *> sp;
+    std::vector<double> gr;
+    for (auto &I : inst) { sp.push_back(I.s.p); gr.push_back(I.gamma_ref); }
+    DBuf<const double *> dsp;
+    dsp.upload(sp, st);
+    inst_gref.upload(gr, st);
+    long long mx = 0;
+    for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
+    k_ctrl_rhs<<<dim3(grid_for(mx, 256), (unsigned)inst.size()), 256, 0, st>>>(d_inst.p, dsp.p, inst_gref.p, o.eps,
+                                                                              o.include_Ls_n, b64.p + 4 * F0);
+    KCHECK();
+    sync();
+  }
+  const int n_inst = (int)inst.size();
+  auto inst_norms = [&](const double *x, std::vector<double> &out) {
+    seg_norms(x);
+    std::vector<double> hp(h_segs.size() * 64);
+    CK(cudaMemcpyAsync(hp.data(), seg_partial.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    out.assign(n_inst, 0.0);
+    for (size_t sgi = 0; sgi < h_segs.size(); ++sgi)
+      for (int q2 = 0; q2 < 64; ++q2) out[h_segs[sgi].inst] += hp[sgi * 64 + q2];
+    for (auto &v : out) v = std::sqrt(v);
+  };
+  std::vector<double> bn, rn;
+  inst_norms(b64.p, bn);
+  CK(cudaMemsetAsync(xi64.p, 0, nkkt * sizeof(double), st));
+  CK(cudaMemcpyAsync(rho_k64.p, b64.p, nkkt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const bool c128 = o.precision == FWI_C128;
+  if (c128) ensure_krylov<double>(o); else ensure_krylov<float>(o);
+  int outer = 0, sweeps = 0;
+  long long inner = 0;
+  double worst = 0.0;
+  int status = FWI_E_NOCONV;
+  for (;;) {
+    inst_norms(rho_k64.p, rn);
+    worst = 0.0;
+    for (int i = 0; i < n_inst; ++i) {
+      if (!std::isfinite(rn[i])) fail(FWI_E_NUMERIC, "non-finite KKT residual");
+      if (bn[i] > 0.0) worst = std::max(worst, rn[i] / bn[i]);
+    }
+    if (worst <= o.tol) { status = FWI_OK; break; }
+    if (sweeps >= o.max_refine || outer >= o.max_outer) break;
+    std::vector<double> fac(n_inst), back(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+      fac[i] = rn[i] > 0.0 ? 1.0 / rn[i] : 0.0;
+      back[i] = rn[i];
+    }
+    inst_fac.upload(fac, st);
+    dim3 g(64, (unsigned)h_segs.size());
+    int left = o.max_outer - outer;
+    if (c128) {
+      Work<double> &w = w64;
+      k_seg_scale<double, double><<<g, 256, 0, st>>>(d_segs.p, rho_k64.p, inst_fac.p, w.rhs.p);
+      KCHECK();
+      fgmres<double>(w.rhs.p, w.sol.p, std::max(o.tol * 0.5, 1e-14), left, o.eps, o, &outer, &inner, u_T<double>());
+      inst_fac.upload(back, st);
+      k_seg_axpy<double><<<g, 256, 0, st>>>(d_segs.p, w.sol.p, inst_fac.p, xi64.p);
+      KCHECK();
+    } else {
+      Work<float> &w = w32;
+      k_seg_scale<double, float><<<g, 256, 0, st>>>(d_segs.p, rho_k64.p, inst_fac.p, w.rhs.p);
+      KCHECK();
+      fgmres<float>(w.rhs.p, w.sol.p, o.sweep_tol, left, o.eps, o, &outer, &inner, u_T<float>());
+      inst_fac.upload(back, st);
+      k_seg_axpy<float><<<g, 256, 0, st>>>(d_segs.p, w.sol.p, inst_fac.p, xi64.p);
+      KCHECK();
+    }
+    // rho = b - M xi in FP64 (c128 matvec with the FP64 wavefields)
+    kkt_matvec<double>(xi64.p, rho_k64.p, o.eps, u64.p);
+    k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nkkt, 1.0, b64.p, -1.0, rho_k64.p);
+    KCHECK();
+    ++sweeps;
+  }
+  if (stats) {
+    stats->outer_iters += outer;
+    stats->refinements += sweeps;
+    stats->inner_iters += inner;
+    stats->rel_res = worst;
+    stats->t_solve_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+int Ctx::gradient(const fwi_opts &o, double *misfit_out, double *grad, int on_device, fwi_stats *stats) {
+  forward(o, stats);
+  bool have_d = true;
+  for (auto &I : inst) have_d = have_d && I.has_data;
+  if (!have_d) fail(FWI_E_INVAL, "observed data missing");
+  // adjoint right-hand side Q^T W^T W r and lambda' = A'^{-H} rhs
+  DBuf<double2> rhs, lam;
+  rhs.alloc(F0); lam.alloc(F0);
+  rhs.zero(st);
+  if (n_unique)
+    k_rec_scatter<<<grid_for(n_unique, 128, 1 << 20), 128, 0, st>>>(n_unique, d_unode.p, d_uoff.p, d_uidx.p, d_rec_w.p,
+                                                                    r.p, rhs.p);
+  KCHECK();
+  int rc = o.precision == FWI_C128 ? refined_solve<double>(rhs.p, lam.p, 1, o, stats)
+                                   : refined_solve<float>(rhs.p, lam.p, 1, o, stats);
+  DBuf<double> g;
+  double *target = grad;
+  if (!on_device) { g.alloc(Nc); target = g.p; }
+  long long mx = 0;
+  for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
+  dim3 gr((unsigned)((mx + 127) / 128), (unsigned)inst.size());
+  k_coupling_reduce<double, double><<<gr, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfG.p, u64.p,
+                                                                 lam.p, nullptr, 0.0, 2, target);
+  KCHECK();
+  if (!on_device) CK(cudaMemcpyAsync(grad, g.p, Nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+  sync();
+  if (misfit_out)
+    for (size_t i = 0; i < inst.size(); ++i) misfit_out[i] = misfit[i];
+  if (rc != FWI_OK) fail(FWI_E_NOCONV, "adjoint solve did not reach fwd_tol");
+  return FWI_OK;
+}
+
+int Ctx::newton_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  build_hierarchy(o);
+  if (stats) stats->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  forward(o, stats);
+  int rc = kkt_solve(o, stats);
+  // ds = gamma_ref * ds~ ; s += ds
+  std::vector<double> gr;
+  for (auto &I : inst) gr.push_back(I.gamma_ref);
+  DBuf<double> dsd;
+  dsd.alloc(Nc);
+  write_ctrl(xi64.p + 4 * F0, dsd.p, 1, gr.data());
+  std::vector<double *> sp;
+  for (auto &I : inst) sp.push_back(I.s.p);
+  DBuf<double *> dsp;
+  dsp.upload(sp, st);
+  long long mx = 0;
+  for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
+  k_update_model<<<dim3(grid_for(mx, 256), (unsigned)inst.size()), 256, 0, st>>>(d_inst.p, dsp.p, dsd.p);
+  KCHECK();
+  if (ds) {
+    if (on_device) CK(cudaMemcpyAsync(ds, dsd.p, Nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else CK(cudaMemcpyAsync(ds, dsd.p, Nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  sync();
+  ++model_version;
+  have_fwd = false;
+  return rc;
+}
+
+}  // namespace fwi
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+using fwi::Ctx;
+using fwi::Err;
+
+struct fwi_ctx {
+  Ctx c;
+};
+
+static std::string g_create_error;
+
+#define API_BEGIN(ctx)                       \
+  if (!(ctx)) return FWI_E_INVAL;            \
+  (ctx)->c.err.clear();                      \
+  try {
+#define API_END(ctx)                         \
+  }                                          \
+  catch (const Err &e) {                     \
+    (ctx)->c.err = e.msg;                    \
+    return e.code;                           \
+  }                                          \
+  catch (const std::exception &e) {          \
+    (ctx)->c.err = e.what();                 \
+    return FWI_E_INVAL;                      \
+  }
+
+static int check_opts(const fwi_opts *o) {
+  if (!o) return 0;
+  if (o->restart < 1 || o->restart > 200 || o->nu1 < 0 || o->nu2 < 0 || o->mg_cycle < 1 || o->mg_cycle > 2 ||
+      o->inner_iters < 1 || o->fwd_iters < 1 || !(o->tol > 0.0) || o->max_outer < 1 ||
+      (o->precision != FWI_C128 && o->precision != FWI_C64_REFINE))
+    return 0;
+  return 1;
+}
+
+extern "C" {
+
+void fwi_default_opts(fwi_opts *o) {
+  if (!o) return;
+  o->precision = FWI_C64_REFINE;
+  o->eps = 1e-3;
+  o->include_Ls_n = 1;
+  o->tol = 1e-6;
+  o->restart = 30;
+  o->max_outer = 600;
+  o->sweep_tol = 1e-3;
+  o->max_refine = 8;
+  o->inner_iters = 8;
+  o->inner_tol = 0.0;
+  o->mg_cycle = 2;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->omega_jac = 0.5;
+  o->shift_beta = 0.5;
+  o->sigma_cap = 1.0;
+  o->mg_levels = 0;
+  o->fwd_tol = 1e-10;
+  o->fwd_iters = 60;
+  o->max_fwd_refine = 10;
+  o->use_graph = 1;
+}
+
+int fwi_create(fwi_ctx **out, int n_instances, const fwi_grid *grids, void *cuda_stream) {
+  if (!out) return FWI_E_INVAL;
+  *out = nullptr;
+  g_create_error.clear();
+  if (n_instances < 1 || !grids) { g_create_error = "n_instances >= 1 and grids required"; return FWI_E_INVAL; }
+  for (int i = 0; i < n_instances; ++i) {
+    const fwi_grid &g = grids[i];
+    if (g.nx < 2 || g.nz < 2 || g.npml < 0 || !(g.h > 0.0) ||
+        (g.npml > 0 && (!(g.pml_c > 0.0) || !(g.pml_R > 0.0) || !(g.pml_R < 1.0)))) {
+      g_create_error = "invalid grid of instance " + std::to_string(i);
+      return FWI_E_INVAL;
+    }
+  }
+  fwi_ctx *c = new (std::nothrow) fwi_ctx;
+  if (!c) return FWI_E_NOMEM;
+  c->c.st = (cudaStream_t)cuda_stream;
+  c->c.inst.resize(n_instances);
+  for (int i = 0; i < n_instances; ++i) {
+    fwi::Instance &I = c->c.inst[i];
+    I.g = grids[i];
+    I.Nx = grids[i].nx + 2 * grids[i].npml;
+    I.Nz = grids[i].nz + 2 * grids[i].npml;
+  }
+  *out = c;
+  return FWI_OK;
+}
+
+int fwi_set_survey(fwi_ctx *ctx, int inst, int n_freq, const double *freq_hz, int n_src, const int *src_ix,
+                   const int *src_iz, const double *src_amp, const int *rec_offsets, const int *rec_ix,
+                   const int *rec_iz, const double *rec_weight) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  if (inst < 0 || inst >= (int)c.inst.size()) fwi::fail(FWI_E_INVAL, "instance index out of range");
+  if (n_freq < 1 || n_src < 1 || !freq_hz || !src_ix || !src_iz || !src_amp || !rec_offsets)
+    fwi::fail(FWI_E_INVAL, "bad survey arguments");
+  fwi::Instance &I = c.inst[inst];
+  for (int f = 0; f < n_freq; ++f)
+    if (!(freq_hz[f] > 0.0)) fwi::fail(FWI_E_INVAL, "frequencies must be > 0");
+  for (int k = 0; k < n_src; ++k)
+    if (src_ix[k] < 0 || src_ix[k] >= I.g.nx || src_iz[k] < 0 || src_iz[k] >= I.g.nz)
+      fwi::fail(FWI_E_INVAL, "source outside the core");
+  if (rec_offsets[0] != 0) fwi::fail(FWI_E_INVAL, "rec_offsets[0] must be 0");
+  for (int k = 0; k < n_src; ++k)
+    if (rec_offsets[k + 1] < rec_offsets[k]) fwi::fail(FWI_E_INVAL, "rec_offsets must be non-decreasing");
+  int nr = rec_offsets[n_src];
+  if (nr > 0 && (!rec_ix || !rec_iz)) fwi::fail(FWI_E_INVAL, "receiver arrays missing");
+  for (int e = 0; e < nr; ++e)
+    if (rec_ix[e] < 0 || rec_ix[e] >= I.g.nx || rec_iz[e] < 0 || rec_iz[e] >= I.g.nz)
+      fwi::fail(FWI_E_INVAL, "receiver outside the core");
+  I.freqs.assign(freq_hz, freq_hz + n_freq);
+  I.n_src = n_src;
+  I.src_ix.assign(src_ix, src_ix + n_src);
+  I.src_iz.assign(src_iz, src_iz + n_src);
+  I.src_amp.assign(src_amp, src_amp + 2 * n_src);
+  I.rec_off.assign(rec_offsets, rec_offsets + n_src + 1);
+  I.rec_ix.assign(rec_ix, rec_ix + nr);
+  I.rec_iz.assign(rec_iz, rec_iz + nr);
+  I.rec_w.assign(nr, 1.0);
+  if (rec_weight) I.rec_w.assign(rec_weight, rec_weight + nr);
+  I.has_survey = true;
+  I.has_data = false;
+  c.layout_ok = false;
+  c.have_fwd = false;
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_set_model(fwi_ctx *ctx, int inst, const double *gamma_core, double gamma_ref, int on_device) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  if (inst < 0 || inst >= (int)c.inst.size() || !gamma_core) fwi::fail(FWI_E_INVAL, "bad model arguments");
+  fwi::Instance &I = c.inst[inst];
+  size_t n = (size_t)I.g.nx * I.g.nz;
+  std::vector<double> h(n);
+  if (on_device) {
+    CK(cudaMemcpyAsync(h.data(), gamma_core, n * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+  } else {
+    std::memcpy(h.data(), gamma_core, n * sizeof(double));
+  }
+  double sum = 0.0;
+  for (double v : h) {
+    if (!std::isfinite(v) || !(v > 0.0)) fwi::fail(FWI_E_NUMERIC, "gamma must be finite and > 0");
+    sum += v;
+  }
+  I.s.upload(h, c.st);
+  if (!I.has_model) {
+    I.gamma_ref = gamma_ref > 0.0 ? gamma_ref : sum / (double)n;
+    I.layer.alloc((size_t)I.Nx * I.Nz);
+    fwi::k_gamma_pad<<<fwi::grid_for((long long)I.Nx * I.Nz, 256), 256, 0, c.st>>>(I.s.p, I.Nx, I.Nz, I.g.npml,
+                                                                                   I.g.nx, I.g.nz, I.layer.p);
+    KCHECK();
+  } else if (gamma_ref > 0.0) {
+    I.gamma_ref = gamma_ref;
+  }
+  c.sync();
+  bool first = !I.has_model;
+  I.has_model = true;
+  ++c.model_version;
+  c.have_fwd = false;
+  if (first) c.layout_ok = false;
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_get_model(fwi_ctx *ctx, int inst, double *gamma_core) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  if (inst < 0 || inst >= (int)c.inst.size() || !gamma_core || !c.inst[inst].has_model)
+    fwi::fail(FWI_E_INVAL, "bad arguments or no model");
+  fwi::Instance &I = c.inst[inst];
+  CK(cudaMemcpyAsync(gamma_core, I.s.p, (size_t)I.g.nx * I.g.nz * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  c.sync();
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_set_observed(fwi_ctx *ctx, int inst, const double *d, int on_device) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  if (inst < 0 || inst >= (int)c.inst.size() || !d) fwi::fail(FWI_E_INVAL, "bad data arguments");
+  fwi::Instance &I = c.inst[inst];
+  if (!I.has_survey) fwi::fail(FWI_E_INVAL, "set the survey first");
+  size_t n = I.freqs.size() * (size_t)I.rec_total();
+  I.d.alloc(std::max<size_t>(n, 1));
+  if (n) CK(cudaMemcpyAsync(I.d.p, d, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.st));
+  c.sync();
+  I.has_data = true;
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_forward(fwi_ctx *ctx, const fwi_opts *opts, double *d_pred, double *misfit, fwi_stats *stats) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid options");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  c.forward(o, stats);
+  if (d_pred) {
+    // entries are in block order; write [inst][f][rec_total]
+    std::vector<double2> hq(std::max<size_t>(1, c.rec_node.size()));
+    if (!c.rec_node.empty())
+      CK(cudaMemcpyAsync(hq.data(), c.q.p, c.rec_node.size() * sizeof(double2), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    size_t e = 0, base = 0;
+    for (size_t i = 0; i < c.inst.size(); ++i) {
+      fwi::Instance &I = c.inst[i];
+      for (size_t f = 0; f < I.freqs.size(); ++f)
+        for (int k = 0; k < I.n_src; ++k)
+          for (int q = I.rec_off[k]; q < I.rec_off[k + 1]; ++q, ++e) {
+            size_t o2 = base + f * I.rec_total() + q;
+            d_pred[2 * o2] = hq[e].x;
+            d_pred[2 * o2 + 1] = hq[e].y;
+          }
+      base += I.freqs.size() * I.rec_total();
+    }
+  }
+  if (misfit)
+    for (size_t i = 0; i < c.inst.size(); ++i) misfit[i] = c.misfit[i];
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_get_wavefields(fwi_ctx *ctx, double *u_device) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  if (!c.have_fwd || !u_device) fwi::fail(FWI_E_INVAL, "no forward wavefields");
+  CK(cudaMemcpyAsync(u_device, c.u64.p, c.F0 * sizeof(double2), cudaMemcpyDeviceToDevice, c.st));
+  c.sync();
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_gradient(fwi_ctx *ctx, const fwi_opts *opts, double *misfit, double *grad, int on_device, fwi_stats *stats) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!check_opts(&o) || !grad) fwi::fail(FWI_E_INVAL, "invalid arguments");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  return c.gradient(o, misfit, grad, on_device, stats);
+  API_END(ctx)
+}
+
+int fwi_kkt_solve(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device, fwi_stats *stats) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid options");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  c.build_hierarchy(o);
+  int rc = c.kkt_solve(o, stats);
+  if (ds) {
+    std::vector<double> gr;
+    for (auto &I : c.inst) gr.push_back(I.gamma_ref);
+    c.write_ctrl(c.xi64.p + 4 * c.F0, ds, on_device, gr.data());
+  }
+  if (rc != FWI_OK) c.err = "KKT solve stopped at the iteration cap";
+  return rc;
+  API_END(ctx)
+}
+
+int fwi_newton_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device, fwi_stats *stats) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid options");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  int rc = c.newton_step(o, ds, on_device, stats);
+  if (rc != FWI_OK) c.err = "KKT solve stopped at the iteration cap";
+  return rc;
+  API_END(ctx)
+}
+
+int fwi_apply_helmholtz(fwi_ctx *ctx, const void *x, void *y, int adjoint, int precision) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  if (!x || !y) fwi::fail(FWI_E_INVAL, "null buffer");
+  fwi_opts o;
+  fwi_default_opts(&o);
+  c.build_hierarchy(o);
+  if (precision == FWI_C128)
+    c.field_op<double>(fwi::FM_APPLY, adjoint ? 1 : 0, 0.0, (const double2 *)x, nullptr, (double2 *)y, true, 0);
+  else if (precision == FWI_C64_REFINE)
+    c.field_op<float>(fwi::FM_APPLY, adjoint ? 1 : 0, 0.0f, (const float2 *)x, nullptr, (float2 *)y, true, 0);
+  else fwi::fail(FWI_E_INVAL, "bad precision");
+  c.sync();
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_apply_kkt(fwi_ctx *ctx, const fwi_opts *opts, const void *xi, void *y, int precision) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!xi || !y) fwi::fail(FWI_E_INVAL, "null buffer");
+  if (!c.have_fwd) fwi::fail(FWI_E_INVAL, "fwi_apply_kkt needs fwi_forward");
+  c.build_hierarchy(o);
+  if (precision == FWI_C128) c.kkt_matvec<double>((const double *)xi, (double *)y, o.eps, c.u_T<double>());
+  else if (precision == FWI_C64_REFINE) {
+    c.ensure_work<float>(o);
+    c.kkt_matvec<float>((const float *)xi, (float *)y, o.eps, c.u_T<float>());
+  } else fwi::fail(FWI_E_INVAL, "bad precision");
+  c.sync();
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_apply_precond(fwi_ctx *ctx, const fwi_opts *opts, const void *v, void *z, int precision) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!v || !z || !check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid arguments");
+  if (!c.have_fwd) fwi::fail(FWI_E_INVAL, "fwi_apply_precond needs fwi_forward");
+  c.build_hierarchy(o);
+  long long cnt = 0;
+  if (precision == FWI_C128) {
+    c.ensure_work<double>(o);
+    c.precond<double>((const double *)v, (double *)z, o, &cnt);
+  } else if (precision == FWI_C64_REFINE) {
+    c.ensure_work<float>(o);
+    c.u_T<float>();
+    c.precond<float>((const float *)v, (float *)z, o, &cnt);
+  } else fwi::fail(FWI_E_INVAL, "bad precision");
+  c.sync();
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_inner_solve(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int adjoint, int precision) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!b || !x || !check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid arguments");
+  c.build_hierarchy(o);
+  int iters = o.inner_iters;
+  long long cnt = 0;
+  if (precision == FWI_C128) {
+    c.ensure_work<double>(o);
+    c.inner_solve<double>((const double2 *)b, (double2 *)x, adjoint ? 1 : 0, iters, o.inner_tol, o, &cnt);
+  } else if (precision == FWI_C64_REFINE) {
+    c.ensure_work<float>(o);
+    c.inner_solve<float>((const float2 *)b, (float2 *)x, adjoint ? 1 : 0, iters, o.inner_tol, o, &cnt);
+  } else fwi::fail(FWI_E_INVAL, "bad precision");
+  c.sync();
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_mg_cycle(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int precision) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!b || !x || !check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid arguments");
+  c.build_hierarchy(o);
+  if (precision == FWI_C128) {
+    c.ensure_work<double>(o);
+    c.mg_cycle<double>((const double2 *)b, (double2 *)x, 0, o);
+  } else if (precision == FWI_C64_REFINE) {
+    c.ensure_work<float>(o);
+    c.mg_cycle<float>((const float2 *)b, (float2 *)x, 0, o);
+  } else fwi::fail(FWI_E_INVAL, "bad precision");
+  c.sync();
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  if (!info) fwi::fail(FWI_E_INVAL, "null info");
+  c.build_layout();
+  info->n_instances = (int)c.inst.size();
+  info->n_blocks = c.B;
+  info->field_elems = c.F0;
+  info->ctrl_elems = c.Nc;
+  info->kkt_elems = c.nkkt;
+  return FWI_OK;
+  API_END(ctx)
+}
+
+const char *fwi_last_error(const fwi_ctx *ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->c.err.c_str();
+}
+
+void fwi_destroy(fwi_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->c.st);
+  delete ctx;
+}
+
+}  // extern "C"
