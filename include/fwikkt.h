@@ -114,9 +114,12 @@ typedef struct {
 void fwi_default_opts(fwi_opts *o);
 
 /* Create a context with n_instances independent problems on the current CUDA
- * device.  grids: host array [n_instances].  cuda_stream: a cudaStream_t (NULL =
- * legacy default stream) on which all work is queued.  *out receives the
- * context (NULL on failure).  Returns FWI_E_INVAL for bad grid values. */
+ * device.  grids: host array [n_instances].  cuda_stream: a cudaStream_t on
+ * which all work is queued; NULL makes the context create a private blocking
+ * stream (ordered with the legacy default stream) on first device use, because
+ * the legacy stream cannot be captured into a CUDA graph.  *out receives the
+ * context (NULL on failure).  Makes no CUDA call.  Returns FWI_E_INVAL for bad
+ * grid values. */
 int fwi_create(fwi_ctx **out, int n_instances, const fwi_grid *grids, void *cuda_stream);
 
 /* Sources and receivers of one instance (Sec. 2: point sources f_k, receivers

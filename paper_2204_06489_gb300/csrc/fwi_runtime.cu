@@ -198,9 +198,11 @@ struct Ctx {
   double *pin = nullptr;  // pinned scalars
   int *pinflag = nullptr;
 
+  bool own_stream = false;
   ~Ctx() {
     if (pin) cudaFreeHost(pin);
     if (pinflag) cudaFreeHost(pinflag);
+    if (own_stream && st) cudaStreamDestroy(st);
   }
 
   template <typename T> Work<T> &work();
@@ -227,8 +229,10 @@ struct Ctx {
                                         const typename cplx<T>::t *a1, const typename cplx<T>::t *b1,
                                         const typename cplx<T>::t *a2, const typename cplx<T>::t *b2);
   template <typename T> void kkt_matvec(const T *xi, T *y, double eps, const typename cplx<T>::t *u);
-  template <typename T> void precond(const T *v, T *z, const fwi_opts &o, long long *count);
-  template <typename T> void precond_any(const T *v, T *z, const fwi_opts &o, long long *count);
+  template <typename T> void precond(const T *v, T *z, const fwi_opts &o, long long *count,
+                                     const typename cplx<T>::t *u);
+  template <typename T> void precond_any(const T *v, T *z, const fwi_opts &o, long long *count,
+                                         const typename cplx<T>::t *u);
   template <typename T> int fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi_opts &o,
                                    int *iters, long long *inner, const typename cplx<T>::t *u);
   template <typename T> void multidot(long long n, int nv, T *const *dV, const T *w, double *out, int acc);
@@ -278,6 +282,12 @@ static int auto_levels(int Nx, int Nz, int max_nodes = 256, int min_dim = 3) {
 
 void Ctx::build_layout() {
   if (layout_ok) return;
+  if (!st) {
+    // the legacy default stream cannot be captured into a CUDA graph: use a
+    // private blocking stream (it still orders with the legacy default stream)
+    CK(cudaStreamCreate(&st));
+    own_stream = true;
+  }
   for (size_t i = 0; i < inst.size(); ++i)
     if (!inst[i].has_survey || !inst[i].has_model) fail(FWI_E_INVAL, "every instance needs a survey and a model");
   B = 0; F0 = 0; Nc = 0;
@@ -779,7 +789,7 @@ void Ctx::kkt_matvec(const T *xi, T *y, double eps, const typename cplx<T>::t *u
 }
 
 template <typename T>
-void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count) {
+void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count, const typename cplx<T>::t *u) {
   typedef typename cplx<T>::t T2;
   Work<T> &w = work<T>();
   const T2 *v1 = (const T2 *)v;
@@ -797,11 +807,11 @@ void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count) {
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
   dim3 g((unsigned)((mx + 127) / 128), (unsigned)inst.size());
-  k_coupling_reduce<T, T><<<g, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfK.p, w.u.p, zl, v2, o.eps, 1, zs);
+  k_coupling_reduce<T, T><<<g, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfK.p, u, zl, v2, o.eps, 1, zs);
   KCHECK();
   // z_u = A'^{-1} (v3 + P~ z_s)
   LevelView<T> L = viewA<T>();
-  k_coupling_scatter<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, d_inst.p, cfK.p, w.u.p, v3, zs, w.t0b.p);
+  k_coupling_scatter<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, d_inst.p, cfK.p, u, v3, zs, w.t0b.p);
   KCHECK();
   inner_solve<T>(w.t0b.p, zu, 0, iters, tol, o, count);
 }
@@ -809,20 +819,20 @@ void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count) {
 // Preconditioner application, replayed from a CUDA graph when requested (the
 // graph reads w.vin and writes w.zout).
 template <typename T>
-void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count) {
+void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, const typename cplx<T>::t *u) {
   Work<T> &w = work<T>();
   bool graphable = o.use_graph && !(o.inner_tol > 0.0);
-  if (!graphable) { precond<T>(v, z, o, count); return; }
+  if (!graphable) { precond<T>(v, z, o, count, u); return; }
   char key[256];
-  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%.17g|%.17g|%.17g", hier_key.c_str(), o.inner_iters, o.mg_cycle,
-           o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta);
+  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p", hier_key.c_str(), o.inner_iters, o.mg_cycle,
+           o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta, (const void *)u);
   if (w.graph_key != key) {
     if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
     cudaGraph_t gr;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     long long dummy = 0;
     try {
-      precond<T>(w.vin.p, w.zout.p, o, &dummy);
+      precond<T>(w.vin.p, w.zout.p, o, &dummy, u);
     } catch (...) {
       cudaStreamEndCapture(st, &gr);
       throw;
@@ -895,7 +905,7 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
       T *vj = w.V.p + (size_t)j * n;
       T *zj = w.Z.p + (size_t)j * n;
       T *wv = w.V.p + (size_t)(j + 1) * n;
-      precond_any<T>(vj, zj, o, inner);
+      precond_any<T>(vj, zj, o, inner, u);
       kkt_matvec<T>(zj, wv, eps, u);
       // classical Gram-Schmidt, twice
       multidot<T>(n, j + 1, dV, wv, w.hcol.p, 0);
@@ -1622,11 +1632,10 @@ int fwi_apply_precond(fwi_ctx *ctx, const fwi_opts *opts, const void *v, void *z
   long long cnt = 0;
   if (precision == FWI_C128) {
     c.ensure_work<double>(o);
-    c.precond<double>((const double *)v, (double *)z, o, &cnt);
+    c.precond<double>((const double *)v, (double *)z, o, &cnt, c.u_T<double>());
   } else if (precision == FWI_C64_REFINE) {
     c.ensure_work<float>(o);
-    c.u_T<float>();
-    c.precond<float>((const float *)v, (float *)z, o, &cnt);
+    c.precond<float>((const float *)v, (float *)z, o, &cnt, c.u_T<float>());
   } else fwi::fail(FWI_E_INVAL, "bad precision");
   c.sync();
   return FWI_OK;
@@ -1696,7 +1705,9 @@ const char *fwi_last_error(const fwi_ctx *ctx) {
 
 void fwi_destroy(fwi_ctx *ctx) {
   if (!ctx) return;
-  cudaStreamSynchronize(ctx->c.st);
+  bool touched = ctx->c.pin != nullptr;
+  for (auto &I : ctx->c.inst) touched = touched || I.has_model;
+  if (touched) cudaStreamSynchronize(ctx->c.st);
   delete ctx;
 }
 

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle, element by
+element, on seeded inputs that span several row tiles and ragged batches of
+two different grids.  Tolerances: complex128 kernels 1e-10 relative (rounding
+order only), complex64 kernels 2e-5 relative (single-precision stencil
+arithmetic on O(1) entries), wavefields 1e-5 (the stated target), KKT relative
+residual 1e-6 and model update 1e-5 against the direct solve."""
+import numpy as np
+import pytest
+
+import fwi_inputs as FI
+from oracle import fwi, kkt, krylov, mg
+from oracle import grid as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _workloads():
+    a = FI.tiny_workload(seed=0)
+    b = FI.micro_workload(seed=1, nx=37, nz=23, npml=6, n_src=3, n_rec=5, freq=4.0)
+    b.survey.freqs_hz = [4.0, 6.5]
+    return [a, b]
+
+
+@pytest.fixture(scope="module")
+def setup(lib):
+    import paper_2204_06489_gb300 as P
+    wls = _workloads()
+    f = P.from_workload(wls)
+    probs = [fwi.Problem.create(w.grid, w.survey, w.gamma_start) for w in wls]
+    d_obs = []
+    for i, (w, p) in enumerate(zip(wls, probs)):
+        d = fwi.sample(p, fwi.forward(p, w.gamma_true.ravel()))
+        d_obs.append(d)
+        nf, ns = w.survey.n_freq, w.survey.n_src
+        arr = np.zeros((nf, int(w.survey.rec_offsets[-1])), dtype=complex)
+        for b in range(p.n_blocks):
+            k = p.block_src(b)
+            arr[p.block_freq(b), w.survey.rec_offsets[k]:w.survey.rec_offsets[k + 1]] = d[b]
+        f.set_observed(i, arr)
+    return P, f, wls, probs, d_obs
+
+
+def _split(wls, probs, field):
+    """Field (all blocks) -> list per instance of [B_i, N_i] arrays."""
+    out, o = [], 0
+    for w, p in zip(wls, probs):
+        Nz, Nx = G.padded_shape(w.grid)
+        n = p.n_blocks * Nz * Nx
+        out.append(field[o:o + n].reshape(p.n_blocks, Nz * Nx))
+        o += n
+    return out
+
+
+def _rand_field(n, seed, dtype=torch.complex128):
+    g = np.random.default_rng(seed)
+    z = g.standard_normal(n) + 1j * g.standard_normal(n)
+    return torch.from_numpy(z).to(dtype).cuda(), z
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+@pytest.mark.parametrize("prec,tol", [(torch.complex128, 1e-12), (torch.complex64, 2e-6)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_helmholtz_operator(setup, prec, tol, adjoint):
+    P, f, wls, probs, _ = setup
+    lay = f.layout()
+    xt, x = _rand_field(lay["field_elems"], 3, prec)
+    y = f.apply_helmholtz(xt, adjoint=adjoint).cpu().numpy().astype(np.complex128)
+    xs = _split(wls, probs, x if prec == torch.complex128 else xt.cpu().numpy().astype(complex))
+    ys = _split(wls, probs, y)
+    for i, (w, p) in enumerate(zip(wls, probs)):
+        for b in range(p.n_blocks):
+            A = p.operator(w.gamma_start.ravel(), p.block_freq(b))
+            ref = np.conj(A @ np.conj(xs[i][b])) if adjoint else A @ xs[i][b]
+            assert _rel(ys[i][b], ref) < tol, (i, b, _rel(ys[i][b], ref))
+
+
+def test_adjoint_identity(setup):
+    """<A u, v> = <u, A^H v> with the CUDA operator (complex128)."""
+    P, f, wls, probs, _ = setup
+    n = f.layout()["field_elems"]
+    u, _ = _rand_field(n, 4)
+    v, _ = _rand_field(n, 5)
+    lhs = torch.vdot(v, f.apply_helmholtz(u)).item()
+    rhs = torch.vdot(f.apply_helmholtz(v, adjoint=True), u).item()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def _oracle_hier(P, w, p, fidx, opts):
+    return mg.Hierarchy(w.grid, p.omegas[fidx], p.gamma_pad(w.gamma_start.ravel()), shift=opts.shift_beta,
+                        nu1=opts.nu1, nu2=opts.nu2, wj=opts.omega_jac, cycle=opts.mg_cycle,
+                        sigma_cap=opts.sigma_cap)
+
+
+@pytest.mark.parametrize("cycle", [1, 2])
+def test_multigrid_cycle(setup, cycle):
+    P, f, wls, probs, _ = setup
+    opts = P.default_opts(mg_cycle=cycle)
+    n = f.layout()["field_elems"]
+    bt, b = _rand_field(n, 6)
+    x = f.mg_cycle(bt, opts).cpu().numpy()
+    bs, xs = _split(wls, probs, b), _split(wls, probs, x)
+    for i, (w, p) in enumerate(zip(wls, probs)):
+        hs = {}
+        for blk in range(p.n_blocks):
+            fi = p.block_freq(blk)
+            if fi not in hs:
+                hs[fi] = _oracle_hier(P, w, p, fi, opts)
+            ref = hs[fi].vcycle(bs[i][blk])
+            assert _rel(xs[i][blk], ref) < 1e-10, (i, blk, _rel(xs[i][blk], ref))
+    x32 = f.mg_cycle(bt.to(torch.complex64), opts).cpu().numpy().astype(complex)
+    assert _rel(x32, x) < 1e-4
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_inner_solve(setup, adjoint):
+    """Batched BiCGStab + multigrid, 6 iterations, complex128, against the
+    oracle's same iteration per block."""
+    P, f, wls, probs, _ = setup
+    opts = P.default_opts(inner_iters=6)
+    n = f.layout()["field_elems"]
+    bt, b = _rand_field(n, 7)
+    x = f.inner_solve(bt, opts, adjoint=adjoint).cpu().numpy()
+    bs, xs = _split(wls, probs, b), _split(wls, probs, x)
+    for i, (w, p) in enumerate(zip(wls, probs)):
+        for blk in range(p.n_blocks):
+            fi = p.block_freq(blk)
+            h = _oracle_hier(P, w, p, fi, opts)
+            A = p.operator(w.gamma_start.ravel(), fi)
+            ref, _ = mg.inner_solve(A, h, bs[i][blk], 6, adjoint=adjoint)
+            assert _rel(xs[i][blk], ref) < 1e-8, (i, blk, _rel(xs[i][blk], ref))
+
+
+def test_inner_solve_zero_rhs_block(setup):
+    """A block with a zero right-hand side stays exactly zero (no NaN)."""
+    P, f, wls, probs, _ = setup
+    n = f.layout()["field_elems"]
+    bt, _ = _rand_field(n, 8)
+    Nz, Nx = G.padded_shape(wls[0].grid)
+    bt[:Nz * Nx] = 0
+    x = f.inner_solve(bt, P.default_opts(inner_iters=4))
+    assert torch.all(x[:Nz * Nx] == 0)
+    assert torch.isfinite(torch.view_as_real(x)).all()
+
+
+@pytest.fixture(scope="module")
+def forward_done(setup):
+    P, f, wls, probs, d_obs = setup
+    d_pred, mis, st = f.forward(P.default_opts())
+    return d_pred, mis, st
+
+
+def test_forward_wavefields_and_misfit(setup, forward_done):
+    P, f, wls, probs, d_obs = setup
+    d_pred, mis, st = forward_done
+    u = f.wavefields().cpu().numpy()
+    us = _split(wls, probs, u)
+    for i, (w, p) in enumerate(zip(wls, probs)):
+        ref = fwi.forward(p, w.gamma_start.ravel())
+        for b in range(p.n_blocks):
+            assert _rel(us[i][b], ref[b]) < 1e-5, (i, b, _rel(us[i][b], ref[b]))
+        r = fwi.residual(p, ref, d_obs[i])
+        assert abs(mis[i] - fwi.misfit(p, r)) <= 1e-6 * fwi.misfit(p, r)
+        q = fwi.sample(p, ref)
+        for b in range(p.n_blocks):
+            k = p.block_src(b)
+            got = d_pred[i][p.block_freq(b), w.survey.rec_offsets[k]:w.survey.rec_offsets[k + 1]]
+            assert _rel(got, q[b]) < 1e-5
+
+
+def _oracle_kkts(wls, probs, d_obs, eps, include):
+    return [kkt.KKT(p, w.gamma_start.ravel(), d, eps, include_Ls_n=include) for w, p, d in zip(wls, probs, d_obs)]
+
+
+def _pack_gpu(Ks, parts):
+    """Per-instance (du, ds, lm) -> GPU packed [du all | lm all | ds all]."""
+    du = np.concatenate([p[0].ravel() for p in parts])
+    lm = np.concatenate([p[2].ravel() for p in parts])
+    ds = np.concatenate([p[1].ravel() for p in parts])
+    return np.concatenate([du.view(np.float64), lm.view(np.float64), ds])
+
+
+def _unpack_gpu(Ks, x):
+    nf = sum(K.B * K.N for K in Ks)
+    du = x[:2 * nf].view(np.complex128)
+    lm = x[2 * nf:4 * nf].view(np.complex128)
+    ds = x[4 * nf:]
+    out, o, oc = [], 0, 0
+    for K in Ks:
+        n = K.B * K.N
+        out.append((du[o:o + n].reshape(K.B, K.N), ds[oc:oc + K.Nc], lm[o:o + n].reshape(K.B, K.N)))
+        o += n
+        oc += K.Nc
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [(torch.float64, 1e-9), (torch.float32, 2e-5)])
+def test_kkt_matvec(setup, forward_done, prec, tol):
+    P, f, wls, probs, d_obs = setup
+    eps = 1e-2
+    Ks = _oracle_kkts(wls, probs, d_obs, eps, True)
+    rng = np.random.default_rng(9)
+    parts = [(rng.standard_normal((K.B, K.N)) + 1j * rng.standard_normal((K.B, K.N)), rng.standard_normal(K.Nc),
+              rng.standard_normal((K.B, K.N)) + 1j * rng.standard_normal((K.B, K.N))) for K in Ks]
+    x = _pack_gpu(Ks, parts)
+    y = f.apply_kkt(torch.from_numpy(x).to(prec).cuda(), P.default_opts(eps=eps)).cpu().numpy().astype(np.float64)
+    got = _unpack_gpu(Ks, y)
+    for K, p, g in zip(Ks, parts, got):
+        ref = K.unpack(K.matvec(K.pack(*p)))
+        for a, r in zip(g, ref):
+            assert _rel(a, r) < tol, _rel(a, r)
+
+
+def test_preconditioner_apply(setup, forward_done):
+    """One application of the inexact block-triangular preconditioner (eq.
+    precond_approx, 4 inner iterations), complex128, against the oracle."""
+    P, f, wls, probs, d_obs = setup
+    eps = 1e-2
+    opts = P.default_opts(eps=eps, inner_iters=4)
+    Ks = _oracle_kkts(wls, probs, d_obs, eps, True)
+    rng = np.random.default_rng(10)
+    parts = [(rng.standard_normal((K.B, K.N)) + 1j * rng.standard_normal((K.B, K.N)), rng.standard_normal(K.Nc),
+              rng.standard_normal((K.B, K.N)) + 1j * rng.standard_normal((K.B, K.N))) for K in Ks]
+    z = f.apply_precond(torch.from_numpy(_pack_gpu(Ks, parts)).cuda(), opts).cpu().numpy()
+    got = _unpack_gpu(Ks, z)
+    for i, (K, w, p, pr, g) in enumerate(zip(Ks, wls, probs, parts, got)):
+        hs = {fi: _oracle_hier(P, w, p, fi, opts) for fi in range(w.survey.n_freq)}
+
+        def inner(b, rhs, adj):
+            fi = p.block_freq(b)
+            return mg.inner_solve(K.A[fi], hs[fi], rhs, 4, adj)[0]
+        ref = K.unpack(K.precond(K.pack(*pr), inner))
+        for a, r in zip(g, ref):
+            assert _rel(a, r) < 1e-8, _rel(a, r)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kkt_solve_matches_direct(setup, forward_done, prec):
+    """Whole KKT solve (both instances jointly) against the oracle's sparse
+    direct solve per instance: relative residual <= 1e-6 recomputed in FP64 and
+    model update within 1e-5."""
+    P, f, wls, probs, d_obs = setup
+    eps = 1e-2
+    opts = P.default_opts(eps=eps, precision=prec, tol=1e-7, inner_iters=6)
+    ds, st = f.kkt_solve(opts)
+    assert st["rel_res"] <= 1e-7
+    Ks = _oracle_kkts(wls, probs, d_obs, eps, True)
+    o = 0
+    for K in Ks:
+        ref = K.delta_s(K.solve_direct())
+        got = ds[o:o + K.Nc]
+        o += K.Nc
+        assert _rel(got, ref) < 1e-5, _rel(got, ref)
+
+
+def test_gradient_matches_oracle(setup):
+    P, f, wls, probs, d_obs = setup
+    mis, g, st = f.gradient(P.default_opts())
+    o = 0
+    for w, p, d, m in zip(wls, probs, d_obs, mis):
+        phi, gr = fwi.gradient(p, w.gamma_start.ravel(), d)
+        n = gr.size
+        assert _rel(g[o:o + n], gr) < 1e-4, _rel(g[o:o + n], gr)
+        assert abs(m - phi) <= 1e-6 * phi
+        o += n
+
+
+def test_invalid_calls_return_errors(setup):
+    P, f, wls, probs, d_obs = setup
+    bad = P.default_opts(restart=0)
+    with pytest.raises(P.FwiError) as e:
+        f.kkt_solve(bad)
+    assert e.value.code == P.FWI_E_INVAL
+    with pytest.raises(P.FwiError) as e:
+        f.set_model(0, -np.ones((wls[0].grid.nz, wls[0].grid.nx)))
+    assert e.value.code == P.FWI_E_NUMERIC
