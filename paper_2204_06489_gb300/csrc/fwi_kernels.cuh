@@ -272,21 +272,43 @@ struct SmemCycle {
     }
     __syncthreads();
   }
-  __device__ void cycle(int l) {
-    if (l == nlev - 1) { coarsest(l); return; }
+  __device__ void presmooth(int l) {
     for (int s = 0; s < a.nu1; ++s) jacobi(l, s == 0);
     if (a.nu1 == 0) {
       int n = op[l].nx * op[l].nz;
       for (int k = threadIdx.x; k < n; k += blockDim.x) xs[l][k] = mk<T2>(0, 0);
       __syncthreads();
     }
-    int reps = l == 0 ? 1 : a.cyc;
-    for (int r = 0; r < reps; ++r) {
-      restrict_to(l);
-      cycle(l + 1);
-      prolong_from(l);
+  }
+  // The multigrid cycle from level `top` written as a loop (no device
+  // recursion): going down, a level pre-smooths and restricts; the coarsest
+  // level solves; going up, a level adds the prolonged correction and either
+  // repeats its coarse-grid correction (cycle index) or post-smooths.
+  __device__ void run(int top) {
+    int reps[MAX_LEVELS];
+    int l = top;
+    bool down = true;
+    for (int guard = 0; guard < (1 << 20); ++guard) {
+      if (down) {
+        if (l == nlev - 1) { coarsest(l); down = false; continue; }
+        presmooth(l);
+        reps[l] = l == 0 ? 1 : a.cyc;
+        restrict_to(l);
+        ++l;
+      } else {
+        if (l == top) break;
+        int p = l - 1;
+        prolong_from(p);
+        if (--reps[p] > 0) {
+          restrict_to(p);
+          l = p + 1;
+          down = true;
+        } else {
+          for (int s = 0; s < a.nu2; ++s) jacobi(p, false);
+          l = p;
+        }
+      }
     }
-    for (int s = 0; s < a.nu2; ++s) jacobi(l, false);
   }
 };
 
@@ -312,7 +334,7 @@ __global__ void k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restri
   int n = c.op[a.ls].nx * c.op[a.ls].nz;
   for (int k = threadIdx.x; k < n; k += blockDim.x) c.bs[a.ls][k] = b[bk.off + k];
   __syncthreads();
-  c.cycle(a.ls);
+  c.run(a.ls);
   for (int k = threadIdx.x; k < n; k += blockDim.x) x[bk.off + k] = c.xs[a.ls][k];
 }
 
