@@ -216,6 +216,11 @@ int fwi_mg_cycle(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int
 /* Sizes of the context's buffers. */
 int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (kernels replayed from a CUDA graph included).  Diagnostics only; the paper
+ * has no counterpart. */
+unsigned long long fwi_kernel_launches(void);
+
 /* Message of the last failure on this context ("" if none). NULL ctx: the
  * message of the last failed fwi_create. */
 const char *fwi_last_error(const fwi_ctx *ctx);

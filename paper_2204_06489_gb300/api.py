@@ -110,6 +110,7 @@ def load(build_if_missing: bool = False):
         "fwi_mg_cycle": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
         "fwi_get_layout": (C.c_int, [P, C.POINTER(LayoutInfo)]),
         "fwi_last_error": (C.c_char_p, [P]),
+        "fwi_kernel_launches": (C.c_ulonglong, []),
         "fwi_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():

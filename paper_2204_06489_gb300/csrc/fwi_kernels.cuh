@@ -1043,6 +1043,28 @@ __global__ void k_seg_axpy(const SegDev *segs, const TI *x, const double *f, dou
     y[i] = fma(fv, (double)x[i], y[i]);
 }
 
+// Model check on the device: partial[blockIdx.x] = sum s; *flag = 1 if any s
+// is non-finite or <= 0.
+__global__ void __launch_bounds__(FLAT_THREADS)
+k_model_stats(long long n, const double *__restrict__ s, double *partial, int *flag) {
+  double acc = 0.0;
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
+    double v = s[i];
+    if (!isfinite(v) || !(v > 0.0)) bad = 1;
+    acc += v;
+  }
+  __shared__ double red[FLAT_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < FLAT_THREADS / 32; ++q) t += red[q];
+    partial[blockIdx.x] = t;
+  }
+}
+
 // z = x - y (FP64, flat)
 __global__ void k_sub(long long n, const double *x, const double *y, double *z) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

@@ -6,6 +6,7 @@
 // row tiles, multigrid levels), sequences the kernel launches of the solvers
 // and reads back only scalars (residual norms) to steer the iterations.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -33,7 +34,14 @@ struct Err {
     if (e_ != cudaSuccess)                                                                 \
       throw Err{FWI_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};           \
   } while (0)
-#define KCHECK() CK(cudaGetLastError())
+// Every kernel launch of the library is followed by KCHECK(), which also
+// counts it (graph replays add the number of kernels captured in the graph).
+static std::atomic<unsigned long long> g_launches{0};
+#define KCHECK()                 \
+  do {                           \
+    ::fwi::g_launches.fetch_add(1); \
+    CK(cudaGetLastError());      \
+  } while (0)
 
 static void fail(int code, const std::string &m) { throw Err{code, m}; }
 
@@ -126,12 +134,14 @@ template <typename T> struct Work {
   // FGMRES
   int m = 0;
   long long n = 0;
+  long long ld = 0;    // basis stride: n rounded up to 64 elements (256-byte aligned vectors)
   DBuf<T> V, Z, vin, zout, tmp, rhs, sol;              // basis, staging, sweep rhs/solution
   DBuf<T *> dptrV, dptrZ;
   DBuf<double> H, cs, sn, g, hcol, hsum, y, scal, partial_flat;
   // preconditioner graph
   cudaGraphExec_t graph = nullptr;
   std::string graph_key;
+  unsigned long long graph_kernels = 0;
   ~Work() {
     if (graph) cudaGraphExecDestroy(graph);
   }
@@ -632,11 +642,12 @@ template <typename T> void Ctx::ensure_krylov(const fwi_opts &o) {
   if (w.m == m && w.V.p) return;
   w.m = m;
   w.n = nkkt;
-  w.V.alloc((size_t)(m + 1) * nkkt);
-  w.Z.alloc((size_t)m * nkkt);
+  w.ld = (nkkt + 63) / 64 * 64;
+  w.V.alloc((size_t)(m + 1) * w.ld);
+  w.Z.alloc((size_t)m * w.ld);
   std::vector<T *> pv(m + 1), pz(m);
-  for (int k = 0; k <= m; ++k) pv[k] = w.V.p + (size_t)k * nkkt;
-  for (int k = 0; k < m; ++k) pz[k] = w.Z.p + (size_t)k * nkkt;
+  for (int k = 0; k <= m; ++k) pv[k] = w.V.p + (size_t)k * w.ld;
+  for (int k = 0; k < m; ++k) pz[k] = w.Z.p + (size_t)k * w.ld;
   w.dptrV.upload(pv, st);
   w.dptrZ.upload(pz, st);
   w.H.alloc((size_t)(m + 1) * m); w.cs.alloc(m); w.sn.alloc(m); w.g.alloc(m + 1);
@@ -829,6 +840,7 @@ void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, con
   if (w.graph_key != key) {
     if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
     cudaGraph_t gr;
+    unsigned long long before = g_launches.load();
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     long long dummy = 0;
     try {
@@ -841,9 +853,12 @@ void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, con
     CK(cudaGraphInstantiate(&w.graph, gr, 0));
     cudaGraphDestroy(gr);
     w.graph_key = key;
+    w.graph_kernels = g_launches.load() - before;
+    g_launches.fetch_sub(w.graph_kernels);   // captured, not launched
   }
   CK(cudaMemcpyAsync(w.vin.p, v, nkkt * sizeof(T), cudaMemcpyDeviceToDevice, st));
   CK(cudaGraphLaunch(w.graph, st));
+  g_launches.fetch_add(w.graph_kernels);
   CK(cudaMemcpyAsync(z, w.zout.p, nkkt * sizeof(T), cudaMemcpyDeviceToDevice, st));
   if (count) *count += 2LL * o.inner_iters * B;
 }
@@ -902,9 +917,9 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
     CK(cudaMemcpyAsync(w.g.p, g0.data(), (m + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
     int k = 0;
     for (int j = 0; j < m && total < maxit; ++j) {
-      T *vj = w.V.p + (size_t)j * n;
-      T *zj = w.Z.p + (size_t)j * n;
-      T *wv = w.V.p + (size_t)(j + 1) * n;
+      T *vj = w.V.p + (size_t)j * w.ld;
+      T *zj = w.Z.p + (size_t)j * w.ld;
+      T *wv = w.V.p + (size_t)(j + 1) * w.ld;
       precond_any<T>(vj, zj, o, inner, u);
       kkt_matvec<T>(zj, wv, eps, u);
       // classical Gram-Schmidt, twice
@@ -1435,19 +1450,33 @@ int fwi_set_model(fwi_ctx *ctx, int inst, const double *gamma_core, double gamma
   if (inst < 0 || inst >= (int)c.inst.size() || !gamma_core) fwi::fail(FWI_E_INVAL, "bad model arguments");
   fwi::Instance &I = c.inst[inst];
   size_t n = (size_t)I.g.nx * I.g.nz;
-  std::vector<double> h(n);
-  if (on_device) {
-    CK(cudaMemcpyAsync(h.data(), gamma_core, n * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-    c.sync();
-  } else {
-    std::memcpy(h.data(), gamma_core, n * sizeof(double));
-  }
   double sum = 0.0;
-  for (double v : h) {
-    if (!std::isfinite(v) || !(v > 0.0)) fwi::fail(FWI_E_NUMERIC, "gamma must be finite and > 0");
-    sum += v;
+  if (on_device) {
+    // validate on the device; only the sum and a flag come back
+    I.s.alloc(n);
+    CK(cudaMemcpyAsync(I.s.p, gamma_core, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+    fwi::DBuf<double> part;
+    part.alloc(FLAT_BLOCKS + 1);
+    fwi::DBuf<int> flag;
+    flag.alloc(1);
+    flag.zero(c.st);
+    fwi::k_model_stats<<<FLAT_BLOCKS, FLAT_THREADS, 0, c.st>>>((long long)n, I.s.p, part.p, flag.p);
+    KCHECK();
+    fwi::k_reduce_partials<<<1, 32, 0, c.st>>>(1, FLAT_BLOCKS, part.p, part.p + FLAT_BLOCKS, 0);
+    KCHECK();
+    int hf = 0;
+    CK(cudaMemcpyAsync(&sum, part.p + FLAT_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    CK(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    if (hf || !std::isfinite(sum)) fwi::fail(FWI_E_NUMERIC, "gamma must be finite and > 0");
+  } else {
+    std::vector<double> h(gamma_core, gamma_core + n);
+    for (double v : h) {
+      if (!std::isfinite(v) || !(v > 0.0)) fwi::fail(FWI_E_NUMERIC, "gamma must be finite and > 0");
+      sum += v;
+    }
+    I.s.upload(h, c.st);
   }
-  I.s.upload(h, c.st);
   if (!I.has_model) {
     I.gamma_ref = gamma_ref > 0.0 ? gamma_ref : sum / (double)n;
     I.layer.alloc((size_t)I.Nx * I.Nz);
@@ -1697,6 +1726,8 @@ int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info) {
   return FWI_OK;
   API_END(ctx)
 }
+
+unsigned long long fwi_kernel_launches(void) { return fwi::g_launches.load(); }
 
 const char *fwi_last_error(const fwi_ctx *ctx) {
   if (!ctx) return g_create_error.c_str();

@@ -278,3 +278,26 @@ def test_invalid_calls_return_errors(setup):
     with pytest.raises(P.FwiError) as e:
         f.set_model(0, -np.ones((wls[0].grid.nz, wls[0].grid.nx)))
     assert e.value.code == P.FWI_E_NUMERIC
+
+
+def test_kkt_solve_odd_control_size(lib):
+    """A control vector of odd length (15 x 11 core) makes the packed KKT
+    length odd; the Krylov basis must still be aligned for complex loads."""
+    import paper_2204_06489_gb300 as P
+    wl = FI.micro_workload(seed=3, nx=15, nz=11, npml=4, n_src=2, n_rec=3)
+    prob = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    d = fwi.sample(prob, fwi.forward(prob, wl.gamma_true.ravel()))
+    obs = np.zeros((1, int(wl.survey.rec_offsets[-1])), dtype=complex)
+    for b in range(prob.n_blocks):
+        k = prob.block_src(b)
+        obs[0, wl.survey.rec_offsets[k]:wl.survey.rec_offsets[k + 1]] = d[b]
+    f = P.from_workload(wl)
+    f.set_observed(0, obs)
+    assert f.layout()["kkt_elems"] % 2 == 1
+    opts = P.default_opts(eps=1e-2, tol=1e-7)
+    f.forward(opts)
+    ds, st = f.kkt_solve(opts)
+    K = kkt.KKT(prob, wl.gamma_start.ravel(), d, 1e-2, include_Ls_n=True)
+    ref = K.delta_s(K.solve_direct())
+    assert st["rel_res"] <= 1e-7 and _rel(ds, ref) < 1e-5
+    f.close()
