@@ -213,6 +213,34 @@ int fwi_inner_solve(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, 
 /* x = one multigrid cycle for the shifted operator from x = 0 (field buffers). */
 int fwi_mg_cycle(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int precision);
 
+/* Size of the static device array behind fwi_mg_cycle_noalloc (16 MiB). */
+#define FWI_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* Same result as fwi_mg_cycle, for callers that must not allocate device
+ * memory during the call: code whose device memory is owned by another pool
+ * or budget, and code that runs this cycle while other streams are busy, where
+ * cudaMalloc / cudaFree would block (cudaFree waits for the whole device).
+ * The paper has no counterpart; this is a service of the library.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *     The cycle's level buffers live in one file-scope __device__ array of
+ *     FWI_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library keeps
+ *     until the process exits.
+ *   - Needs a context whose multigrid hierarchy was already built for the same
+ *     options and models by an allocating call (fwi_mg_cycle or fwi_forward);
+ *     otherwise FWI_E_INVAL.
+ *   - Needs at most FWI_NOALLOC_SCRATCH_BYTES of level buffers (about
+ *     2 x field_elems complex elements of the given precision); larger batches
+ *     get FWI_E_INVAL with the required size in fwi_last_error.
+ *   - The first call on each device (with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - Every call, on every context, shares the one array and leaves its
+ *     contents behind; the cycle writes each buffer before reading it, so no
+ *     clearing is needed.  Calls whose GPU work overlaps (different streams,
+ *     threads or contexts on the same device) race on the array.
+ * b, x: device field buffers as in fwi_mg_cycle; precision FWI_C128 or
+ * FWI_C64_REFINE.  Synchronises the context's stream before returning. */
+int fwi_mg_cycle_noalloc(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int precision);
+
 /* Sizes of the context's buffers. */
 int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info);
 

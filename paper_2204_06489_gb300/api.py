@@ -108,6 +108,7 @@ def load(build_if_missing: bool = False):
         "fwi_apply_precond": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
         "fwi_inner_solve": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int, C.c_int]),
         "fwi_mg_cycle": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
+        "fwi_mg_cycle_noalloc": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
         "fwi_get_layout": (C.c_int, [P, C.POINTER(LayoutInfo)]),
         "fwi_last_error": (C.c_char_p, [P]),
         "fwi_kernel_launches": (C.c_ulonglong, []),

@@ -232,6 +232,10 @@ struct Ctx {
                                       const fwi_opts &o);
   template <typename T> void inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
                                          int iters, double tol, const fwi_opts &o, long long *count);
+  template <typename T> void mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
+                                           const fwi_opts &o, typename cplx<T>::t *const *lx,
+                                           typename cplx<T>::t *const *lb, typename cplx<T>::t *const *lt,
+                                           typename cplx<T>::t *t0);
   template <typename T> void field_op(int mode, int cj, T w, const typename cplx<T>::t *x,
                                       const typename cplx<T>::t *b, typename cplx<T>::t *y, bool opA,
                                       int level);
@@ -724,6 +728,56 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
     return cur;
   };
   T2 *res = cyc(0, b, x, w.t0a.p);
+  if (res != x) CK(cudaMemcpyAsync(x, res, F0 * sizeof(T2), cudaMemcpyDeviceToDevice, st));
+}
+
+// The same cycle as mg_cycle, with every level buffer supplied by the caller
+// (used by fwi_mg_cycle_noalloc, whose buffers live in a static device array).
+template <typename T>
+void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj, const fwi_opts &o,
+                        typename cplx<T>::t *const *lx, typename cplx<T>::t *const *lb,
+                        typename cplx<T>::t *const *lt, typename cplx<T>::t *t0) {
+  typedef typename cplx<T>::t T2;
+  const T wj = (T)o.omega_jac;
+  CoarseArgs ca;
+  for (int l = 0; l < MAX_LEVELS; ++l) ca.blks[l] = l < nlev_max ? lv[l].blksM.p : nullptr;
+  ca.ops = d_ops.p; ca.inv = inv.p; ca.inv_off = inv_off.p; ca.inst_nlev = d_inst_nlev.p;
+  ca.ls = ls; ca.nu1 = o.nu1; ca.nu2 = o.nu2; ca.cyc = o.mg_cycle; ca.cj = cj; ca.w = o.omega_jac;
+  size_t smem = smem_bytes[sizeof(T) == 8];
+  if (ls == 0) {
+    k_coarse_cycle<T><<<B, 256, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
+    KCHECK();
+    return;
+  }
+  std::function<T2 *(int, const T2 *, T2 *, T2 *)> cyc;
+  cyc = [&](int l, const T2 *bl, T2 *xa, T2 *xb) -> T2 * {
+    if (l == ls) {
+      k_coarse_cycle<T><<<B, 256, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), bl, xa);
+      KCHECK();
+      return xa;
+    }
+    T2 *cur = xa, *oth = xb;
+    if (o.nu1 == 0) CK(cudaMemsetAsync(cur, 0, lv[l].field * sizeof(T2), st));
+    for (int s = 0; s < o.nu1; ++s) {
+      field_op<T>(s == 0 ? FM_JACOBI0 : FM_JACOBI, cj, wj, s == 0 ? nullptr : cur, bl, s == 0 ? cur : oth, false, l);
+      if (s > 0) std::swap(cur, oth);
+    }
+    int reps = l == 0 ? 1 : o.mg_cycle;
+    for (int r = 0; r < reps; ++r) {
+      LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
+      k_resid_restrict<T><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cj, cur, bl, lb[l + 1]);
+      KCHECK();
+      T2 *xc = cyc(l + 1, lb[l + 1], lx[l + 1], lt[l + 1]);
+      k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
+      KCHECK();
+    }
+    for (int s = 0; s < o.nu2; ++s) {
+      field_op<T>(FM_JACOBI, cj, wj, cur, bl, oth, false, l);
+      std::swap(cur, oth);
+    }
+    return cur;
+  };
+  T2 *res = cyc(0, b, x, t0);
   if (res != x) CK(cudaMemcpyAsync(x, res, F0 * sizeof(T2), cudaMemcpyDeviceToDevice, st));
 }
 
@@ -1710,6 +1764,79 @@ int fwi_mg_cycle(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int
   } else fwi::fail(FWI_E_INVAL, "bad precision");
   c.sync();
   return FWI_OK;
+  API_END(ctx)
+}
+
+// ---- multigrid cycle without device allocation ---------------------------
+// Scratch of fwi_mg_cycle_noalloc: the level buffers of one multigrid cycle.
+// Device code could name it directly; host code only ever holds its device
+// address, obtained per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FWI_NOALLOC_SCRATCH_BYTES];
+static void *g_noalloc_addr[256];
+static bool g_noalloc_ready[256];
+
+}  // extern "C"
+
+template <typename T>
+static int mg_cycle_noalloc_impl(fwi::Ctx &c, const fwi_opts &o, const void *b, void *x) {
+  typedef typename fwi::cplx<T>::t T2;
+  // buffers: level-0 ping-pong buffer + x, b, t of every global coarse level,
+  // each rounded up to 256 bytes
+  auto up = [](size_t n) { return (n + 255) / 256 * 256; };
+  size_t need = up(c.F0 * sizeof(T2));
+  for (int l = 1; l <= c.ls && l < c.nlev_max; ++l) need += 3 * up(c.lv[l].field * sizeof(T2));
+  if (need > (size_t)FWI_NOALLOC_SCRATCH_BYTES)
+    fwi::fail(FWI_E_INVAL, "fwi_mg_cycle_noalloc: the batch needs " + std::to_string(need) +
+                               " bytes of scratch, more than FWI_NOALLOC_SCRATCH_BYTES (" +
+                               std::to_string((size_t)FWI_NOALLOC_SCRATCH_BYTES) + ")");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) fwi::fail(FWI_E_INVAL, "device index out of range");
+  if (!g_noalloc_ready[dev]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      fwi::fail(FWI_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = ptr;
+    g_noalloc_ready[dev] = true;
+  }
+  unsigned char *base = (unsigned char *)g_noalloc_addr[dev];
+  size_t off = 0;
+  T2 *t0 = (T2 *)(base + off);
+  off += up(c.F0 * sizeof(T2));
+  T2 *lx[MAX_LEVELS] = {}, *lb[MAX_LEVELS] = {}, *lt[MAX_LEVELS] = {};
+  for (int l = 1; l <= c.ls && l < c.nlev_max; ++l) {
+    size_t bytes = up(c.lv[l].field * sizeof(T2));
+    lx[l] = (T2 *)(base + off); off += bytes;
+    lb[l] = (T2 *)(base + off); off += bytes;
+    lt[l] = (T2 *)(base + off); off += bytes;
+  }
+  size_t smem = c.smem_bytes[sizeof(T) == 8];
+  if (smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(fwi::k_coarse_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  c.mg_cycle_into<T>((const T2 *)b, (T2 *)x, 0, o, lx, lb, lt, t0);
+  c.sync();
+  return FWI_OK;
+}
+
+extern "C" {
+
+int fwi_mg_cycle_noalloc(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int precision) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!b || !x || !check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid arguments");
+  char key[256];
+  snprintf(key, sizeof key, "%d|%d|%.17g|%.17g", c.model_version, o.mg_levels, o.shift_beta, o.sigma_cap);
+  if (!c.layout_ok || c.hier_key != key)
+    fwi::fail(FWI_E_INVAL, "fwi_mg_cycle_noalloc: no multigrid hierarchy for these options and the current "
+                           "models; call fwi_mg_cycle (or fwi_forward) with the same options first");
+  if (precision == FWI_C128) return mg_cycle_noalloc_impl<double>(c, o, b, x);
+  if (precision == FWI_C64_REFINE) return mg_cycle_noalloc_impl<float>(c, o, b, x);
+  fwi::fail(FWI_E_INVAL, "bad precision");
+  return FWI_E_INVAL;
   API_END(ctx)
 }
 
