@@ -93,6 +93,59 @@ def _peaks():
         return {}
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one level-0 k_field_op launch
+# (ncu, profiles/k_field_op_marmousi_120blocks.md), per algorithmic byte;
+# None until a capture of the current kernel exists.
+TRAFFIC_PER_ALG_BYTE = None
+
+
+def _roofline(ms, nbytes, n, peaks):
+    peak = peaks.get("hbm_gbs")
+    src = "MEASURED_PEAKS.json hbm_gbs (measured)"
+    if not peak:
+        peak, src = 6800.0, "fallback 6.8 TB/s"
+    if not n or ms <= 0:
+        return None
+    ach = nbytes / (ms / 1e3) / 1e9
+    per_launch = nbytes / n
+    return {"kernel": "k_field_op<float> (level-0 5-point PML stencil / Jacobi sweep, all 120 blocks)",
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": src, "launches_timed": n, "avg_launch_us": ms / n * 1e3,
+            "algorithmic_bytes_per_launch": per_launch,
+            "traffic": (TRAFFIC_PER_ALG_BYTE * per_launch) if TRAFFIC_PER_ALG_BYTE else None}
+
+
+def run_inner_case(args):
+    """Profiling case: batched inner solves (BiCGStab + multigrid) on all 120
+    blocks of the benchmark workload, without the KKT basis (about 2 GB)."""
+    import numpy as np
+    import torch
+    import paper_2204_06489_gb300 as P
+    P.load(build_if_missing=True)
+    wl = _workload()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    f = P.FWI([wl.grid], stream=stream.cuda_stream)
+    f.set_survey(0, wl.survey)
+    f.set_model(0, wl.gamma_start)
+    opts = P.default_opts(inner_iters=4)
+    n = f.layout()["field_elems"]
+    g = np.random.default_rng(0)
+    b = torch.from_numpy((g.standard_normal(n) + 1j * g.standard_normal(n)).astype(np.complex64)).cuda()
+    for _ in range(args.warmup):
+        f.inner_solve(b, opts)
+    torch.cuda.synchronize()
+    f.stencil_timer(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f.inner_solve(b, opts)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    ms, nbytes, cnt = f.stencil_timer(0)
+    print(json.dumps({"case": "inner", "inner_iters": 4, "s_per_solve": dt,
+                      "roofline": _roofline(ms, nbytes, cnt, _peaks())}))
+
+
 def _workload():
     import fwi_inputs as FI
     return FI.marmousi_shaped_workload()
@@ -160,9 +213,14 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--case", default="newton", choices=["newton", "inner"])
+    ap.add_argument("--inner-iters", type=int, default=None)
+    ap.add_argument("--restart", type=int, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "inner":
+        return run_inner_case(args)
 
     import numpy as np
     import torch
@@ -180,6 +238,10 @@ def main():
     f = P.FWI([wl.grid], stream=stream.cuda_stream)
     f.set_survey(0, wl.survey)
     opts = P.default_opts(eps=EPS, precision=args.precision)
+    if args.inner_iters:
+        opts.inner_iters = args.inner_iters
+    if args.restart:
+        opts.restart = args.restart
     # synthetic observed data: the library's forward modelling at the true model
     f.set_model(0, wl.gamma_true)
     d_true, _, _ = f.forward(opts)
@@ -200,6 +262,7 @@ def main():
     for _ in range(args.warmup):
         step_device()
     torch.cuda.synchronize()
+    f.stencil_timer(1)          # live CUDA-event timing of the level-0 stencil kernel
     launches0 = f._L.fwi_kernel_launches()
     clocks = Clocks(local)
     clocks.start()
@@ -219,6 +282,7 @@ def main():
     ck = clocks.stop()
     dev_s = e0.elapsed_time(e1) / 1e3
     launches = f._L.fwi_kernel_launches() - launches0
+    st_ms, st_bytes, st_n = f.stencil_timer(0)
     if ws > 1:
         t = torch.tensor([dev_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -256,6 +320,7 @@ def main():
            "kkt_solve_s": per_step, "outer_iters_per_step": outer, "krylov_iters_per_s": outer / per_step,
            "inner_block_iters_per_s": inner / per_step, "rel_res_max": relres,
            "gpu_launches": int(launches),
+           "roofline": _roofline(st_ms, st_bytes, st_n, peaks),
            "clocks": ck,
            "e2e": {"value": ws / e2e_s, "unit": "Newton-step KKT solves/s",
                    "h2d_bytes_per_step": int(g_host.nbytes + d_host.nbytes),

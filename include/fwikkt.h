@@ -78,7 +78,8 @@ typedef struct {
   int inner_iters;        /* BiCGStab iterations per preconditioner block solve [8]  */
   double inner_tol;       /* > 0: stop a block's inner solve at this relative
                              residual (exact-preconditioner mode uses 1e-12)   [0]    */
-  int mg_cycle;           /* 1 = V-cycle, 2 = W-cycle                          [2]    */
+  int mg_cycle;           /* cycle index on levels 1..mg_wdepth (2 = W)        [2]    */
+  int mg_wdepth;          /* deepest level that repeats its correction; V below [2]  */
   int nu1, nu2;           /* pre / post Jacobi sweeps                          [2, 2] */
   double omega_jac;       /* Jacobi damping                                    [0.5]  */
   double shift_beta;      /* shifted operator omega^2 -> (1 + i beta) omega^2  [0.5]  */
@@ -248,6 +249,15 @@ int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info);
  * (kernels replayed from a CUDA graph included).  Diagnostics only; the paper
  * has no counterpart. */
 unsigned long long fwi_kernel_launches(void);
+
+/* Live timing of the level-0 stencil / smoother kernel (the 5-point operator
+ * of Sec. 2 applied to every block): while enabled, every launch of it that is
+ * not inside a CUDA graph is bracketed by CUDA events on the context's stream.
+ * Writes (nullable) the accumulated time (ms), algorithmic bytes (each complex
+ * element of the operands and result counted once) and launch count since the
+ * last reset; then enable = 1 resets and turns timing on, 0 resets and turns
+ * it off, -1 only reads.  Diagnostics; the paper has no counterpart. */
+int fwi_stencil_timer(fwi_ctx *ctx, int enable, double *ms, double *bytes, long long *launches);
 
 /* Message of the last failure on this context ("" if none). NULL ctx: the
  * message of the last failed fwi_create. */

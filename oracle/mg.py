@@ -22,8 +22,9 @@ fixed-point and convergence properties that the tests check):
     along the layer and rough across it, which no coarse grid removes;
   * smoother: damped Jacobi, x <- x + w D^{-1} (b - M x);
   * coarsest level: exact dense solve;
-  * cycle index ``cycle`` (1 = V, 2 = W) with (nu1, nu2) sweeps, from a zero
-    initial guess.
+  * cycle index ``cycle`` (1 = V, 2 = W) on levels 1..``wdepth`` and V below
+    (the coarse levels, where the shifted operator is nearly diagonal, gain
+    nothing from repeated corrections), (nu1, nu2) sweeps, zero initial guess.
 """
 from __future__ import annotations
 
@@ -70,11 +71,11 @@ class Hierarchy:
 
     def __init__(self, grid, omega: float, gamma_pad: np.ndarray, shift: float = 0.5,
                  levels: int | None = None, nu1: int = 2, nu2: int = 2, wj: float = 0.5,
-                 cycle: int = 2, sigma_cap: float | None = 1.0):
+                 cycle: int = 2, sigma_cap: float | None = 1.0, wdepth: int = 2):
         self.grid = grid
         self.levels = auto_levels(grid) if levels is None else int(levels)
         self.shapes = level_shapes(grid, self.levels)
-        self.nu1, self.nu2, self.wj, self.cycle = nu1, nu2, wj, cycle
+        self.nu1, self.nu2, self.wj, self.cycle, self.wdepth = nu1, nu2, wj, cycle, wdepth
         self.gammas = [H.level_gamma(grid, gamma_pad, l) for l in range(self.levels)]
         self.ops = [H.assemble(grid, omega, self.gammas[l], l, shift, sigma_cap=sigma_cap)
                     for l in range(self.levels)]
@@ -97,14 +98,14 @@ class Hierarchy:
         return self.P[l] @ e
 
     def vcycle(self, b: np.ndarray, l: int = 0) -> np.ndarray:
-        """One multigrid cycle (V for cycle=1, W for cycle=2) with (nu1, nu2)
-        Jacobi sweeps for M_l x = b from x = 0.  The fine level (l = 0) is
-        visited once; every coarser level repeats its coarse-grid correction
-        ``cycle`` times."""
+        """One multigrid cycle with (nu1, nu2) Jacobi sweeps for M_l x = b from
+        x = 0.  The fine level (l = 0) does one coarse-grid correction; levels
+        1..wdepth repeat theirs ``cycle`` times (W for cycle = 2); deeper
+        levels do one (V)."""
         if l == self.levels - 1:
             return self.coarse_inv @ b
         x = self.smooth(l, np.zeros_like(b), b, self.nu1)
-        for _ in range(1 if l == 0 else self.cycle):
+        for _ in range(self.cycle if 0 < l <= self.wdepth else 1):
             rc = self.restrict(l, b - self.ops[l] @ x)
             x = x + self.prolong(l, self.vcycle(rc, l + 1))
         return self.smooth(l, x, b, self.nu2)

@@ -44,7 +44,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("eps", C.c_double), ("include_Ls_n", C.c_int),
                 ("tol", C.c_double), ("restart", C.c_int), ("max_outer", C.c_int),
                 ("sweep_tol", C.c_double), ("max_refine", C.c_int), ("inner_iters", C.c_int),
-                ("inner_tol", C.c_double), ("mg_cycle", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("inner_tol", C.c_double), ("mg_cycle", C.c_int), ("mg_wdepth", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("omega_jac", C.c_double), ("shift_beta", C.c_double), ("sigma_cap", C.c_double),
                 ("mg_levels", C.c_int), ("fwd_tol", C.c_double), ("fwd_iters", C.c_int),
                 ("max_fwd_refine", C.c_int), ("use_graph", C.c_int)]
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = False):
         "fwi_get_layout": (C.c_int, [P, C.POINTER(LayoutInfo)]),
         "fwi_last_error": (C.c_char_p, [P]),
         "fwi_kernel_launches": (C.c_ulonglong, []),
+        "fwi_stencil_timer": (C.c_int, [P, C.c_int, DP, DP, C.POINTER(C.c_longlong)]),
         "fwi_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -289,6 +290,13 @@ class FWI:
                                      C.byref(st))
         self._check(rc, allow_noconv)
         return ds, st.as_dict()
+
+    def stencil_timer(self, enable: int):
+        """(ms, algorithmic bytes, launches) of the level-0 stencil kernel since
+        the last reset; ``enable`` 1/0 resets and switches timing, -1 reads."""
+        ms, by, n = C.c_double(), C.c_double(), C.c_longlong()
+        self._check(self._L.fwi_stencil_timer(self._h, enable, C.byref(ms), C.byref(by), C.byref(n)))
+        return ms.value, by.value, n.value
 
     # ------------------------------------------------------------------ operators (torch CUDA tensors)
     @staticmethod

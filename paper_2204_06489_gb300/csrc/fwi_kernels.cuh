@@ -11,6 +11,38 @@
 namespace fwi {
 
 // ---------------------------------------------------------------------------
+// Dot-product accumulation.  GB300's FP64 throughput is a small fraction of
+// its FP32 rate, so per-element FP64 arithmetic turns a bandwidth-bound dot
+// into an ALU-bound one.  Products of float data are accumulated per thread
+// in "double-float" (an unevaluated sum hi + lo of two floats): Dekker's
+// exact product via FMA and Knuth's TwoSum keep about 44 significant bits, and
+// only the per-thread results are combined in FP64.
+// ---------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ void df_add_prod(DF &a, float x, float y) {
+  float p = x * y;
+  float pe = __fmaf_rn(x, y, -p);          // x*y = p + pe exactly
+  float s = __fadd_rn(a.hi, p);            // TwoSum(a.hi, p) = s + e exactly
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, pe));
+  a.hi = __fadd_rn(s, e);                  // renormalise
+  a.lo = __fsub_rn(e, __fsub_rn(a.hi, s));
+}
+__device__ __forceinline__ double df_value(const DF &a) { return (double)a.hi + (double)a.lo; }
+
+// acc += x*y for the accumulator type of the data precision
+__device__ __forceinline__ void acc_prod(DF &a, float x, float y) { df_add_prod(a, x, y); }
+__device__ __forceinline__ void acc_prod(double &a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ double acc_value(const DF &a) { return df_value(a); }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+template <typename T> struct Acc;
+template <> struct Acc<float> { typedef DF t; static __device__ __forceinline__ DF zero() { DF z; z.hi = 0.f; z.lo = 0.f; return z; } };
+template <> struct Acc<double> { typedef double t; static __device__ __forceinline__ double zero() { return 0.0; } };
+
+// ---------------------------------------------------------------------------
 // stencil coefficients
 // ---------------------------------------------------------------------------
 // Operator of Sec. 2 (eq. helmholtz_preliminary), h_l^2-scaled, at node (j, i):
@@ -52,9 +84,75 @@ struct Stencil {
 
 enum FieldMode { FM_APPLY = 0, FM_RESID = 1, FM_JACOBI = 2, FM_JACOBI0 = 3 };
 
-// y = Op x | b - Op x | x + w (b - Op x)/cc | w b / cc  on every block of a level.
+// 1/z for the smoother's diagonal: conj(z) / |z|^2 with a single reciprocal
+// (float: the hardware reciprocal, correctly rounded; double: plain division).
+__device__ __forceinline__ float2 cinv(float2 z) {
+  float r = __frcp_rn(z.x * z.x + z.y * z.y);
+  return make_float2(z.x * r, -z.y * r);
+}
+__device__ __forceinline__ double2 cinv(double2 z) {
+  double r = 1.0 / (z.x * z.x + z.y * z.y);
+  return make_double2(z.x * r, -z.y * r);
+}
+
+// The 5-point operator along one grid row j, with the row-constant factors
+// (Z_j, 1/Z_{j-1/2}, 1/Z_{j+1/2}, the mass factor) loaded once.  Same
+// arithmetic as Stencil, regrouped: with sZ = 1/Z_{j-1/2} + 1/Z_{j+1/2},
+//   cc = Z_j (1/X_{i-1/2} + 1/X_{i+1/2}) + X_i (sZ - m Z_j gamma_ij)
+//   (Op u)_ij = cc u_ij - Z_j (u_i+1,j / X_{i+1/2} + u_i-1,j / X_{i-1/2})
+//                       - X_i (u_i,j+1 / Z_{j+1/2} + u_i,j-1 / Z_{j-1/2}),
+// every factor conjugated when cj (A^H = conj A).
 template <typename T>
-__global__ void __launch_bounds__(TILE_THREADS)
+struct RowOp {
+  typedef typename cplx<T>::t T2;
+  const T2 *X, *iXh;
+  const T *g;
+  T2 Zj, iZn, iZs, sZ, mZ;
+  bool cj;
+  int nx, nz, j;
+  __device__ __forceinline__ RowOp(const OpDev &op, const T2 *__restrict__ st, const T *__restrict__ gam, int j_,
+                                   bool cj_) {
+    X = st + op.st;
+    iXh = X + op.nx;
+    const T2 *Z = iXh + op.nx + 1;
+    const T2 *iZh = Z + op.nz;
+    nx = op.nx; nz = op.nz; j = j_; cj = cj_;
+    g = gam + op.gam + (long long)j * op.nx;
+    Zj = cmaybe_conj(Z[j], cj);
+    iZn = cmaybe_conj(iZh[j], cj);
+    iZs = cmaybe_conj(iZh[j + 1], cj);
+    sZ = cadd(iZn, iZs);
+    mZ = cmul(cmaybe_conj(mk<T2>(op.mass_re, op.mass_im), cj), Zj);
+  }
+  // returns (Op u)_ij and the diagonal cc; u points at the block's grid
+  __device__ __forceinline__ T2 apply(const T2 *__restrict__ u, int i, T2 &cc) const {
+    T2 Xi = cmaybe_conj(X[i], cj);
+    T2 iw = cmaybe_conj(iXh[i], cj);
+    T2 ie = cmaybe_conj(iXh[i + 1], cj);
+    T gi = g[i];
+    long long k = (long long)j * nx + i;
+    T2 uc = u[k];
+    T2 ue = i + 1 < nx ? u[k + 1] : mk<T2>(0, 0);
+    T2 uw = i > 0 ? u[k - 1] : mk<T2>(0, 0);
+    T2 us = j + 1 < nz ? u[k + nx] : mk<T2>(0, 0);
+    T2 un = j > 0 ? u[k - nx] : mk<T2>(0, 0);
+    cc = cadd(cmul(Zj, cadd(iw, ie)), cmul(Xi, csub(sZ, cscale(mZ, gi))));
+    T2 hx = cadd(cmul(ie, ue), cmul(iw, uw));
+    T2 hz = cadd(cmul(iZs, us), cmul(iZn, un));
+    return csub(csub(cmul(cc, uc), cmul(Zj, hx)), cmul(Xi, hz));
+  }
+  __device__ __forceinline__ T2 diag(int i) const {
+    T2 Xi = cmaybe_conj(X[i], cj);
+    T2 iw = cmaybe_conj(iXh[i], cj);
+    T2 ie = cmaybe_conj(iXh[i + 1], cj);
+    return cadd(cmul(Zj, cadd(iw, ie)), cmul(Xi, csub(sZ, cscale(mZ, g[i]))));
+  }
+};
+
+// y = Op x | b - Op x | x + w (b - Op x)/cc | w b / cc  on every block of a level.
+// One warp per row, two columns per lane in flight.
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 6 : 3)
 k_field_op(LevelView<T> L, int mode, int cj, T w, const typename cplx<T>::t *__restrict__ x,
            const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
   typedef typename cplx<T>::t T2;
@@ -63,60 +161,94 @@ k_field_op(LevelView<T> L, int mode, int cj, T w, const typename cplx<T>::t *__r
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);
   if (j >= op.nz) return;
+  const RowOp<T> R(op, L.st, L.gam, j, cj != 0);
   const T2 *xb = x ? x + bk.off : nullptr;
-  const T2 *bb = b ? b + bk.off : nullptr;
-  T2 *yb = y + bk.off;
-  for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
-    Stencil<T> s;
-    s.load(op, L.st, L.gam, j, i, cj != 0);
-    long long k = (long long)j * op.nx + i;
-    T2 out;
-    if (mode == FM_JACOBI0) {
-      out = cscale(cdiv(bb[k], s.cc), w);
-    } else {
-      T2 ax = s.apply(xb, op.nx, op.nz, j, i);
-      if (mode == FM_APPLY) out = ax;
-      else if (mode == FM_RESID) out = csub(bb[k], ax);
-      else out = cadd(xb[k], cscale(cdiv(csub(bb[k], ax), s.cc), w));
+  const T2 *bb = b ? b + bk.off + (long long)j * op.nx : nullptr;
+  T2 *yb = y + bk.off + (long long)j * op.nx;
+  const int lane = threadIdx.x & 31;
+  for (int i0 = lane; i0 < op.nx; i0 += 64) {
+    T2 out[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int i = i0 + 32 * q;
+      if (i < op.nx) {
+        if (mode == FM_JACOBI0) {
+          out[q] = cscale(cmul(bb[i], cinv(R.diag(i))), w);
+        } else {
+          T2 cc;
+          T2 ax = R.apply(xb, i, cc);
+          if (mode == FM_APPLY) out[q] = ax;
+          else if (mode == FM_RESID) out[q] = csub(bb[i], ax);
+          else out[q] = cadd(xb[(long long)j * op.nx + i], cscale(cmul(csub(bb[i], ax), cinv(cc)), w));
+        }
+      }
     }
-    yb[k] = out;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (i0 + 32 * q < op.nx) yb[i0 + 32 * q] = out[q];
   }
 }
 
 // Fused residual + restriction (R = P^T, i.e. 4x full weighting):
 //   bc[J][I] = sum_{a,b in -1..1} w_a w_b (bf - Op xf)[2J+1+b][2I+1+a],  w = (1/2, 1, 1/2).
-// One warp per coarse row.  Lf: fine level, Lc: coarse level (same block order).
+// A CTA takes one coarse row tile (8 coarse rows) and walks it in chunks of
+// 64 coarse columns: the 17 x 129 fine residuals of a chunk are computed once
+// into shared memory (one warp per fine row), then every coarse node sums its
+// nine weighted neighbours from there.
+#define RR_CW 64
+#define RR_FW (2 * RR_CW + 1)
+#define RR_FR (2 * TILE_ROWS + 1)
 template <typename T>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_resid_restrict(LevelView<T> Lf, LevelView<T> Lc, int cj, const typename cplx<T>::t *__restrict__ xf,
                  const typename cplx<T>::t *__restrict__ bf, typename cplx<T>::t *__restrict__ bc) {
   typedef typename cplx<T>::t T2;
+  __shared__ T2 r[RR_FR][RR_FW];
   const TileDev t = Lc.tiles[blockIdx.x];
   const BlkDev bkc = Lc.blks[t.blk];
   const OpDev opc = Lc.ops[bkc.op];
   const BlkDev bkf = Lf.blks[t.blk];
   const OpDev opf = Lf.ops[bkf.op];
-  const int J = t.row0 + (threadIdx.x >> 5);
-  if (J >= opc.nz) return;
   const T2 *xb = xf + bkf.off;
   const T2 *bb = bf + bkf.off;
-  for (int I = threadIdx.x & 31; I < opc.nx; I += 32) {
-    T2 acc = mk<T2>(0, 0);
-    for (int db = -1; db <= 1; ++db) {
-      int j = 2 * J + 1 + db;
-      if (j < 0 || j >= opf.nz) continue;
-      T wz = db == 0 ? T(1) : T(0.5);
-      for (int da = -1; da <= 1; ++da) {
-        int i = 2 * I + 1 + da;
-        if (i < 0 || i >= opf.nx) continue;
-        T wx = da == 0 ? T(1) : T(0.5);
-        Stencil<T> s;
-        s.load(opf, Lf.st, Lf.gam, j, i, cj != 0);
-        T2 r = csub(bb[(long long)j * opf.nx + i], s.apply(xb, opf.nx, opf.nz, j, i));
-        acc = cadd(acc, cscale(r, wz * wx));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int J0 = t.row0;
+  const int jf0 = 2 * J0;
+  for (int I0 = 0; I0 < opc.nx; I0 += RR_CW) {
+    const int if0 = 2 * I0;
+    for (int rr = warp; rr < RR_FR; rr += TILE_ROWS) {
+      int j = jf0 + rr;
+      if (j < opf.nz) {
+        const RowOp<T> R(opf, Lf.st, Lf.gam, j, cj != 0);
+        for (int c = lane; c < RR_FW; c += 32) {
+          int i = if0 + c;
+          T2 v = mk<T2>(0, 0);
+          if (i < opf.nx) {
+            T2 cc;
+            v = csub(bb[(long long)j * opf.nx + i], R.apply(xb, i, cc));
+          }
+          r[rr][c] = v;
+        }
+      } else {
+        for (int c = lane; c < RR_FW; c += 32) r[rr][c] = mk<T2>(0, 0);
       }
     }
-    bc[bkc.off + (long long)J * opc.nx + I] = acc;
+    __syncthreads();
+    for (int q = threadIdx.x; q < TILE_ROWS * RR_CW; q += TILE_THREADS) {
+      int jl = q / RR_CW, il = q - jl * RR_CW;
+      int J = J0 + jl, I = I0 + il;
+      if (J < opc.nz && I < opc.nx) {
+        // fine rows 2jl..2jl+2 and columns 2il..2il+2 of the chunk
+        const T2 *r0 = r[2 * jl] + 2 * il;
+        const T2 *r1 = r[2 * jl + 1] + 2 * il;
+        const T2 *r2 = r[2 * jl + 2] + 2 * il;
+        T2 e0 = cadd(cadd(cscale(r0[0], (T)0.5), r0[1]), cscale(r0[2], (T)0.5));
+        T2 e1 = cadd(cadd(cscale(r1[0], (T)0.5), r1[1]), cscale(r1[2], (T)0.5));
+        T2 e2 = cadd(cadd(cscale(r2[0], (T)0.5), r2[1]), cscale(r2[2], (T)0.5));
+        bc[bkc.off + (long long)J * opc.nx + I] = cadd(cadd(cscale(e0, (T)0.5), e1), cscale(e2, (T)0.5));
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -171,7 +303,7 @@ struct CoarseArgs {
   const double2 *inv;               // coarsest inverses (offset per op in inv_off)
   const long long *inv_off;         // [n_ops]
   const int *inst_nlev;             // number of levels of each instance
-  int ls, nu1, nu2, cyc, cj;
+  int ls, nu1, nu2, cyc, cj, wdepth;
   double w;
 };
 
@@ -188,27 +320,33 @@ struct SmemCycle {
 
   __device__ void jacobi(int l, bool from_zero) {
     const OpDev &o = op[l];
-    int n = o.nx * o.nz;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      int j = k / o.nx, i = k - j * o.nx;
-      Stencil<T> s;
-      s.load(o, st, gam, j, i, a.cj != 0);
-      T2 r = from_zero ? bs[l][k] : csub(bs[l][k], s.apply(xs[l], o.nx, o.nz, j, i));
-      T2 d = cscale(cdiv(r, s.cc), (T)a.w);
-      ts[l][k] = from_zero ? d : cadd(xs[l][k], d);
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const T w = (T)a.w;
+    for (int j = threadIdx.x >> 5; j < o.nz; j += nw) {
+      const RowOp<T> R(o, st, gam, j, a.cj != 0);
+      for (int i = lane; i < o.nx; i += 32) {
+        int k = j * o.nx + i;
+        if (from_zero) {
+          ts[l][k] = cscale(cmul(bs[l][k], cinv(R.diag(i))), w);
+        } else {
+          T2 cc;
+          T2 ax = R.apply(xs[l], i, cc);
+          ts[l][k] = cadd(xs[l][k], cscale(cmul(csub(bs[l][k], ax), cinv(cc)), w));
+        }
+      }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < n; k += blockDim.x) xs[l][k] = ts[l][k];
-    __syncthreads();
+    T2 *tmp = xs[l]; xs[l] = ts[l]; ts[l] = tmp;   // ping-pong
   }
   __device__ void restrict_to(int l) {  // b_{l+1} = P^T (b_l - M_l x_l)
     const OpDev &o = op[l];
-    int n = o.nx * o.nz;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      int j = k / o.nx, i = k - j * o.nx;
-      Stencil<T> s;
-      s.load(o, st, gam, j, i, a.cj != 0);
-      ts[l][k] = csub(bs[l][k], s.apply(xs[l], o.nx, o.nz, j, i));
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = threadIdx.x >> 5; j < o.nz; j += nw) {
+      const RowOp<T> R(o, st, gam, j, a.cj != 0);
+      for (int i = lane; i < o.nx; i += 32) {
+        T2 cc;
+        ts[l][j * o.nx + i] = csub(bs[l][j * o.nx + i], R.apply(xs[l], i, cc));
+      }
     }
     __syncthreads();
     const OpDev &c = op[l + 1];
@@ -255,20 +393,26 @@ struct SmemCycle {
     }
     __syncthreads();
   }
+  // x = M^{-1} b with the FP64 inverse: one warp per row, lanes over columns.
   __device__ void coarsest(int l) {
     const OpDev &o = op[l];
     int n = o.nx * o.nz;
     const double2 *M = a.inv + a.inv_off[a.blks[l][blk].op];
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int c = 0; c < n; ++c) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < n; r += nw) {
+      double ax = 0.0, ay = 0.0;
+      for (int c = lane; c < n; c += 32) {
         double2 m = M[(long long)r * n + c];
         if (a.cj) m.y = -m.y;
         double2 v = to_d2(bs[l][c]);
-        acc.x += m.x * v.x - m.y * v.y;
-        acc.y += m.x * v.y + m.y * v.x;
+        ax += m.x * v.x - m.y * v.y;
+        ay += m.x * v.y + m.y * v.x;
       }
-      xs[l][r] = mk<T2>(acc.x, acc.y);
+      for (int q = 16; q > 0; q >>= 1) {
+        ax += __shfl_down_sync(0xffffffffu, ax, q);
+        ay += __shfl_down_sync(0xffffffffu, ay, q);
+      }
+      if (lane == 0) xs[l][r] = mk<T2>(ax, ay);
     }
     __syncthreads();
   }
@@ -292,7 +436,7 @@ struct SmemCycle {
       if (down) {
         if (l == nlev - 1) { coarsest(l); down = false; continue; }
         presmooth(l);
-        reps[l] = l == 0 ? 1 : a.cyc;
+        reps[l] = (l > 0 && l <= a.wdepth) ? a.cyc : 1;
         restrict_to(l);
         ++l;
       } else {
@@ -513,19 +657,22 @@ __global__ void k_gauss_jordan(const int *dims, const long long *aug_off, const 
 // ---------------------------------------------------------------------------
 // per-block reductions and BiCGStab vector updates
 // ---------------------------------------------------------------------------
-// partial[tile][q] = sum over the tile of conj(a_q) b_q (q < nd), accumulated
-// in FP64; fixed order, no atomics.
+// partial[tile][q] = sum over the tile of conj(a_q) b_q (q < nd): per-thread
+// double-float (complex64 data) or FP64 (complex128) accumulation, FP64
+// across threads; fixed order, no atomics.
 template <typename T>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typename cplx<T>::t *b0,
              const typename cplx<T>::t *a1, const typename cplx<T>::t *b1,
              const typename cplx<T>::t *a2, const typename cplx<T>::t *b2, double2 *partial) {
   typedef typename cplx<T>::t T2;
+  typedef typename Acc<T>::t A;
   const TileDev t = L.tiles[blockIdx.x];
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);
-  double2 acc[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+  A re[3] = {Acc<T>::zero(), Acc<T>::zero(), Acc<T>::zero()};
+  A im[3] = {Acc<T>::zero(), Acc<T>::zero(), Acc<T>::zero()};
   const T2 *as[3] = {a0, a1, a2};
   const T2 *bs[3] = {b0, b1, b2};
   if (j < op.nz) {
@@ -534,9 +681,12 @@ k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typena
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         if (q < nd) {
-          double2 a = to_d2(as[q][base + i]), b = to_d2(bs[q][base + i]);
-          acc[q].x += a.x * b.x + a.y * b.y;
-          acc[q].y += a.x * b.y - a.y * b.x;
+          T2 a = as[q][base + i], b = bs[q][base + i];
+          // conj(a) b = (ax bx + ay by) + i (ax by - ay bx)
+          acc_prod(re[q], a.x, b.x);
+          acc_prod(re[q], a.y, b.y);
+          acc_prod(im[q], a.x, b.y);
+          acc_prod(im[q], -a.y, b.x);
         }
       }
     }
@@ -544,7 +694,7 @@ k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typena
   __shared__ double2 red[3][TILE_THREADS / 32];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    double x = acc[q].x, y = acc[q].y;
+    double x = acc_value(re[q]), y = acc_value(im[q]);
     for (int o = 16; o > 0; o >>= 1) {
       x += __shfl_down_sync(0xffffffffu, x, o);
       y += __shfl_down_sync(0xffffffffu, y, o);
@@ -859,26 +1009,28 @@ __global__ void k_update_model(const InstDev *inst, double *const *s_core, const
 #define FLAT_THREADS 256
 #define MD_CHUNK 8
 
-// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv (FP64 accumulation, fixed grid).
+// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv (double-float or FP64
+// accumulation per thread, FP64 across threads; fixed grid, deterministic).
 template <typename T>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, double *partial) {
-  double acc[MD_CHUNK];
+  typedef typename Acc<T>::t A;
+  A acc[MD_CHUNK];
 #pragma unroll
-  for (int v = 0; v < MD_CHUNK; ++v) acc[v] = 0.0;
+  for (int v = 0; v < MD_CHUNK; ++v) acc[v] = Acc<T>::zero();
   const T *vp[MD_CHUNK];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) vp[v] = v < nv ? V[v] : nullptr;
   for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
-    double wi = (double)w[i];
+    T wi = w[i];
 #pragma unroll
     for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) acc[v] = fma((double)vp[v][i], wi, acc[v]);
+      if (v < nv) acc_prod(acc[v], vp[v][i], wi);
   }
   __shared__ double red[MD_CHUNK][FLAT_THREADS / 32];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) {
-    double x = acc[v];
+    double x = acc_value(acc[v]);
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = x;
   }
@@ -900,30 +1052,33 @@ __global__ void k_reduce_partials(int nv, int nb, const double *partial, double 
   if (threadIdx.x == 0) out[v] = accumulate ? out[v] + s : s;
 }
 
-// w -= sum_v coef[v] V_v  (coef on device, FP64); sign = -1, or x += sum (sign = +1)
+// w += sign * sum_v coef[v] V_v  (coefficients from the device, FP64, applied
+// in the data precision T: the result is stored in T anyway)
 template <typename T>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_multi_axpy(long long n, int nv, const T *const *V, const double *coef, double sign, T *w) {
-  double c[MD_CHUNK];
+  T c[MD_CHUNK];
   const T *vp[MD_CHUNK];
 #pragma unroll
-  for (int v = 0; v < MD_CHUNK; ++v) { c[v] = v < nv ? sign * coef[v] : 0.0; vp[v] = v < nv ? V[v] : nullptr; }
+  for (int v = 0; v < MD_CHUNK; ++v) { c[v] = v < nv ? (T)(sign * coef[v]) : (T)0; vp[v] = v < nv ? V[v] : nullptr; }
   for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
-    double acc = (double)w[i];
+    T acc = w[i];
 #pragma unroll
     for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) acc = fma(c[v], (double)vp[v][i], acc);
-    w[i] = (T)acc;
+      if (v < nv) acc = fma(c[v], vp[v][i], acc);
+    w[i] = acc;
   }
 }
 
-// partial[blockIdx.x] = sum x[i] y[i] (FP64 accumulation, fixed grid)
+// partial[blockIdx.x] = sum x[i] y[i] (double-float / FP64 per thread, FP64
+// across threads, fixed grid)
 template <typename T>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_dot2(long long n, const T *__restrict__ x, const T *__restrict__ y, double *partial) {
-  double acc = 0.0;
+  typename Acc<T>::t a = Acc<T>::zero();
   for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS)
-    acc = fma((double)x[i], (double)y[i], acc);
+    acc_prod(a, x[i], y[i]);
+  double acc = acc_value(a);
   __shared__ double red[FLAT_THREADS / 32];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -935,11 +1090,12 @@ k_dot2(long long n, const T *__restrict__ x, const T *__restrict__ y, double *pa
   }
 }
 
-// y = a x + b y (FP64 arithmetic)
+// y = a x + b y (arithmetic in the data precision)
 template <typename T>
 __global__ void k_axpby(long long n, double a, const T *__restrict__ x, double b, T *__restrict__ y) {
+  const T ta = (T)a, tb = (T)b;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = (T)(a * (double)x[i] + b * (double)y[i]);
+    y[i] = ta * x[i] + tb * y[i];
 }
 
 // a[i] += b[i] for i < n (small FP64 vectors)
@@ -951,9 +1107,9 @@ __global__ void k_dadd(int n, double *a, const double *b) {
 template <typename T>
 __global__ void k_scale_inv(long long n, const double *s, const T *x, T *y) {
   double sv = *s;
-  double f = sv != 0.0 ? 1.0 / sv : 0.0;
+  const T f = (T)(sv != 0.0 ? 1.0 / sv : 0.0);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = (T)((double)x[i] * f);
+    y[i] = x[i] * f;
 }
 
 // Arnoldi column j of the flexible GMRES: h[0..j] = dots (accumulated over the

@@ -175,6 +175,7 @@ struct Ctx {
   int model_version = 1;
   std::string hier_key;
   int ls = 1, nlev_max = 1;
+  int ls_p[2] = {1, 1};   // first shared-memory level for complex64 / complex128
   LevelTables lv[MAX_LEVELS];
   std::vector<OpDev> h_ops;
   DBuf<OpDev> d_ops;
@@ -207,9 +208,30 @@ struct Ctx {
   Work<double> w64;
   double *pin = nullptr;  // pinned scalars
   int *pinflag = nullptr;
+  // live timing of the level-0 stencil kernel (k_field_op): event pairs around
+  // direct launches on this context's stream, with the launch's algorithmic bytes
+  int timer_on = 0;
+  std::vector<cudaEvent_t> ev_a, ev_b;
+  std::vector<double> ev_bytes;
+  size_t ev_used = 0;
+  double timer_ms = 0.0, timer_bytes = 0.0;
+  long long timer_n = 0;
+  void harvest() {
+    for (size_t q = 0; q < ev_used; ++q) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev_a[q], ev_b[q]) == cudaSuccess) {
+        timer_ms += ms;
+        timer_bytes += ev_bytes[q];
+        ++timer_n;
+      }
+    }
+    ev_used = 0;
+  }
 
   bool own_stream = false;
   ~Ctx() {
+    for (auto e : ev_a) cudaEventDestroy(e);
+    for (auto e : ev_b) cudaEventDestroy(e);
     if (pin) cudaFreeHost(pin);
     if (pinflag) cudaFreeHost(pinflag);
     if (own_stream && st) cudaStreamDestroy(st);
@@ -255,7 +277,10 @@ struct Ctx {
                                           fwi_stats *stats);
   void seg_norms(const double *x);
   int kkt_solve(const fwi_opts &o, fwi_stats *stats);
-  void sync() { CK(cudaStreamSynchronize(st)); }
+  void sync() {
+    CK(cudaStreamSynchronize(st));
+    if (ev_used) harvest();
+  }
 };
 
 template <> Work<float> &Ctx::work<float>() { return w32; }
@@ -438,12 +463,17 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   };
   int minlev = nlev_max;
   for (auto &I : inst) minlev = std::min(minlev, I.nlev);
-  ls = 1;
-  while (ls < minlev - 1 && smem_from(ls, sizeof(double2)) > budget) ++ls;
-  if (minlev < 2) ls = 0;  // single-level instances: the whole cycle is the coarse solve
-  smem_bytes[0] = smem_from(ls, sizeof(float2));
-  smem_bytes[1] = smem_from(ls, sizeof(double2));
-  if (smem_bytes[1] > 227 * 1024) fail(FWI_E_INVAL, "grids too different for one batch (coarse levels exceed shared memory)");
+  for (int p = 0; p < 2; ++p) {
+    size_t elem = p ? sizeof(double2) : sizeof(float2);
+    int l0 = 1;
+    while (l0 < minlev - 1 && smem_from(l0, elem) > budget) ++l0;
+    if (minlev < 2) l0 = 0;  // single-level instances: the whole cycle is the coarse solve
+    ls_p[p] = l0;
+    smem_bytes[p] = smem_from(l0, elem);
+  }
+  ls = std::max(ls_p[0], ls_p[1]);   // tiles and global level tables are built up to here
+  if (smem_bytes[1] > 227 * 1024 || smem_bytes[0] > 227 * 1024)
+    fail(FWI_E_INVAL, "grids too different for one batch (coarse levels exceed shared memory)");
   // operators
   h_ops.clear();
   std::vector<AxisDev> axes;
@@ -617,7 +647,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
 template <typename T> void Ctx::ensure_work(const fwi_opts &o) {
   Work<T> &w = work<T>();
   if (w.ready) return;
-  for (int l = 1; l <= ls && l < nlev_max; ++l) {
+  for (int l = 1; l <= ls_p[sizeof(T) == 8] && l < nlev_max; ++l) {
     w.lx[l].alloc(lv[l].field); w.lb[l].alloc(lv[l].field); w.lt[l].alloc(lv[l].field);
   }
   w.t0a.alloc(F0); w.t0b.alloc(F0);
@@ -667,8 +697,31 @@ template <typename T>
 void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
                    typename cplx<T>::t *y, bool opA, int level) {
   LevelView<T> L = opA ? viewA<T>() : viewM<T>(level);
+  bool timed = false;
+  if (timer_on && level == 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    timed = cs == cudaStreamCaptureStatusNone;
+  }
+  if (timed) {
+    if (ev_used == ev_a.size()) {
+      cudaEvent_t a, b2;
+      CK(cudaEventCreate(&a));
+      CK(cudaEventCreate(&b2));
+      ev_a.push_back(a); ev_b.push_back(b2); ev_bytes.push_back(0.0);
+    }
+    CK(cudaEventRecord(ev_a[ev_used], st));
+  }
   k_field_op<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, cj, wj, x, b, y);
   KCHECK();
+  if (timed) {
+    CK(cudaEventRecord(ev_b[ev_used], st));
+    // algorithmic bytes: each complex element read/written once
+    int streams = (mode == FM_APPLY || mode == FM_JACOBI0) ? 2 : 3;
+    ev_bytes[ev_used] = (double)streams * (double)F0 * sizeof(typename cplx<T>::t);
+    ++ev_used;
+    if (ev_used >= 4096) sync();
+  }
 }
 
 template <typename T>
@@ -690,10 +743,12 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
   CoarseArgs ca;
   for (int l = 0; l < MAX_LEVELS; ++l) ca.blks[l] = l < nlev_max ? lv[l].blksM.p : nullptr;
   ca.ops = d_ops.p; ca.inv = inv.p; ca.inv_off = inv_off.p; ca.inst_nlev = d_inst_nlev.p;
+  const int ls = ls_p[sizeof(T) == 8];
   ca.ls = ls; ca.nu1 = o.nu1; ca.nu2 = o.nu2; ca.cyc = o.mg_cycle; ca.cj = cj; ca.w = o.omega_jac;
+  ca.wdepth = o.mg_wdepth;
   size_t smem = smem_bytes[sizeof(T) == 8];
   if (ls == 0) {
-    k_coarse_cycle<T><<<B, 256, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
+    k_coarse_cycle<T><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
     KCHECK();
     return;
   }
@@ -702,7 +757,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
   std::function<T2 *(int, const T2 *, T2 *, T2 *)> cyc;
   cyc = [&](int l, const T2 *bl, T2 *xa, T2 *xb) -> T2 * {
     if (l == ls) {
-      k_coarse_cycle<T><<<B, 256, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), bl, xa);
+      k_coarse_cycle<T><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), bl, xa);
       KCHECK();
       return xa;
     }
@@ -712,7 +767,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
       field_op<T>(s == 0 ? FM_JACOBI0 : FM_JACOBI, cj, wj, s == 0 ? nullptr : cur, bl, s == 0 ? cur : oth, false, l);
       if (s > 0) std::swap(cur, oth);
     }
-    int reps = l == 0 ? 1 : o.mg_cycle;
+    int reps = (l > 0 && l <= o.mg_wdepth) ? o.mg_cycle : 1;
     for (int r = 0; r < reps; ++r) {
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
       k_resid_restrict<T><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cj, cur, bl, w.lb[l + 1].p);
@@ -742,17 +797,19 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
   CoarseArgs ca;
   for (int l = 0; l < MAX_LEVELS; ++l) ca.blks[l] = l < nlev_max ? lv[l].blksM.p : nullptr;
   ca.ops = d_ops.p; ca.inv = inv.p; ca.inv_off = inv_off.p; ca.inst_nlev = d_inst_nlev.p;
+  const int ls = ls_p[sizeof(T) == 8];
   ca.ls = ls; ca.nu1 = o.nu1; ca.nu2 = o.nu2; ca.cyc = o.mg_cycle; ca.cj = cj; ca.w = o.omega_jac;
+  ca.wdepth = o.mg_wdepth;
   size_t smem = smem_bytes[sizeof(T) == 8];
   if (ls == 0) {
-    k_coarse_cycle<T><<<B, 256, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
+    k_coarse_cycle<T><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
     KCHECK();
     return;
   }
   std::function<T2 *(int, const T2 *, T2 *, T2 *)> cyc;
   cyc = [&](int l, const T2 *bl, T2 *xa, T2 *xb) -> T2 * {
     if (l == ls) {
-      k_coarse_cycle<T><<<B, 256, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), bl, xa);
+      k_coarse_cycle<T><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), bl, xa);
       KCHECK();
       return xa;
     }
@@ -762,7 +819,7 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
       field_op<T>(s == 0 ? FM_JACOBI0 : FM_JACOBI, cj, wj, s == 0 ? nullptr : cur, bl, s == 0 ? cur : oth, false, l);
       if (s > 0) std::swap(cur, oth);
     }
-    int reps = l == 0 ? 1 : o.mg_cycle;
+    int reps = (l > 0 && l <= o.mg_wdepth) ? o.mg_cycle : 1;
     for (int r = 0; r < reps; ++r) {
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
       k_resid_restrict<T><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cj, cur, bl, lb[l + 1]);
@@ -889,8 +946,8 @@ void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, con
   bool graphable = o.use_graph && !(o.inner_tol > 0.0);
   if (!graphable) { precond<T>(v, z, o, count, u); return; }
   char key[256];
-  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p", hier_key.c_str(), o.inner_iters, o.mg_cycle,
-           o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta, (const void *)u);
+  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p", hier_key.c_str(), o.inner_iters, o.mg_cycle,
+           o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta, (const void *)u);
   if (w.graph_key != key) {
     if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
     cudaGraph_t gr;
@@ -1397,7 +1454,7 @@ static std::string g_create_error;
 
 static int check_opts(const fwi_opts *o) {
   if (!o) return 0;
-  if (o->restart < 1 || o->restart > 200 || o->nu1 < 0 || o->nu2 < 0 || o->mg_cycle < 1 || o->mg_cycle > 2 ||
+  if (o->restart < 1 || o->restart > 200 || o->nu1 < 0 || o->nu2 < 0 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_wdepth < 0 ||
       o->inner_iters < 1 || o->fwd_iters < 1 || !(o->tol > 0.0) || o->max_outer < 1 ||
       (o->precision != FWI_C128 && o->precision != FWI_C64_REFINE))
     return 0;
@@ -1419,6 +1476,7 @@ void fwi_default_opts(fwi_opts *o) {
   o->inner_iters = 8;
   o->inner_tol = 0.0;
   o->mg_cycle = 2;
+  o->mg_wdepth = 2;
   o->nu1 = 2;
   o->nu2 = 2;
   o->omega_jac = 0.5;
@@ -1784,7 +1842,8 @@ static int mg_cycle_noalloc_impl(fwi::Ctx &c, const fwi_opts &o, const void *b, 
   // each rounded up to 256 bytes
   auto up = [](size_t n) { return (n + 255) / 256 * 256; };
   size_t need = up(c.F0 * sizeof(T2));
-  for (int l = 1; l <= c.ls && l < c.nlev_max; ++l) need += 3 * up(c.lv[l].field * sizeof(T2));
+  const int lsT = c.ls_p[sizeof(T) == 8];
+  for (int l = 1; l <= lsT && l < c.nlev_max; ++l) need += 3 * up(c.lv[l].field * sizeof(T2));
   if (need > (size_t)FWI_NOALLOC_SCRATCH_BYTES)
     fwi::fail(FWI_E_INVAL, "fwi_mg_cycle_noalloc: the batch needs " + std::to_string(need) +
                                " bytes of scratch, more than FWI_NOALLOC_SCRATCH_BYTES (" +
@@ -1805,7 +1864,7 @@ static int mg_cycle_noalloc_impl(fwi::Ctx &c, const fwi_opts &o, const void *b, 
   T2 *t0 = (T2 *)(base + off);
   off += up(c.F0 * sizeof(T2));
   T2 *lx[MAX_LEVELS] = {}, *lb[MAX_LEVELS] = {}, *lt[MAX_LEVELS] = {};
-  for (int l = 1; l <= c.ls && l < c.nlev_max; ++l) {
+  for (int l = 1; l <= lsT && l < c.nlev_max; ++l) {
     size_t bytes = up(c.lv[l].field * sizeof(T2));
     lx[l] = (T2 *)(base + off); off += bytes;
     lb[l] = (T2 *)(base + off); off += bytes;
@@ -1855,6 +1914,21 @@ int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info) {
 }
 
 unsigned long long fwi_kernel_launches(void) { return fwi::g_launches.load(); }
+
+int fwi_stencil_timer(fwi_ctx *ctx, int enable, double *ms, double *bytes, long long *launches) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  if (c.st) c.sync();
+  if (ms) *ms = c.timer_ms;
+  if (bytes) *bytes = c.timer_bytes;
+  if (launches) *launches = c.timer_n;
+  if (enable >= 0) {
+    c.timer_on = enable > 0;
+    c.timer_ms = 0.0; c.timer_bytes = 0.0; c.timer_n = 0;
+  }
+  return FWI_OK;
+  API_END(ctx)
+}
 
 const char *fwi_last_error(const fwi_ctx *ctx) {
   if (!ctx) return g_create_error.c_str();

@@ -93,13 +93,13 @@ def test_adjoint_identity(setup):
 def _oracle_hier(P, w, p, fidx, opts):
     return mg.Hierarchy(w.grid, p.omegas[fidx], p.gamma_pad(w.gamma_start.ravel()), shift=opts.shift_beta,
                         nu1=opts.nu1, nu2=opts.nu2, wj=opts.omega_jac, cycle=opts.mg_cycle,
-                        sigma_cap=opts.sigma_cap)
+                        sigma_cap=opts.sigma_cap, wdepth=opts.mg_wdepth)
 
 
-@pytest.mark.parametrize("cycle", [1, 2])
-def test_multigrid_cycle(setup, cycle):
+@pytest.mark.parametrize("cycle,wdepth", [(1, 2), (2, 2), (2, 9)])
+def test_multigrid_cycle(setup, cycle, wdepth):
     P, f, wls, probs, _ = setup
-    opts = P.default_opts(mg_cycle=cycle)
+    opts = P.default_opts(mg_cycle=cycle, mg_wdepth=wdepth)
     n = f.layout()["field_elems"]
     bt, b = _rand_field(n, 6)
     x = f.mg_cycle(bt, opts).cpu().numpy()
