@@ -75,7 +75,7 @@ typedef struct {
   int max_outer;          /* cap on FGMRES iterations over all sweeps          [600]  */
   double sweep_tol;       /* c64 FGMRES tolerance per refinement sweep         [1e-3] */
   int max_refine;         /* cap on FP64 refinement sweeps                     [8]    */
-  int inner_iters;        /* BiCGStab iterations per preconditioner block solve [8]  */
+  int inner_iters;        /* BiCGStab iterations per preconditioner block solve [4]  */
   double inner_tol;       /* > 0: stop a block's inner solve at this relative
                              residual (exact-preconditioner mode uses 1e-12)   [0]    */
   int mg_cycle;           /* cycle index on levels 1..mg_wdepth (2 = W)        [2]    */

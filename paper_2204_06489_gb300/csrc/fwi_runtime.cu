@@ -1473,7 +1473,7 @@ void fwi_default_opts(fwi_opts *o) {
   o->max_outer = 600;
   o->sweep_tol = 1e-3;
   o->max_refine = 8;
-  o->inner_iters = 8;
+  o->inner_iters = 4;
   o->inner_tol = 0.0;
   o->mg_cycle = 2;
   o->mg_wdepth = 2;

@@ -1,0 +1,178 @@
+"""GPU checks of the drivers around the KKT solve: the autograd function
+(hand-written adjoint), Newton steps (step-wise parity with the oracle),
+frequency continuation, batching of independent instances, graph replay and
+the two precision forms."""
+import numpy as np
+import pytest
+from scipy.ndimage import gaussian_filter
+
+import fwi_inputs as FI
+from oracle import fwi, kkt
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _obs_array(wl, prob, d):
+    arr = np.zeros((wl.survey.n_freq, int(wl.survey.rec_offsets[-1])), dtype=complex)
+    for b in range(prob.n_blocks):
+        k = prob.block_src(b)
+        arr[prob.block_freq(b), wl.survey.rec_offsets[k]:wl.survey.rec_offsets[k + 1]] = d[b]
+    return arr
+
+
+def _setup(wl):
+    import paper_2204_06489_gb300 as P
+    prob = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    d = fwi.sample(prob, fwi.forward(prob, wl.gamma_true.ravel()))
+    f = P.from_workload(wl)
+    f.set_observed(0, _obs_array(wl, prob, d))
+    return P, f, prob, d
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.mark.parametrize("mode", ["save", "recompute"])
+def test_autograd_misfit_gradient(lib, mode):
+    """HelmholtzMisfit: backward vs the oracle gradient (<= 1e-4) and vs central
+    differences of its own forward along smooth random directions (<= 1e-3)."""
+    from paper_2204_06489_gb300.autograd import misfit
+    wl = FI.micro_workload(seed=4, nx=41, nz=21, npml=8, n_src=3, n_rec=8)
+    P, f, prob, d = _setup(wl)
+    g0 = torch.tensor(wl.gamma_start, dtype=torch.float64, device="cuda", requires_grad=True)
+    phi = misfit(g0, f, mode=mode)
+    phi.backward()
+    grad = g0.grad.detach().cpu().numpy().ravel()
+    phi_o, grad_o = fwi.gradient(prob, wl.gamma_start.ravel(), d)
+    assert abs(phi.item() - phi_o) <= 1e-6 * phi_o
+    assert _rel(grad, grad_o) < 1e-4
+    s0 = wl.gamma_start
+    for seed in range(3):
+        dirn = gaussian_filter(np.random.default_rng(seed).standard_normal(s0.shape), 3.0)
+        dirn *= 0.003 * s0.mean() / np.abs(dirn).max()
+        with torch.no_grad():
+            fp = misfit(torch.tensor(s0 + dirn, device="cuda"), f, mode=mode).item()
+            fm = misfit(torch.tensor(s0 - dirn, device="cuda"), f, mode=mode).item()
+        fd = (fp - fm) / 2
+        an = float(np.dot(grad, dirn.ravel()))
+        assert abs(fd - an) <= 1e-3 * abs(an), (seed, fd, an)
+    f.close()
+
+
+def test_autograd_save_equals_recompute(lib):
+    from paper_2204_06489_gb300.autograd import misfit
+    wl = FI.micro_workload(seed=5, nx=31, nz=17, npml=6, n_src=2, n_rec=6)
+    P, f, prob, d = _setup(wl)
+    gs = []
+    for mode in ("save", "recompute"):
+        g0 = torch.tensor(wl.gamma_start, dtype=torch.float64, device="cuda", requires_grad=True)
+        misfit(g0, f, mode=mode).backward()
+        gs.append(g0.grad.cpu().numpy())
+    assert _rel(gs[0], gs[1]) < 1e-7
+    f.close()
+
+
+def test_newton_steps_stepwise_parity(lib):
+    """Two Gauss-Newton steps on the GPU; at every model s_n the GPU reached,
+    the oracle's direct KKT solve gives the same update (<= 1e-5), and the first
+    full step lowers the misfit (the trajectory itself is not pinned end to end;
+    full steps without line search need not decrease the misfit every time)."""
+    wl = FI.micro_workload(seed=6, nx=41, nz=21, npml=8, n_src=3, n_rec=8)
+    P, f, prob, d = _setup(wl)
+    opts = P.default_opts(eps=1e-2, tol=1e-8, include_Ls_n=0)
+    mis = []
+    for step in range(2):
+        s_n = f.get_model(0).ravel()
+        _, m, _ = f.forward(opts, want_data=False)
+        mis.append(m[0])
+        ds, st = f.newton_step(opts)
+        K = kkt.KKT(prob, s_n, d, 1e-2, include_Ls_n=False)
+        ref = K.delta_s(K.solve_direct())
+        assert st["rel_res"] <= 1e-8
+        assert _rel(ds, ref) < 1e-5, (step, _rel(ds, ref))
+    assert mis[1] < mis[0]
+    f.close()
+
+
+def test_frequency_continuation_reduces_misfit(lib):
+    import paper_2204_06489_gb300 as P
+    from paper_2204_06489_gb300.newton import frequency_continuation
+    wl = FI.micro_workload(seed=7, nx=41, nz=21, npml=8, n_src=3, n_rec=8)
+    freqs = [3.0, 5.0, 7.0]
+
+    def observed(fq):
+        sv = FI.Survey(**{**wl.survey.__dict__, "freqs_hz": [fq]})
+        p = fwi.Problem.create(wl.grid, sv, wl.gamma_start)
+        dd = fwi.sample(p, fwi.forward(p, wl.gamma_true.ravel()))
+        return _obs_array(FI.Workload("x", wl.grid, sv, wl.gamma_true, wl.gamma_start), p, dd)
+
+    opts = P.default_opts(eps=1e-2, include_Ls_n=0)
+    g, log = frequency_continuation(wl.grid, wl.survey, wl.gamma_start, observed, freqs, 1, opts)
+    assert len(log) == 3
+    for st in log:
+        assert st["misfit_after"] < st["misfit_before"] if "misfit_after" in st else True
+    err0 = np.linalg.norm(wl.gamma_start - wl.gamma_true)
+    err1 = np.linalg.norm(g - wl.gamma_true)
+    assert err1 < err0
+
+
+def test_batched_instances_equal_separate_solves(lib):
+    """Two instances of different grid sizes solved in one batch give the same
+    updates as each solved alone (independent problems; ragged launches)."""
+    import paper_2204_06489_gb300 as P
+    wa = FI.micro_workload(seed=8, nx=41, nz=21, npml=8, n_src=3, n_rec=8)
+    wb = FI.micro_workload(seed=9, nx=29, nz=25, npml=6, n_src=2, n_rec=5, freq=6.0)
+    opts = P.default_opts(eps=1e-2, tol=1e-8)
+    sep = []
+    datas = []
+    for w in (wa, wb):
+        Pm, f, prob, d = _setup(w)
+        datas.append(_obs_array(w, prob, d))
+        f.forward(opts, want_data=False)
+        ds, st = f.kkt_solve(opts)
+        sep.append(ds)
+        f.close()
+    fb = P.from_workload([wa, wb])
+    fb.set_observed(0, datas[0])
+    fb.set_observed(1, datas[1])
+    fb.forward(opts, want_data=False)
+    ds, st = fb.kkt_solve(opts)
+    n0 = wa.grid.nx * wa.grid.nz
+    assert _rel(ds[:n0], sep[0]) < 1e-6
+    assert _rel(ds[n0:], sep[1]) < 1e-6
+    fb.close()
+
+
+def test_graph_replay_equals_direct_launches_and_precisions_agree(lib):
+    import paper_2204_06489_gb300 as P
+    wl = FI.micro_workload(seed=10, nx=41, nz=21, npml=8, n_src=3, n_rec=8)
+    Pm, f, prob, d = _setup(wl)
+    out = {}
+    for name, kw in (("graph", dict(use_graph=1)), ("direct", dict(use_graph=0)),
+                     ("c128", dict(precision=P.FWI_C128))):
+        opts = P.default_opts(eps=1e-2, tol=1e-8, **kw)
+        f.forward(opts, want_data=False)
+        ds, st = f.kkt_solve(opts)
+        assert st["rel_res"] <= 1e-8
+        out[name] = ds
+    assert _rel(out["graph"], out["direct"]) < 1e-12
+    assert _rel(out["c128"], out["graph"]) < 1e-6
+    f.close()
+
+
+def test_autotuner_picks_a_converging_schedule(lib):
+    import paper_2204_06489_gb300 as P
+    from paper_2204_06489_gb300.autotune import tune_inner
+    wl = FI.tiny_workload()
+    f = P.from_workload(wl)
+    n = f.layout()["field_elems"]
+    g = np.random.default_rng(1)
+    b = torch.from_numpy((g.standard_normal(n) + 1j * g.standard_normal(n)).astype(np.complex64)).cuda()
+    best, table = tune_inner(f, b, P.default_opts(inner_iters=3), nus=(1, 2), omegas=(0.5,), wdepths=(1, 2))
+    assert len(table) == 4
+    rates = {(t[0], t[2]): t[6] for t in table}
+    assert rates[(best.nu1, best.mg_wdepth)] == max(rates.values())
+    assert all(t[4] < 1.0 for t in table)
+    f.close()
