@@ -53,6 +53,7 @@ struct OpDev {
   int nx, nz;            // grid of this level
   long long st;          // offset of the stretch arrays (complex): X[nx], 1/Xh[nx+1], Z[nz], 1/Zh[nz+1]
   long long gam;         // offset of gamma on this level (real, [nz][nx])
+  long long dg;          // offset of the diagonal cc and its inverse (complex, [nz][nx])
   double mass_re, mass_im;  // (1 + i beta) (omega h_l)^2
 };
 
@@ -75,6 +76,8 @@ template <typename T> struct LevelView {
   const TileDev *tiles;
   const typename cplx<T>::t *st;   // stretch arrays (precision T)
   const T *gam;                    // gamma values (precision T)
+  const typename cplx<T>::t *dg;   // diagonal of every operator (precision T)
+  const typename cplx<T>::t *dgi;  // its inverse
   int n_tiles;
   int n_blocks;
 };

@@ -13,34 +13,31 @@ namespace fwi {
 // ---------------------------------------------------------------------------
 // Dot-product accumulation.  GB300's FP64 throughput is a small fraction of
 // its FP32 rate, so per-element FP64 arithmetic turns a bandwidth-bound dot
-// into an ALU-bound one.  Products of float data are accumulated per thread
-// in "double-float" (an unevaluated sum hi + lo of two floats): Dekker's
-// exact product via FMA and Knuth's TwoSum keep about 44 significant bits, and
-// only the per-thread results are combined in FP64.
+// into an ALU-bound one.  For complex64 data each thread accumulates products
+// in FP32 over runs of at most DOT_RUN elements and adds every run into an
+// FP64 total (the error of a run stays at single-precision level relative to
+// that run, and runs combine in double); threads then combine in FP64.
+// complex128 data accumulate in FP64 throughout.
 // ---------------------------------------------------------------------------
-struct DF {
-  float hi, lo;
-};
-__device__ __forceinline__ void df_add_prod(DF &a, float x, float y) {
-  float p = x * y;
-  float pe = __fmaf_rn(x, y, -p);          // x*y = p + pe exactly
-  float s = __fadd_rn(a.hi, p);            // TwoSum(a.hi, p) = s + e exactly
-  float bb = __fsub_rn(s, a.hi);
-  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  e = __fadd_rn(e, __fadd_rn(a.lo, pe));
-  a.hi = __fadd_rn(s, e);                  // renormalise
-  a.lo = __fsub_rn(e, __fsub_rn(a.hi, s));
-}
-__device__ __forceinline__ double df_value(const DF &a) { return (double)a.hi + (double)a.lo; }
+#define DOT_RUN 16
 
-// acc += x*y for the accumulator type of the data precision
-__device__ __forceinline__ void acc_prod(DF &a, float x, float y) { df_add_prod(a, x, y); }
-__device__ __forceinline__ void acc_prod(double &a, double x, double y) { a = fma(x, y, a); }
-__device__ __forceinline__ double acc_value(const DF &a) { return df_value(a); }
-__device__ __forceinline__ double acc_value(double a) { return a; }
-template <typename T> struct Acc;
-template <> struct Acc<float> { typedef DF t; static __device__ __forceinline__ DF zero() { DF z; z.hi = 0.f; z.lo = 0.f; return z; } };
-template <> struct Acc<double> { typedef double t; static __device__ __forceinline__ double zero() { return 0.0; } };
+// Loads of the small per-operator arrays (stretch factors, diagonal) that every
+// source of a frequency re-reads: keep them in L2 while the fields stream past.
+__device__ __forceinline__ unsigned long long keep_policy() {
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float2 ld_keep(const float2 *p) {
+  float2 v;
+  asm("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(keep_policy()));
+  return v;
+}
+__device__ __forceinline__ double2 ld_keep(const double2 *p) {
+  double2 v;
+  asm("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(keep_policy()));
+  return v;
+}
 
 // ---------------------------------------------------------------------------
 // stencil coefficients
@@ -95,65 +92,55 @@ __device__ __forceinline__ double2 cinv(double2 z) {
   return make_double2(z.x * r, -z.y * r);
 }
 
-// The 5-point operator along one grid row j, with the row-constant factors
-// (Z_j, 1/Z_{j-1/2}, 1/Z_{j+1/2}, the mass factor) loaded once.  Same
-// arithmetic as Stencil, regrouped: with sZ = 1/Z_{j-1/2} + 1/Z_{j+1/2},
-//   cc = Z_j (1/X_{i-1/2} + 1/X_{i+1/2}) + X_i (sZ - m Z_j gamma_ij)
+// The 5-point operator along one grid row j.  Row constants (Z_j,
+// 1/Z_{j-1/2}, 1/Z_{j+1/2}) are loaded once; the diagonal cc and 1/cc come
+// from per-operator arrays computed at set-up (shared by all sources of a
+// frequency, L2-resident), so a node costs
 //   (Op u)_ij = cc u_ij - Z_j (u_i+1,j / X_{i+1/2} + u_i-1,j / X_{i-1/2})
 //                       - X_i (u_i,j+1 / Z_{j+1/2} + u_i,j-1 / Z_{j-1/2}),
-// every factor conjugated when cj (A^H = conj A).
-template <typename T>
+// every factor conjugated when CJ (A^H = conj A, A^T = A).
+template <typename T, bool CJ>
 struct RowOp {
   typedef typename cplx<T>::t T2;
-  const T2 *X, *iXh;
-  const T *g;
-  T2 Zj, iZn, iZs, sZ, mZ;
-  bool cj;
+  const T2 *X, *iXh, *dg, *dgi;
+  T2 Zj, iZn, iZs;
   int nx, nz, j;
-  __device__ __forceinline__ RowOp(const OpDev &op, const T2 *__restrict__ st, const T *__restrict__ gam, int j_,
-                                   bool cj_) {
+  __device__ __forceinline__ RowOp(const OpDev &op, const T2 *__restrict__ st, const T2 *__restrict__ dgb,
+                                   const T2 *__restrict__ dgib, int j_) {
     X = st + op.st;
     iXh = X + op.nx;
     const T2 *Z = iXh + op.nx + 1;
     const T2 *iZh = Z + op.nz;
-    nx = op.nx; nz = op.nz; j = j_; cj = cj_;
-    g = gam + op.gam + (long long)j * op.nx;
-    Zj = cmaybe_conj(Z[j], cj);
-    iZn = cmaybe_conj(iZh[j], cj);
-    iZs = cmaybe_conj(iZh[j + 1], cj);
-    sZ = cadd(iZn, iZs);
-    mZ = cmul(cmaybe_conj(mk<T2>(op.mass_re, op.mass_im), cj), Zj);
+    nx = op.nx; nz = op.nz; j = j_;
+    dg = dgb + op.dg + j * op.nx;
+    dgi = dgib + op.dg + j * op.nx;
+    Zj = cmaybe_conj(Z[j], CJ);
+    iZn = cmaybe_conj(iZh[j], CJ);
+    iZs = cmaybe_conj(iZh[j + 1], CJ);
   }
-  // returns (Op u)_ij and the diagonal cc; u points at the block's grid
-  __device__ __forceinline__ T2 apply(const T2 *__restrict__ u, int i, T2 &cc) const {
-    T2 Xi = cmaybe_conj(X[i], cj);
-    T2 iw = cmaybe_conj(iXh[i], cj);
-    T2 ie = cmaybe_conj(iXh[i + 1], cj);
-    T gi = g[i];
-    long long k = (long long)j * nx + i;
-    T2 uc = u[k];
-    T2 ue = i + 1 < nx ? u[k + 1] : mk<T2>(0, 0);
-    T2 uw = i > 0 ? u[k - 1] : mk<T2>(0, 0);
-    T2 us = j + 1 < nz ? u[k + nx] : mk<T2>(0, 0);
-    T2 un = j > 0 ? u[k - nx] : mk<T2>(0, 0);
-    cc = cadd(cmul(Zj, cadd(iw, ie)), cmul(Xi, csub(sZ, cscale(mZ, gi))));
+  __device__ __forceinline__ T2 diag(int i) const { return cmaybe_conj(ld_keep(dg + i), CJ); }
+  __device__ __forceinline__ T2 dinv(int i) const { return cmaybe_conj(ld_keep(dgi + i), CJ); }
+  // (Op u)_ij; urow points at row j of the block's grid
+  __device__ __forceinline__ T2 apply(const T2 *__restrict__ urow, int i) const {
+    T2 Xi = cmaybe_conj(ld_keep(X + i), CJ);
+    T2 iw = cmaybe_conj(ld_keep(iXh + i), CJ);
+    T2 ie = cmaybe_conj(ld_keep(iXh + i + 1), CJ);
+    T2 uc = urow[i];
+    T2 ue = i + 1 < nx ? urow[i + 1] : mk<T2>(0, 0);
+    T2 uw = i > 0 ? urow[i - 1] : mk<T2>(0, 0);
+    T2 us = j + 1 < nz ? urow[i + nx] : mk<T2>(0, 0);
+    T2 un = j > 0 ? urow[i - nx] : mk<T2>(0, 0);
     T2 hx = cadd(cmul(ie, ue), cmul(iw, uw));
     T2 hz = cadd(cmul(iZs, us), cmul(iZn, un));
-    return csub(csub(cmul(cc, uc), cmul(Zj, hx)), cmul(Xi, hz));
-  }
-  __device__ __forceinline__ T2 diag(int i) const {
-    T2 Xi = cmaybe_conj(X[i], cj);
-    T2 iw = cmaybe_conj(iXh[i], cj);
-    T2 ie = cmaybe_conj(iXh[i + 1], cj);
-    return cadd(cmul(Zj, cadd(iw, ie)), cmul(Xi, csub(sZ, cscale(mZ, g[i]))));
+    return csub(csub(cmul(diag(i), uc), cmul(Zj, hx)), cmul(Xi, hz));
   }
 };
 
 // y = Op x | b - Op x | x + w (b - Op x)/cc | w b / cc  on every block of a level.
 // One warp per row, two columns per lane in flight.
-template <typename T>
+template <typename T, bool CJ>
 __global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 6 : 3)
-k_field_op(LevelView<T> L, int mode, int cj, T w, const typename cplx<T>::t *__restrict__ x,
+k_field_op(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__restrict__ x,
            const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
   typedef typename cplx<T>::t T2;
   const TileDev t = L.tiles[blockIdx.x];
@@ -161,10 +148,11 @@ k_field_op(LevelView<T> L, int mode, int cj, T w, const typename cplx<T>::t *__r
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);
   if (j >= op.nz) return;
-  const RowOp<T> R(op, L.st, L.gam, j, cj != 0);
-  const T2 *xb = x ? x + bk.off : nullptr;
-  const T2 *bb = b ? b + bk.off + (long long)j * op.nx : nullptr;
-  T2 *yb = y + bk.off + (long long)j * op.nx;
+  const RowOp<T, CJ> R(op, L.st, L.dg, L.dgi, j);
+  const long long row = bk.off + (long long)j * op.nx;
+  const T2 *xr = x ? x + row : nullptr;
+  const T2 *br = b ? b + row : nullptr;
+  T2 *yr = y + row;
   const int lane = threadIdx.x & 31;
   for (int i0 = lane; i0 < op.nx; i0 += 64) {
     T2 out[2];
@@ -173,19 +161,121 @@ k_field_op(LevelView<T> L, int mode, int cj, T w, const typename cplx<T>::t *__r
       int i = i0 + 32 * q;
       if (i < op.nx) {
         if (mode == FM_JACOBI0) {
-          out[q] = cscale(cmul(bb[i], cinv(R.diag(i))), w);
+          out[q] = cscale(cmul(br[i], R.dinv(i)), w);
         } else {
-          T2 cc;
-          T2 ax = R.apply(xb, i, cc);
+          T2 ax = R.apply(xr, i);
           if (mode == FM_APPLY) out[q] = ax;
-          else if (mode == FM_RESID) out[q] = csub(bb[i], ax);
-          else out[q] = cadd(xb[(long long)j * op.nx + i], cscale(cmul(csub(bb[i], ax), cinv(cc)), w));
+          else if (mode == FM_RESID) out[q] = csub(br[i], ax);
+          else out[q] = cadd(xr[i], cscale(cmul(csub(br[i], ax), R.dinv(i)), w));
         }
       }
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-      if (i0 + 32 * q < op.nx) yb[i0 + 32 * q] = out[q];
+      if (i0 + 32 * q < op.nx) yr[i0 + 32 * q] = out[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory staged variant of k_field_op for the big levels: a CTA stages
+// its 8 rows plus one halo row above and below, in chunks of FT_CW columns
+// plus a one-column halo, with asynchronous 8/16-byte copies (cp.async, all
+// loads in flight at once), then applies the stencil from shared memory.
+// Nodes outside the grid are staged as zeros (Dirichlet ghosts).
+// ---------------------------------------------------------------------------
+#define FT_CW 128
+#define FT_W (FT_CW + 2)
+#define FT_R (TILE_ROWS + 2)
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+}
+template <typename T2> __device__ __forceinline__ void cp_async_elem(T2 *smem, const T2 *gmem);
+template <> __device__ __forceinline__ void cp_async_elem<float2>(float2 *smem, const float2 *gmem) { cp_async8(smem, gmem); }
+template <> __device__ __forceinline__ void cp_async_elem<double2>(double2 *smem, const double2 *gmem) { cp_async16(smem, gmem); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename T, bool CJ>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__restrict__ x,
+                const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
+  typedef typename cplx<T>::t T2;
+  __shared__ __align__(16) T2 xs[FT_R][FT_W];
+  __shared__ __align__(16) T2 bs[TILE_ROWS][FT_CW];
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlkDev bk = L.blks[t.blk];
+  const OpDev op = L.ops[bk.op];
+  const int nx = op.nx, nz = op.nz;
+  const int j0 = t.row0;
+  const T2 *xb = x ? x + bk.off : nullptr;
+  const T2 *bb = b ? b + bk.off : nullptr;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = j0 + warp;
+  const bool row_ok = j < nz;
+  // row constants of this warp's row
+  const T2 *X = L.st + op.st;
+  const T2 *iXh = X + nx;
+  const T2 *Zr = iXh + nx + 1;
+  const T2 *iZh = Zr + nz;
+  T2 Zj = mk<T2>(0, 0), iZn = Zj, iZs = Zj;
+  if (row_ok) {
+    Zj = cmaybe_conj(Zr[j], CJ);
+    iZn = cmaybe_conj(iZh[j], CJ);
+    iZs = cmaybe_conj(iZh[j + 1], CJ);
+  }
+  const T2 *dgr = L.dg + op.dg + (long long)j * nx;
+  const T2 *dgir = L.dgi + op.dg + (long long)j * nx;
+  const bool need_x = mode != FM_JACOBI0;
+  for (int c0 = 0; c0 < nx; c0 += FT_CW) {
+    // stage x rows j0-1..j0+8, columns c0-1..c0+FT_CW, and b rows j0..j0+7
+    if (need_x) {
+      for (int q = threadIdx.x; q < FT_R * FT_W; q += TILE_THREADS) {
+        int r = q / FT_W, c = q - r * FT_W;
+        int jj = j0 - 1 + r, ii = c0 - 1 + c;
+        if (jj >= 0 && jj < nz && ii >= 0 && ii < nx) cp_async_elem(&xs[r][c], xb + (long long)jj * nx + ii);
+        else xs[r][c] = mk<T2>(0, 0);
+      }
+    }
+    if (mode != FM_APPLY) {
+      for (int q = threadIdx.x; q < TILE_ROWS * FT_CW; q += TILE_THREADS) {
+        int r = q / FT_CW, c = q - r * FT_CW;
+        int jj = j0 + r, ii = c0 + c;
+        if (jj < nz && ii < nx) cp_async_elem(&bs[r][c], bb + (long long)jj * nx + ii);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (row_ok) {
+#pragma unroll
+      for (int q = 0; q < FT_CW / 32; ++q) {
+        int c = lane + 32 * q;
+        int i = c0 + c;
+        if (i < nx) {
+          T2 out;
+          if (mode == FM_JACOBI0) {
+            out = cscale(cmul(bs[warp][c], cmaybe_conj(ld_keep(dgir + i), CJ)), w);
+          } else {
+            T2 Xi = cmaybe_conj(ld_keep(X + i), CJ);
+            T2 iw = cmaybe_conj(ld_keep(iXh + i), CJ);
+            T2 ie = cmaybe_conj(ld_keep(iXh + i + 1), CJ);
+            const T2 *xc = &xs[warp + 1][c + 1];
+            T2 hx = cadd(cmul(ie, xc[1]), cmul(iw, xc[-1]));
+            T2 hz = cadd(cmul(iZs, xc[FT_W]), cmul(iZn, xc[-FT_W]));
+            T2 ax = csub(csub(cmul(cmaybe_conj(ld_keep(dgr + i), CJ), xc[0]), cmul(Zj, hx)), cmul(Xi, hz));
+            if (mode == FM_APPLY) out = ax;
+            else if (mode == FM_RESID) out = csub(bs[warp][c], ax);
+            else out = cadd(xc[0], cscale(cmul(csub(bs[warp][c], ax), cmaybe_conj(ld_keep(dgir + i), CJ)), w));
+          }
+          y[bk.off + (long long)j * nx + i] = out;
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -198,9 +288,9 @@ k_field_op(LevelView<T> L, int mode, int cj, T w, const typename cplx<T>::t *__r
 #define RR_CW 64
 #define RR_FW (2 * RR_CW + 1)
 #define RR_FR (2 * TILE_ROWS + 1)
-template <typename T>
+template <typename T, bool CJ>
 __global__ void __launch_bounds__(TILE_THREADS)
-k_resid_restrict(LevelView<T> Lf, LevelView<T> Lc, int cj, const typename cplx<T>::t *__restrict__ xf,
+k_resid_restrict(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__restrict__ xf,
                  const typename cplx<T>::t *__restrict__ bf, typename cplx<T>::t *__restrict__ bc) {
   typedef typename cplx<T>::t T2;
   __shared__ T2 r[RR_FR][RR_FW];
@@ -219,14 +309,13 @@ k_resid_restrict(LevelView<T> Lf, LevelView<T> Lc, int cj, const typename cplx<T
     for (int rr = warp; rr < RR_FR; rr += TILE_ROWS) {
       int j = jf0 + rr;
       if (j < opf.nz) {
-        const RowOp<T> R(opf, Lf.st, Lf.gam, j, cj != 0);
+        const RowOp<T, CJ> R(opf, Lf.st, Lf.dg, Lf.dgi, j);
+        const T2 *xr = xb + (long long)j * opf.nx;
+        const T2 *br = bb + (long long)j * opf.nx;
         for (int c = lane; c < RR_FW; c += 32) {
           int i = if0 + c;
           T2 v = mk<T2>(0, 0);
-          if (i < opf.nx) {
-            T2 cc;
-            v = csub(bb[(long long)j * opf.nx + i], R.apply(xb, i, cc));
-          }
+          if (i < opf.nx) v = csub(br[i], R.apply(xr, i));
           r[rr][c] = v;
         }
       } else {
@@ -307,31 +396,31 @@ struct CoarseArgs {
   double w;
 };
 
-template <typename T>
+template <typename T, bool CJ>
 struct SmemCycle {
   typedef typename cplx<T>::t T2;
   const CoarseArgs &a;
-  const T2 *st;
-  const T *gam;
+  const T2 *st, *dg, *dgi;
   T2 *xs[MAX_LEVELS], *bs[MAX_LEVELS], *ts[MAX_LEVELS];
   OpDev op[MAX_LEVELS];
   int blk, nlev;
-  __device__ SmemCycle(const CoarseArgs &a_, const T2 *st_, const T *gam_) : a(a_), st(st_), gam(gam_) {}
+  __device__ SmemCycle(const CoarseArgs &a_, const T2 *st_, const T2 *dg_, const T2 *dgi_)
+      : a(a_), st(st_), dg(dg_), dgi(dgi_) {}
 
   __device__ void jacobi(int l, bool from_zero) {
     const OpDev &o = op[l];
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const T w = (T)a.w;
     for (int j = threadIdx.x >> 5; j < o.nz; j += nw) {
-      const RowOp<T> R(o, st, gam, j, a.cj != 0);
+      const RowOp<T, CJ> R(o, st, dg, dgi, j);
+      const T2 *xr = xs[l] + j * o.nx;
       for (int i = lane; i < o.nx; i += 32) {
         int k = j * o.nx + i;
         if (from_zero) {
-          ts[l][k] = cscale(cmul(bs[l][k], cinv(R.diag(i))), w);
+          ts[l][k] = cscale(cmul(bs[l][k], R.dinv(i)), w);
         } else {
-          T2 cc;
-          T2 ax = R.apply(xs[l], i, cc);
-          ts[l][k] = cadd(xs[l][k], cscale(cmul(csub(bs[l][k], ax), cinv(cc)), w));
+          T2 ax = R.apply(xr, i);
+          ts[l][k] = cadd(xr[i], cscale(cmul(csub(bs[l][k], ax), R.dinv(i)), w));
         }
       }
     }
@@ -342,11 +431,9 @@ struct SmemCycle {
     const OpDev &o = op[l];
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = threadIdx.x >> 5; j < o.nz; j += nw) {
-      const RowOp<T> R(o, st, gam, j, a.cj != 0);
-      for (int i = lane; i < o.nx; i += 32) {
-        T2 cc;
-        ts[l][j * o.nx + i] = csub(bs[l][j * o.nx + i], R.apply(xs[l], i, cc));
-      }
+      const RowOp<T, CJ> R(o, st, dg, dgi, j);
+      const T2 *xr = xs[l] + j * o.nx;
+      for (int i = lane; i < o.nx; i += 32) ts[l][j * o.nx + i] = csub(bs[l][j * o.nx + i], R.apply(xr, i));
     }
     __syncthreads();
     const OpDev &c = op[l + 1];
@@ -403,7 +490,7 @@ struct SmemCycle {
       double ax = 0.0, ay = 0.0;
       for (int c = lane; c < n; c += 32) {
         double2 m = M[(long long)r * n + c];
-        if (a.cj) m.y = -m.y;
+        if (CJ) m.y = -m.y;
         double2 v = to_d2(bs[l][c]);
         ax += m.x * v.x - m.y * v.y;
         ay += m.x * v.y + m.y * v.x;
@@ -456,14 +543,14 @@ struct SmemCycle {
   }
 };
 
-template <typename T>
+template <typename T, bool CJ>
 __global__ void k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restrict__ st,
-                               const T *__restrict__ gam, const typename cplx<T>::t *__restrict__ b,
-                               typename cplx<T>::t *__restrict__ x) {
+                               const typename cplx<T>::t *__restrict__ dg, const typename cplx<T>::t *__restrict__ dgi,
+                               const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ x) {
   typedef typename cplx<T>::t T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2 *sm = reinterpret_cast<T2 *>(smem_raw);
-  SmemCycle<T> c(a, st, gam);
+  SmemCycle<T, CJ> c(a, st, dg, dgi);
   c.blk = blockIdx.x;
   c.nlev = a.inst_nlev[a.blks[a.ls][c.blk].inst];
   size_t off = 0;
@@ -578,6 +665,24 @@ __global__ void k_gamma_restrict(const double *__restrict__ gf, int nxf, int nzf
   }
 }
 
+// Diagonal cc of every operator and its inverse (FP64 arithmetic, stored in
+// both precisions).  One CTA per operator.
+__global__ void k_diag_setup(const OpDev *ops, const double2 *st64, const double *gam64, double2 *dg64,
+                             double2 *dgi64, float2 *dg32, float2 *dgi32) {
+  const OpDev o = ops[blockIdx.x];
+  int n = o.nx * o.nz;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    int j = k / o.nx, i = k - j * o.nx;
+    Stencil<double> s;
+    s.load(o, st64, gam64, j, i, false);
+    double2 inv = cdiv(make_double2(1.0, 0.0), s.cc);
+    dg64[o.dg + k] = s.cc;
+    dgi64[o.dg + k] = inv;
+    dg32[o.dg + k] = make_float2((float)s.cc.x, (float)s.cc.y);
+    dgi32[o.dg + k] = make_float2((float)inv.x, (float)inv.y);
+  }
+}
+
 // Dense coarsest operator [M | I] (row-major n x 2n, complex128) of one op.
 __global__ void k_coarse_assemble(const OpDev *ops, const int *op_ids, const long long *aug_off,
                                   const double2 *st64, const double *gam64, double2 *aug) {
@@ -658,43 +763,45 @@ __global__ void k_gauss_jordan(const int *dims, const long long *aug_off, const 
 // per-block reductions and BiCGStab vector updates
 // ---------------------------------------------------------------------------
 // partial[tile][q] = sum over the tile of conj(a_q) b_q (q < nd): per-thread
-// double-float (complex64 data) or FP64 (complex128) accumulation, FP64
-// across threads; fixed order, no atomics.
+// run accumulation (see DOT_RUN), FP64 across threads; fixed order, no atomics.
 template <typename T>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typename cplx<T>::t *b0,
              const typename cplx<T>::t *a1, const typename cplx<T>::t *b1,
              const typename cplx<T>::t *a2, const typename cplx<T>::t *b2, double2 *partial) {
   typedef typename cplx<T>::t T2;
-  typedef typename Acc<T>::t A;
   const TileDev t = L.tiles[blockIdx.x];
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);
-  A re[3] = {Acc<T>::zero(), Acc<T>::zero(), Acc<T>::zero()};
-  A im[3] = {Acc<T>::zero(), Acc<T>::zero(), Acc<T>::zero()};
+  double tre[3] = {0, 0, 0}, tim[3] = {0, 0, 0};
+  T rre[3] = {0, 0, 0}, rim[3] = {0, 0, 0};
   const T2 *as[3] = {a0, a1, a2};
   const T2 *bs[3] = {b0, b1, b2};
   if (j < op.nz) {
     long long base = bk.off + (long long)j * op.nx;
+    int cnt = 0;
     for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         if (q < nd) {
           T2 a = as[q][base + i], b = bs[q][base + i];
           // conj(a) b = (ax bx + ay by) + i (ax by - ay bx)
-          acc_prod(re[q], a.x, b.x);
-          acc_prod(re[q], a.y, b.y);
-          acc_prod(im[q], a.x, b.y);
-          acc_prod(im[q], -a.y, b.x);
+          rre[q] = fma(a.x, b.x, fma(a.y, b.y, rre[q]));
+          rim[q] = fma(a.x, b.y, fma(-a.y, b.x, rim[q]));
         }
+      }
+      if (sizeof(T) == 4 && ++cnt == DOT_RUN) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) { tre[q] += rre[q]; tim[q] += rim[q]; rre[q] = 0; rim[q] = 0; }
+        cnt = 0;
       }
     }
   }
   __shared__ double2 red[3][TILE_THREADS / 32];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    double x = acc_value(re[q]), y = acc_value(im[q]);
+    double x = tre[q] + (double)rre[q], y = tim[q] + (double)rim[q];
     for (int o = 16; o > 0; o >>= 1) {
       x += __shfl_down_sync(0xffffffffu, x, o);
       y += __shfl_down_sync(0xffffffffu, y, o);
@@ -1009,28 +1116,34 @@ __global__ void k_update_model(const InstDev *inst, double *const *s_core, const
 #define FLAT_THREADS 256
 #define MD_CHUNK 8
 
-// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv (double-float or FP64
-// accumulation per thread, FP64 across threads; fixed grid, deterministic).
+// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv (run accumulation as
+// above, FP64 across threads; fixed grid, deterministic).
 template <typename T>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, double *partial) {
-  typedef typename Acc<T>::t A;
-  A acc[MD_CHUNK];
+  double tot[MD_CHUNK];
+  T run[MD_CHUNK];
 #pragma unroll
-  for (int v = 0; v < MD_CHUNK; ++v) acc[v] = Acc<T>::zero();
+  for (int v = 0; v < MD_CHUNK; ++v) { tot[v] = 0.0; run[v] = 0; }
   const T *vp[MD_CHUNK];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) vp[v] = v < nv ? V[v] : nullptr;
+  int cnt = 0;
   for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
     T wi = w[i];
 #pragma unroll
     for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) acc_prod(acc[v], vp[v][i], wi);
+      if (v < nv) run[v] = fma(vp[v][i], wi, run[v]);
+    if (sizeof(T) == 4 && ++cnt == DOT_RUN) {
+#pragma unroll
+      for (int v = 0; v < MD_CHUNK; ++v) { tot[v] += run[v]; run[v] = 0; }
+      cnt = 0;
+    }
   }
   __shared__ double red[MD_CHUNK][FLAT_THREADS / 32];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) {
-    double x = acc_value(acc[v]);
+    double x = tot[v] + (double)run[v];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = x;
   }
@@ -1070,15 +1183,19 @@ k_multi_axpy(long long n, int nv, const T *const *V, const double *coef, double 
   }
 }
 
-// partial[blockIdx.x] = sum x[i] y[i] (double-float / FP64 per thread, FP64
+// partial[blockIdx.x] = sum x[i] y[i] (run accumulation per thread, FP64
 // across threads, fixed grid)
 template <typename T>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_dot2(long long n, const T *__restrict__ x, const T *__restrict__ y, double *partial) {
-  typename Acc<T>::t a = Acc<T>::zero();
-  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS)
-    acc_prod(a, x[i], y[i]);
-  double acc = acc_value(a);
+  double tot = 0.0;
+  T run = 0;
+  int cnt = 0;
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
+    run = fma(x[i], y[i], run);
+    if (sizeof(T) == 4 && ++cnt == DOT_RUN) { tot += run; run = 0; cnt = 0; }
+  }
+  double acc = tot + (double)run;
   __shared__ double red[FLAT_THREADS / 32];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

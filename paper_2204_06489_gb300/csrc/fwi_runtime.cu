@@ -185,6 +185,8 @@ struct Ctx {
   DBuf<float> gam32;
   DBuf<double2> inv;
   DBuf<long long> inv_off;
+  DBuf<double2> dg64, dgi64;
+  DBuf<float2> dg32, dgi32;
   DBuf<int> d_inst_nlev;
   DBuf<double> cfK, cfG;   // per-block coupling factors (KKT scaled, gradient)
   size_t smem_bytes[2] = {0, 0};
@@ -246,6 +248,8 @@ struct Ctx {
   void build_hierarchy(const fwi_opts &o);
   template <typename T> void ensure_work(const fwi_opts &o);
   template <typename T> void ensure_krylov(const fwi_opts &o);
+  template <typename T> void launch_coarse(const CoarseArgs &ca, size_t smem, const typename cplx<T>::t *b,
+                                           typename cplx<T>::t *x, int cj);
   template <typename T> const typename cplx<T>::t *u_T();
   int gradient(const fwi_opts &o, double *misfit_out, double *grad, int on_device, fwi_stats *stats);
   int newton_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats);
@@ -289,14 +293,29 @@ template <> Work<double> &Ctx::work<double>() { return w64; }
 template <typename T> static const typename cplx<T>::t *st_ptr(Ctx &c);
 template <> const float2 *st_ptr<float>(Ctx &c) { return c.st32.p; }
 template <> const double2 *st_ptr<double>(Ctx &c) { return c.st64.p; }
+template <typename T> static const typename cplx<T>::t *dg_ptr(Ctx &c);
+template <> const float2 *dg_ptr<float>(Ctx &c) { return c.dg32.p; }
+template <> const double2 *dg_ptr<double>(Ctx &c) { return c.dg64.p; }
+template <typename T> static const typename cplx<T>::t *dgi_ptr(Ctx &c);
+template <> const float2 *dgi_ptr<float>(Ctx &c) { return c.dgi32.p; }
+template <> const double2 *dgi_ptr<double>(Ctx &c) { return c.dgi64.p; }
 template <typename T> static const T *gam_ptr(Ctx &c);
 template <> const float *gam_ptr<float>(Ctx &c) { return c.gam32.p; }
 template <> const double *gam_ptr<double>(Ctx &c) { return c.gam64.p; }
+
+template <typename T>
+void Ctx::launch_coarse(const CoarseArgs &ca, size_t smem, const typename cplx<T>::t *b, typename cplx<T>::t *x,
+                        int cj) {
+  if (cj) k_coarse_cycle<T, true><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), dg_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+  else k_coarse_cycle<T, false><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), dg_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+  KCHECK();
+}
 
 template <typename T> LevelView<T> Ctx::viewA() {
   LevelView<T> v;
   v.ops = d_ops.p; v.blks = lv[0].blksA.p; v.tiles = lv[0].tiles.p;
   v.st = st_ptr<T>(*this); v.gam = gam_ptr<T>(*this);
+  v.dg = dg_ptr<T>(*this); v.dgi = dgi_ptr<T>(*this);
   v.n_tiles = lv[0].n_tiles; v.n_blocks = B;
   return v;
 }
@@ -304,6 +323,7 @@ template <typename T> LevelView<T> Ctx::viewM(int l) {
   LevelView<T> v;
   v.ops = d_ops.p; v.blks = lv[l].blksM.p; v.tiles = lv[l].tiles.p;
   v.st = st_ptr<T>(*this); v.gam = gam_ptr<T>(*this);
+  v.dg = dg_ptr<T>(*this); v.dgi = dgi_ptr<T>(*this);
   v.n_tiles = lv[l].n_tiles; v.n_blocks = B;
   return v;
 }
@@ -477,7 +497,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   // operators
   h_ops.clear();
   std::vector<AxisDev> axes;
-  long long st_tot = 0;
+  long long st_tot = 0, dg_tot = 0;
   std::vector<long long> gam_off(n_inst * MAX_LEVELS, -1);
   long long gam_tot = 0;
   for (int i = 0; i < n_inst; ++i)
@@ -508,6 +528,8 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
           od.nx = nx; od.nz = nz;
           od.st = st_tot;
           od.gam = gam_off[i * MAX_LEVELS + l];
+          od.dg = dg_tot;
+          dg_tot += (long long)nx * nz;
           double beta = kind == 0 ? 0.0 : o.shift_beta;
           od.mass_re = (om * hl) * (om * hl);
           od.mass_im = beta * (om * hl) * (om * hl);
@@ -555,6 +577,10 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
       KCHECK();
     }
   }
+  // diagonal of every operator and its inverse
+  dg64.alloc(dg_tot); dgi64.alloc(dg_tot); dg32.alloc(dg_tot); dgi32.alloc(dg_tot);
+  k_diag_setup<<<(int)h_ops.size(), 256, 0, st>>>(d_ops.p, st64.p, gam64.p, dg64.p, dgi64.p, dg32.p, dgi32.p);
+  KCHECK();
   // coarsest inverses
   std::vector<long long> h_inv_off(h_ops.size(), -1), aug_off, inv_off_l;
   std::vector<int> cdims;
@@ -658,9 +684,12 @@ template <typename T> void Ctx::ensure_work(const fwi_opts &o) {
   w.vin.alloc(nkkt); w.zout.alloc(nkkt); w.tmp.alloc(nkkt);
   w.scal.alloc(8);
   w.partial_flat.alloc((size_t)MD_CHUNK * FLAT_BLOCKS);
-  if (smem_bytes[sizeof(T) == 8] > 48 * 1024)
-    CK(cudaFuncSetAttribute(k_coarse_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (smem_bytes[sizeof(T) == 8] > 48 * 1024) {
+    CK(cudaFuncSetAttribute(k_coarse_cycle<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_bytes[sizeof(T) == 8]));
+    CK(cudaFuncSetAttribute(k_coarse_cycle<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_bytes[sizeof(T) == 8]));
+  }
   if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
   w.graph_key.clear();
   sync();
@@ -712,7 +741,14 @@ void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const t
     }
     CK(cudaEventRecord(ev_a[ev_used], st));
   }
-  k_field_op<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, cj, wj, x, b, y);
+  // the shared-memory staged kernel on the fine levels, the direct one on small grids
+  if (level <= 1) {
+    if (cj) k_field_op_tile<T, true><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
+    else k_field_op_tile<T, false><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
+  } else {
+    if (cj) k_field_op<T, true><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
+    else k_field_op<T, false><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
+  }
   KCHECK();
   if (timed) {
     CK(cudaEventRecord(ev_b[ev_used], st));
@@ -748,8 +784,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
   ca.wdepth = o.mg_wdepth;
   size_t smem = smem_bytes[sizeof(T) == 8];
   if (ls == 0) {
-    k_coarse_cycle<T><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
-    KCHECK();
+    launch_coarse<T>(ca, smem, b, x, cj);
     return;
   }
   // recursive cycle over the global levels 0..ls-1; returns the buffer that
@@ -757,8 +792,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
   std::function<T2 *(int, const T2 *, T2 *, T2 *)> cyc;
   cyc = [&](int l, const T2 *bl, T2 *xa, T2 *xb) -> T2 * {
     if (l == ls) {
-      k_coarse_cycle<T><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), bl, xa);
-      KCHECK();
+      launch_coarse<T>(ca, smem, bl, xa, cj);
       return xa;
     }
     T2 *cur = xa, *oth = xb;
@@ -770,7 +804,8 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
     int reps = (l > 0 && l <= o.mg_wdepth) ? o.mg_cycle : 1;
     for (int r = 0; r < reps; ++r) {
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
-      k_resid_restrict<T><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cj, cur, bl, w.lb[l + 1].p);
+      if (cj) k_resid_restrict<T, true><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cur, bl, w.lb[l + 1].p);
+      else k_resid_restrict<T, false><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cur, bl, w.lb[l + 1].p);
       KCHECK();
       T2 *xc = cyc(l + 1, w.lb[l + 1].p, w.lx[l + 1].p, w.lt[l + 1].p);
       k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
@@ -802,15 +837,13 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
   ca.wdepth = o.mg_wdepth;
   size_t smem = smem_bytes[sizeof(T) == 8];
   if (ls == 0) {
-    k_coarse_cycle<T><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
-    KCHECK();
+    launch_coarse<T>(ca, smem, b, x, cj);
     return;
   }
   std::function<T2 *(int, const T2 *, T2 *, T2 *)> cyc;
   cyc = [&](int l, const T2 *bl, T2 *xa, T2 *xb) -> T2 * {
     if (l == ls) {
-      k_coarse_cycle<T><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), bl, xa);
-      KCHECK();
+      launch_coarse<T>(ca, smem, bl, xa, cj);
       return xa;
     }
     T2 *cur = xa, *oth = xb;
@@ -822,7 +855,8 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
     int reps = (l > 0 && l <= o.mg_wdepth) ? o.mg_cycle : 1;
     for (int r = 0; r < reps; ++r) {
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
-      k_resid_restrict<T><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cj, cur, bl, lb[l + 1]);
+      if (cj) k_resid_restrict<T, true><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cur, bl, lb[l + 1]);
+      else k_resid_restrict<T, false><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cur, bl, lb[l + 1]);
       KCHECK();
       T2 *xc = cyc(l + 1, lb[l + 1], lx[l + 1], lt[l + 1]);
       k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
@@ -1871,8 +1905,10 @@ static int mg_cycle_noalloc_impl(fwi::Ctx &c, const fwi_opts &o, const void *b, 
     lt[l] = (T2 *)(base + off); off += bytes;
   }
   size_t smem = c.smem_bytes[sizeof(T) == 8];
-  if (smem > 48 * 1024)
-    CK(cudaFuncSetAttribute(fwi::k_coarse_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) {
+    CK(cudaFuncSetAttribute(fwi::k_coarse_cycle<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(fwi::k_coarse_cycle<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
   c.mg_cycle_into<T>((const T2 *)b, (T2 *)x, 0, o, lx, lb, lt, t0);
   c.sync();
   return FWI_OK;
