@@ -248,6 +248,14 @@ def main():
     f.set_model(0, wl.gamma_true)
     d_true, _, _ = f.forward(opts)
     f.set_observed(0, d_true[0])
+    tuned = None
+    if not args.inner_iters:
+        # untimed set-up: pick the inner iteration count by timing one KKT solve each
+        from paper_2204_06489_gb300.autotune import tune_kkt
+        f.set_model(0, wl.gamma_start)
+        f.forward(opts, want_data=False)
+        opts, table = tune_kkt(f, opts, (4, 6, 8, 12))
+        tuned = [{"inner_iters": n, "s": round(t, 3), "outer": o, "ok": ok} for n, t, o, ok in table]
     g0 = torch.from_numpy(wl.gamma_start).cuda()
     d_dev = torch.from_numpy(d_true[0]).cuda()
     ds_dev = torch.zeros(wl.grid.nx * wl.grid.nz, dtype=torch.float64, device="cuda")
@@ -294,6 +302,8 @@ def main():
     outer = sum(s.outer_iters for s in stats) / len(stats)
     inner = sum(s.inner_iters for s in stats) / len(stats)
     relres = max(s.rel_res for s in stats)
+    t_fwd = sum(s.t_forward_ms for s in stats) / len(stats)
+    t_kkt = sum(s.t_solve_ms for s in stats) / len(stats)
 
     # end to end through the C ABI with host buffers (h2d model + data, d2h update)
     g_host = np.ascontiguousarray(wl.gamma_start)
@@ -321,6 +331,7 @@ def main():
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "kkt_solve_s": per_step, "outer_iters_per_step": outer, "krylov_iters_per_s": outer / per_step,
            "inner_block_iters_per_s": inner / per_step, "rel_res_max": relres,
+           "phase_ms": {"forward": t_fwd, "kkt_solve": t_kkt}, "autotune": tuned,
            "gpu_launches": int(launches),
            "roofline": _roofline(st_ms, st_bytes, st_n, peaks),
            "clocks": ck,

@@ -186,6 +186,7 @@ k_field_op(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__restrict_
 #define FT_CW 128
 #define FT_W (FT_CW + 2)
 #define FT_R (TILE_ROWS + 2)
+static_assert(TILE_THREADS == 2 * FT_CW, "stretch staging assumes two threads per chunk column");
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -200,6 +201,17 @@ template <> __device__ __forceinline__ void cp_async_elem<float2>(float2 *smem, 
 template <> __device__ __forceinline__ void cp_async_elem<double2>(double2 *smem, const double2 *gmem) { cp_async16(smem, gmem); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+__device__ __forceinline__ float2 ld_keep_p(const float2 *p, unsigned long long pol) {
+  float2 v;
+  asm("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_keep_p(const double2 *p, unsigned long long pol) {
+  double2 v;
+  asm("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+
 template <typename T, bool CJ>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__restrict__ x,
@@ -207,17 +219,17 @@ k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__rest
   typedef typename cplx<T>::t T2;
   __shared__ __align__(16) T2 xs[FT_R][FT_W];
   __shared__ __align__(16) T2 bs[TILE_ROWS][FT_CW];
+  __shared__ __align__(16) T2 sX[FT_CW];
+  __shared__ __align__(16) T2 siX[FT_CW + 1];
   const TileDev t = L.tiles[blockIdx.x];
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const int nx = op.nx, nz = op.nz;
   const int j0 = t.row0;
-  const T2 *xb = x ? x + bk.off : nullptr;
-  const T2 *bb = b ? b + bk.off : nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j = j0 + warp;
   const bool row_ok = j < nz;
-  // row constants of this warp's row
+  const unsigned long long pol = keep_policy();
   const T2 *X = L.st + op.st;
   const T2 *iXh = X + nx;
   const T2 *Zr = iXh + nx + 1;
@@ -228,50 +240,64 @@ k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__rest
     iZn = cmaybe_conj(iZh[j], CJ);
     iZs = cmaybe_conj(iZh[j + 1], CJ);
   }
+  const T2 *blk_x = x ? x + bk.off : nullptr;
+  const T2 *brow = b ? b + bk.off + (long long)j * nx : nullptr;
+  T2 *yrow = y + bk.off + (long long)j * nx;
   const T2 *dgr = L.dg + op.dg + (long long)j * nx;
   const T2 *dgir = L.dgi + op.dg + (long long)j * nx;
-  const bool need_x = mode != FM_JACOBI0;
   for (int c0 = 0; c0 < nx; c0 += FT_CW) {
-    // stage x rows j0-1..j0+8, columns c0-1..c0+FT_CW, and b rows j0..j0+7
-    if (need_x) {
-      for (int q = threadIdx.x; q < FT_R * FT_W; q += TILE_THREADS) {
-        int r = q / FT_W, c = q - r * FT_W;
-        int jj = j0 - 1 + r, ii = c0 - 1 + c;
-        if (jj >= 0 && jj < nz && ii >= 0 && ii < nx) cp_async_elem(&xs[r][c], xb + (long long)jj * nx + ii);
-        else xs[r][c] = mk<T2>(0, 0);
+    if (mode != FM_JACOBI0) {
+      // x rows j0-1 .. j0+8, columns c0-1 .. c0+FT_CW: warp per row, lane per column
+      for (int r = warp; r < FT_R; r += TILE_ROWS) {
+        const int jj = j0 - 1 + r;
+        const bool rok = jj >= 0 && jj < nz;
+        const T2 *src = blk_x + (long long)(rok ? jj : 0) * nx + (c0 - 1);
+        for (int c = lane; c < FT_W; c += 32) {
+          const int ii = c0 - 1 + c;
+          if (rok && ii >= 0 && ii < nx) cp_async_elem(&xs[r][c], src + c);
+          else xs[r][c] = mk<T2>(0, 0);
+        }
+      }
+      // per-column stretch factors of the chunk (shared by the 8 rows)
+      // (threads 0..127: X; 128..255: 1/X at half nodes 0..127; thread 0 also
+      // the last half node 128; iXh has nx + 1 entries)
+      if (threadIdx.x < FT_CW) {
+        const int ii = c0 + threadIdx.x;
+        if (ii < nx) cp_async_elem(&sX[threadIdx.x], X + ii);
+        if (threadIdx.x == 0 && c0 + FT_CW <= nx) cp_async_elem(&siX[FT_CW], iXh + c0 + FT_CW);
+      } else {
+        const int c = threadIdx.x - FT_CW;
+        if (c0 + c <= nx) cp_async_elem(&siX[c], iXh + c0 + c);
       }
     }
-    if (mode != FM_APPLY) {
-      for (int q = threadIdx.x; q < TILE_ROWS * FT_CW; q += TILE_THREADS) {
-        int r = q / FT_CW, c = q - r * FT_CW;
-        int jj = j0 + r, ii = c0 + c;
-        if (jj < nz && ii < nx) cp_async_elem(&bs[r][c], bb + (long long)jj * nx + ii);
-      }
+    if (mode != FM_APPLY && row_ok) {
+      for (int c = lane; c < FT_CW; c += 32)
+        if (c0 + c < nx) cp_async_elem(&bs[warp][c], brow + c0 + c);
     }
     cp_async_wait_all();
     __syncthreads();
     if (row_ok) {
 #pragma unroll
       for (int q = 0; q < FT_CW / 32; ++q) {
-        int c = lane + 32 * q;
-        int i = c0 + c;
+        const int c = lane + 32 * q;
+        const int i = c0 + c;
         if (i < nx) {
           T2 out;
           if (mode == FM_JACOBI0) {
-            out = cscale(cmul(bs[warp][c], cmaybe_conj(ld_keep(dgir + i), CJ)), w);
+            out = cscale(cmul(bs[warp][c], cmaybe_conj(ld_keep_p(dgir + i, pol), CJ)), w);
           } else {
-            T2 Xi = cmaybe_conj(ld_keep(X + i), CJ);
-            T2 iw = cmaybe_conj(ld_keep(iXh + i), CJ);
-            T2 ie = cmaybe_conj(ld_keep(iXh + i + 1), CJ);
+            const T2 Xi = cmaybe_conj(sX[c], CJ);
+            const T2 iw = cmaybe_conj(siX[c], CJ);
+            const T2 ie = cmaybe_conj(siX[c + 1], CJ);
             const T2 *xc = &xs[warp + 1][c + 1];
-            T2 hx = cadd(cmul(ie, xc[1]), cmul(iw, xc[-1]));
-            T2 hz = cadd(cmul(iZs, xc[FT_W]), cmul(iZn, xc[-FT_W]));
-            T2 ax = csub(csub(cmul(cmaybe_conj(ld_keep(dgr + i), CJ), xc[0]), cmul(Zj, hx)), cmul(Xi, hz));
+            const T2 hx = cadd(cmul(ie, xc[1]), cmul(iw, xc[-1]));
+            const T2 hz = cadd(cmul(iZs, xc[FT_W]), cmul(iZn, xc[-FT_W]));
+            const T2 ax = csub(csub(cmul(cmaybe_conj(ld_keep_p(dgr + i, pol), CJ), xc[0]), cmul(Zj, hx)), cmul(Xi, hz));
             if (mode == FM_APPLY) out = ax;
             else if (mode == FM_RESID) out = csub(bs[warp][c], ax);
-            else out = cadd(xc[0], cscale(cmul(csub(bs[warp][c], ax), cmaybe_conj(ld_keep(dgir + i), CJ)), w));
+            else out = cadd(xc[0], cscale(cmul(csub(bs[warp][c], ax), cmaybe_conj(ld_keep_p(dgir + i, pol), CJ)), w));
           }
-          y[bk.off + (long long)j * nx + i] = out;
+          yrow[i] = out;
         }
       }
     }
