@@ -147,6 +147,92 @@ def run_inner_case(args):
                       "roofline": _roofline(ms, nbytes, cnt, _peaks())}))
 
 
+def _setup_ctx(P, wls, opts, stream):
+    """Context over one or more workloads with synthetic data from the
+    library's forward modelling at the true models (untimed)."""
+    f = P.FWI([w.grid for w in wls], stream=stream.cuda_stream)
+    for i, w in enumerate(wls):
+        f.set_survey(i, w.survey)
+        f.set_model(i, w.gamma_true)
+    d, _, _ = f.forward(opts, want_data=True)
+    for i, w in enumerate(wls):
+        f.set_observed(i, d[i])
+        f.set_model(i, w.gamma_start)
+    return f
+
+
+def run_extra_case(args):
+    """Other workloads of the scope table, one JSON line each (not the headline):
+      batch3a   1024 blocks (256 sources x 2/4/6/8 Hz, 401x141) in one batch
+      batch3b   8 instances of uneven grids x 32 sources x 2/4/6/8 Hz
+      large     1601x561 h=5 m, 128 sources, one frequency (4 Hz)
+      autograd  801x281 h=10 m, 64 sources, 6 Hz: misfit + gradient through
+                torch.autograd, with central-difference checks
+    batch3a/3b/large run one Newton step with a cap of ``--max-outer`` outer
+    iterations and report throughput (outer and inner iterations per second)."""
+    import numpy as np
+    import torch
+    import fwi_inputs as FI
+    import paper_2204_06489_gb300 as P
+    P.load(build_if_missing=True)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    opts = P.default_opts(eps=args.eps or EPS, inner_iters=args.inner_iters or 8)
+    if args.case == "batch3a":
+        wls = [FI.batching_workload()]
+    elif args.case == "batch3b":
+        wls = FI.uneven_workloads()
+    elif args.case == "large":
+        wls = [FI.large_workload(freqs=(4.0,))]
+    else:
+        wls = [FI.autograd_workload()]
+    t0 = time.perf_counter()
+    f = _setup_ctx(P, wls, opts, stream)
+    t_setup = time.perf_counter() - t0
+    lay = f.layout()
+    out = {"case": args.case, "workloads": [w.name for w in wls], "blocks": lay["n_blocks"],
+           "field_complex": lay["field_elems"], "setup_s": t_setup}
+    if args.case == "autograd":
+        from scipy.ndimage import gaussian_filter
+        from paper_2204_06489_gb300.autograd import misfit
+        w = wls[0]
+        g0 = torch.tensor(w.gamma_start, dtype=torch.float64, device="cuda", requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        phi = misfit(g0, f, mode="recompute", opts=opts)
+        phi.backward()
+        torch.cuda.synchronize()
+        out["forward_backward_s"] = time.perf_counter() - t0
+        grad = g0.grad.detach().cpu().numpy()
+        errs = []
+        for seed in range(args.fd_dirs):
+            dirn = gaussian_filter(np.random.default_rng(seed).standard_normal(grad.shape), 10.0)
+            dirn *= 0.003 * w.gamma_start.mean() / np.abs(dirn).max()
+            with torch.no_grad():
+                fp = misfit(torch.tensor(w.gamma_start + dirn, device="cuda"), f, opts=opts).item()
+                fm = misfit(torch.tensor(w.gamma_start - dirn, device="cuda"), f, opts=opts).item()
+            an = float(np.sum(grad * dirn))
+            errs.append(abs((fp - fm) / 2 - an) / abs(an))
+        out.update(misfit=phi.item(), fd_rel_err_max=max(errs), fd_directions=len(errs))
+    else:
+        o = P.Opts.from_buffer_copy(opts)
+        o.max_outer = args.max_outer
+        f.stencil_timer(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ds, st = f.newton_step(o, allow_noconv=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ms, nbytes, cnt = f.stencil_timer(0)
+        out.update(newton_step_s=dt, outer_iters=st["outer_iters"], rel_res=st["rel_res"],
+                   forward_ms=st["t_forward_ms"], kkt_ms=st["t_solve_ms"],
+                   krylov_iters_per_s=st["outer_iters"] / (st["t_solve_ms"] / 1e3),
+                   inner_block_iters_per_s=st["inner_iters"] / (dt),
+                   roofline=_roofline(ms, nbytes, cnt, _peaks()))
+    print(json.dumps(out))
+    f.close()
+
+
 def _workload():
     import fwi_inputs as FI
     return FI.marmousi_shaped_workload()
@@ -214,7 +300,9 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--case", default="newton", choices=["newton", "inner"])
+    ap.add_argument("--case", default="newton", choices=["newton", "inner", "batch3a", "batch3b", "large", "autograd"])
+    ap.add_argument("--max-outer", type=int, default=60)
+    ap.add_argument("--fd-dirs", type=int, default=4)
     ap.add_argument("--inner-iters", type=int, default=None)
     ap.add_argument("--restart", type=int, default=None)
     ap.add_argument("--eps", type=float, default=None)
@@ -223,6 +311,8 @@ def main():
         return run_reference(args)
     if args.case == "inner":
         return run_inner_case(args)
+    if args.case != "newton":
+        return run_extra_case(args)
 
     import numpy as np
     import torch

@@ -185,3 +185,42 @@ def micro_workload(seed: int = 0, nx: int = 15, nz: int = 11, npml: int = 4, n_s
     sv.rec_offsets = (np.arange(n_src + 1) * n_rec).astype(np.int32)
     sv.rec_w = np.ones(sv.rec_ix.shape, dtype=np.float64)
     return Workload(f"micro_{nx}x{nz}", g, sv, gamma_of(v), gamma_of(smooth(v, 3.0)))
+
+
+def batching_workload(seed: int = 0) -> Workload:
+    """256 sources x 2/4/6/8 Hz on the 401x141 Marmousi-shaped model
+    (1024 Helmholtz blocks in one batch)."""
+    return marmousi_shaped_workload(seed=seed, n_src=256, freqs=(2.0, 4.0, 6.0, 8.0))
+
+
+UNEVEN_GRIDS = [(201, 71), (301, 106), (401, 141), (601, 211), (801, 281), (201, 71), (301, 106), (401, 141)]
+
+
+def uneven_workloads(n_src: int = 32, freqs=(2.0, 4.0, 6.0, 8.0)) -> List[Workload]:
+    """Eight independent instances of uneven grid sizes (h = 20 m, 20-node
+    layer), each a seeded layered-faulted model with ``n_src`` sources."""
+    out = []
+    for k, (nx, nz) in enumerate(UNEVEN_GRIDS):
+        g = Grid(nx=nx, nz=nz, npml=20, h=20.0, pml_c=4700.0)
+        v = layered_faulted_model(nx, nz, g.h, seed=k)
+        out.append(Workload(f"uneven_{k}_{nx}x{nz}", g, surface_survey(nx, n_src, list(freqs)),
+                            gamma_of(v), gamma_of(smooth(v, 25.0))))
+    return out
+
+
+def autograd_workload(seed: int = 0) -> Workload:
+    """801x281 at h = 10 m, 30-node layer, layered-faulted model, 64 sources,
+    801 receivers, 6 Hz."""
+    g = Grid(nx=801, nz=281, npml=30, h=10.0, pml_c=4700.0)
+    v = layered_faulted_model(g.nx, g.nz, g.h, seed=seed)
+    return Workload("autograd_801x281_h10_pml30_64src_6Hz", g, surface_survey(g.nx, 64, [6.0]),
+                    gamma_of(v), gamma_of(smooth(v, 25.0)))
+
+
+def large_workload(seed: int = 0, freqs=(4.0, 6.0, 8.0, 10.0)) -> Workload:
+    """1601x561 at h = 5 m, 40-node layer, 128 sources, 1601 receivers,
+    4/6/8/10 Hz (processed one frequency at a time)."""
+    g = Grid(nx=1601, nz=561, npml=40, h=5.0, pml_c=4700.0)
+    v = layered_faulted_model(g.nx, g.nz, g.h, seed=seed)
+    return Workload("large_1601x561_h5_pml40_128src", g, surface_survey(g.nx, 128, list(freqs)),
+                    gamma_of(v), gamma_of(smooth(v, 25.0)))
