@@ -186,11 +186,15 @@ def run_extra_case(args):
         wls = [FI.large_workload(freqs=(4.0,))]
     else:
         wls = [FI.autograd_workload()]
+    from paper_2204_06489_gb300.autotune import auto_wdepth
+    opts.mg_wdepth = auto_wdepth([w.grid for w in wls], [w.survey.freqs_hz for w in wls],
+                                 [w.gamma_start for w in wls])
     t0 = time.perf_counter()
     f = _setup_ctx(P, wls, opts, stream)
     t_setup = time.perf_counter() - t0
     lay = f.layout()
     out = {"case": args.case, "workloads": [w.name for w in wls], "blocks": lay["n_blocks"],
+           "mg_wdepth": opts.mg_wdepth, "inner_iters": opts.inner_iters,
            "field_complex": lay["field_elems"], "setup_s": t_setup}
     if args.case == "autograd":
         from scipy.ndimage import gaussian_filter

@@ -86,8 +86,9 @@ typedef struct {
   double sigma_cap;       /* clip sigma/omega of the shifted operator's layer  [1.0]  */
   int mg_levels;          /* 0 = automatic                                     [0]    */
   double fwd_tol;         /* forward/adjoint wavefield residual target (FP64)  [1e-10]*/
-  int fwd_iters;          /* BiCGStab iterations per forward refinement sweep  [60]   */
-  int max_fwd_refine;     /* cap on forward refinement sweeps                  [10]   */
+  int fwd_iters;          /* BiCGStab iterations of the first forward refinement sweep;
+                             doubled (up to 8x) after a sweep that gains < 20x [60]   */
+  int max_fwd_refine;     /* cap on forward refinement sweeps                  [20]   */
   int use_graph;          /* replay the preconditioner from a CUDA graph       [1]    */
 } fwi_opts;
 
@@ -99,6 +100,7 @@ typedef struct {
   double rel_res;         /* final ||b - M xi|| / ||b|| recomputed in FP64 (max over instances) */
   double misfit;          /* data misfit 1/2 sum |W r|^2 at the step's model (sum over instances) */
   double t_setup_ms, t_forward_ms, t_solve_ms;
+  double fwd_rel_res;     /* final max_b ||f_b - A u_b|| / ||f_b|| of the forward / adjoint solve */
 } fwi_stats;
 
 /* Layout of the context's buffers (element counts). */

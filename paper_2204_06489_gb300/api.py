@@ -53,7 +53,8 @@ class Opts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("refinements", C.c_int), ("fwd_sweeps", C.c_int),
                 ("inner_iters", C.c_longlong), ("rel_res", C.c_double), ("misfit", C.c_double),
-                ("t_setup_ms", C.c_double), ("t_forward_ms", C.c_double), ("t_solve_ms", C.c_double)]
+                ("t_setup_ms", C.c_double), ("t_forward_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("fwd_rel_res", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -74,3 +74,21 @@ def tune_kkt(fwi: FWI, base: Optional[Opts] = None, inner_iters: Iterable[int] =
         if ok and dt < best_t:
             best, best_t = o, dt
     return (best if best is not None else base), table
+
+
+def auto_wdepth(grids, freqs_per_grid, gammas, kh_max: float = 2.0, levels_max: int = 12) -> int:
+    """Deepest multigrid level whose grid still resolves the wave field
+    (omega h_l / c <= kh_max with c = 1/sqrt(mean gamma)), over every grid and
+    frequency of a batch: the levels down to there repeat their coarse-grid
+    correction (W), the coarser ones do not."""
+    depth = 1
+    for g, fr, gam in zip(grids, freqs_per_grid, gammas):
+        c = 1.0 / math.sqrt(float(sum(map(float, [gam.mean()]))))
+        for f in fr:
+            om = 2.0 * math.pi * f
+            l, h = 0, g.h
+            while l + 1 < levels_max and om * (2.0 * h) / c <= kh_max:
+                l += 1
+                h *= 2.0
+            depth = max(depth, l)
+    return depth
