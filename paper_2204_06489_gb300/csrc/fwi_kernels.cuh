@@ -21,6 +21,11 @@ namespace fwi {
 // ---------------------------------------------------------------------------
 #define DOT_RUN 16
 
+// Fused multiply-add in the precision of the operands (the generic fma() of
+// the math headers promotes float operands to double).
+__device__ __forceinline__ float tfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Loads of the small per-operator arrays (stretch factors, diagonal) that every
 // source of a frequency re-reads: keep them in L2 while the fields stream past.
 __device__ __forceinline__ unsigned long long keep_policy() {
@@ -212,15 +217,26 @@ __device__ __forceinline__ double2 ld_keep_p(const double2 *p, unsigned long lon
   return v;
 }
 
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Two shared-memory stages: the copies of chunk k+1 are in flight while chunk
+// k is computed.
+template <typename T> struct FtStage {
+  typedef typename cplx<T>::t T2;
+  T2 xs[FT_R][FT_W];
+  T2 bs[TILE_ROWS][FT_CW];
+  T2 sX[FT_CW];
+  T2 siX[FT_CW + 1];
+};
+
 template <typename T, bool CJ>
-__global__ void __launch_bounds__(TILE_THREADS)
+__global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 5 : 2)
 k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__restrict__ x,
                 const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
   typedef typename cplx<T>::t T2;
-  __shared__ __align__(16) T2 xs[FT_R][FT_W];
-  __shared__ __align__(16) T2 bs[TILE_ROWS][FT_CW];
-  __shared__ __align__(16) T2 sX[FT_CW];
-  __shared__ __align__(16) T2 siX[FT_CW + 1];
+  extern __shared__ __align__(16) unsigned char ft_raw[];
+  FtStage<T> *stg = reinterpret_cast<FtStage<T> *>(ft_raw);
   const TileDev t = L.tiles[blockIdx.x];
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
@@ -245,7 +261,8 @@ k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__rest
   T2 *yrow = y + bk.off + (long long)j * nx;
   const T2 *dgr = L.dg + op.dg + (long long)j * nx;
   const T2 *dgir = L.dgi + op.dg + (long long)j * nx;
-  for (int c0 = 0; c0 < nx; c0 += FT_CW) {
+
+  auto stage = [&](FtStage<T> &S, int c0) {
     if (mode != FM_JACOBI0) {
       // x rows j0-1 .. j0+8, columns c0-1 .. c0+FT_CW: warp per row, lane per column
       for (int r = warp; r < FT_R; r += TILE_ROWS) {
@@ -254,28 +271,40 @@ k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__rest
         const T2 *src = blk_x + (long long)(rok ? jj : 0) * nx + (c0 - 1);
         for (int c = lane; c < FT_W; c += 32) {
           const int ii = c0 - 1 + c;
-          if (rok && ii >= 0 && ii < nx) cp_async_elem(&xs[r][c], src + c);
-          else xs[r][c] = mk<T2>(0, 0);
+          if (rok && ii >= 0 && ii < nx) cp_async_elem(&S.xs[r][c], src + c);
+          else S.xs[r][c] = mk<T2>(0, 0);
         }
       }
-      // per-column stretch factors of the chunk (shared by the 8 rows)
-      // (threads 0..127: X; 128..255: 1/X at half nodes 0..127; thread 0 also
-      // the last half node 128; iXh has nx + 1 entries)
+      // per-column stretch factors of the chunk (threads 0..127: X; 128..255:
+      // 1/X at half nodes 0..127; thread 0 also half node 128; iXh has nx + 1 entries)
       if (threadIdx.x < FT_CW) {
         const int ii = c0 + threadIdx.x;
-        if (ii < nx) cp_async_elem(&sX[threadIdx.x], X + ii);
-        if (threadIdx.x == 0 && c0 + FT_CW <= nx) cp_async_elem(&siX[FT_CW], iXh + c0 + FT_CW);
+        if (ii < nx) cp_async_elem(&S.sX[threadIdx.x], X + ii);
+        if (threadIdx.x == 0 && c0 + FT_CW <= nx) cp_async_elem(&S.siX[FT_CW], iXh + c0 + FT_CW);
       } else {
         const int c = threadIdx.x - FT_CW;
-        if (c0 + c <= nx) cp_async_elem(&siX[c], iXh + c0 + c);
+        if (c0 + c <= nx) cp_async_elem(&S.siX[c], iXh + c0 + c);
       }
     }
     if (mode != FM_APPLY && row_ok) {
       for (int c = lane; c < FT_CW; c += 32)
-        if (c0 + c < nx) cp_async_elem(&bs[warp][c], brow + c0 + c);
+        if (c0 + c < nx) cp_async_elem(&S.bs[warp][c], brow + c0 + c);
     }
-    cp_async_wait_all();
+    cp_async_commit();
+  };
+
+  const int nchunk = (nx + FT_CW - 1) / FT_CW;
+  stage(stg[0], 0);
+  for (int k = 0; k < nchunk; ++k) {
+    const int c0 = k * FT_CW;
+    if (k + 1 < nchunk) {
+      stage(stg[(k + 1) & 1], c0 + FT_CW);
+      cp_async_wait_prev();          // chunk k has landed; chunk k+1 may still be in flight
+    } else {
+      cp_async_wait_all();
+    }
     __syncthreads();
+    FtStage<T> &S = stg[k & 1];
     if (row_ok) {
 #pragma unroll
       for (int q = 0; q < FT_CW / 32; ++q) {
@@ -284,24 +313,24 @@ k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__rest
         if (i < nx) {
           T2 out;
           if (mode == FM_JACOBI0) {
-            out = cscale(cmul(bs[warp][c], cmaybe_conj(ld_keep_p(dgir + i, pol), CJ)), w);
+            out = cscale(cmul(S.bs[warp][c], cmaybe_conj(ld_keep_p(dgir + i, pol), CJ)), w);
           } else {
-            const T2 Xi = cmaybe_conj(sX[c], CJ);
-            const T2 iw = cmaybe_conj(siX[c], CJ);
-            const T2 ie = cmaybe_conj(siX[c + 1], CJ);
-            const T2 *xc = &xs[warp + 1][c + 1];
+            const T2 Xi = cmaybe_conj(S.sX[c], CJ);
+            const T2 iw = cmaybe_conj(S.siX[c], CJ);
+            const T2 ie = cmaybe_conj(S.siX[c + 1], CJ);
+            const T2 *xc = &S.xs[warp + 1][c + 1];
             const T2 hx = cadd(cmul(ie, xc[1]), cmul(iw, xc[-1]));
             const T2 hz = cadd(cmul(iZs, xc[FT_W]), cmul(iZn, xc[-FT_W]));
             const T2 ax = csub(csub(cmul(cmaybe_conj(ld_keep_p(dgr + i, pol), CJ), xc[0]), cmul(Zj, hx)), cmul(Xi, hz));
             if (mode == FM_APPLY) out = ax;
-            else if (mode == FM_RESID) out = csub(bs[warp][c], ax);
-            else out = cadd(xc[0], cscale(cmul(csub(bs[warp][c], ax), cmaybe_conj(ld_keep_p(dgir + i, pol), CJ)), w));
+            else if (mode == FM_RESID) out = csub(S.bs[warp][c], ax);
+            else out = cadd(xc[0], cscale(cmul(csub(S.bs[warp][c], ax), cmaybe_conj(ld_keep_p(dgir + i, pol), CJ)), w));
           }
           yrow[i] = out;
         }
       }
     }
-    __syncthreads();
+    __syncthreads();                 // stage k & 1 is refilled two chunks later
   }
 }
 
@@ -813,8 +842,8 @@ k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typena
         if (q < nd) {
           T2 a = as[q][base + i], b = bs[q][base + i];
           // conj(a) b = (ax bx + ay by) + i (ax by - ay bx)
-          rre[q] = fma(a.x, b.x, fma(a.y, b.y, rre[q]));
-          rim[q] = fma(a.x, b.y, fma(-a.y, b.x, rim[q]));
+          rre[q] = tfma(a.x, b.x, tfma(a.y, b.y, rre[q]));
+          rim[q] = tfma(a.x, b.y, tfma(-a.y, b.x, rim[q]));
         }
       }
       if (sizeof(T) == 4 && ++cnt == DOT_RUN) {
@@ -1159,7 +1188,7 @@ k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, doub
     T wi = w[i];
 #pragma unroll
     for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) run[v] = fma(vp[v][i], wi, run[v]);
+      if (v < nv) run[v] = tfma(vp[v][i], wi, run[v]);
     if (sizeof(T) == 4 && ++cnt == DOT_RUN) {
 #pragma unroll
       for (int v = 0; v < MD_CHUNK; ++v) { tot[v] += run[v]; run[v] = 0; }
@@ -1204,7 +1233,7 @@ k_multi_axpy(long long n, int nv, const T *const *V, const double *coef, double 
     T acc = w[i];
 #pragma unroll
     for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) acc = fma(c[v], vp[v][i], acc);
+      if (v < nv) acc = tfma(c[v], vp[v][i], acc);
     w[i] = acc;
   }
 }
@@ -1218,7 +1247,7 @@ k_dot2(long long n, const T *__restrict__ x, const T *__restrict__ y, double *pa
   T run = 0;
   int cnt = 0;
   for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
-    run = fma(x[i], y[i], run);
+    run = tfma(x[i], y[i], run);
     if (sizeof(T) == 4 && ++cnt == DOT_RUN) { tot += run; run = 0; cnt = 0; }
   }
   double acc = tot + (double)run;

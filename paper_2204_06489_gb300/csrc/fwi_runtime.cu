@@ -652,6 +652,15 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
     T.t0.upload(T.ht0, st);
     T.t1.upload(T.ht1, st);
   }
+  // dynamic shared memory of the double-buffered stencil kernels (both precisions)
+  CK(cudaFuncSetAttribute(k_field_op_tile<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(2 * sizeof(FtStage<float>))));
+  CK(cudaFuncSetAttribute(k_field_op_tile<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(2 * sizeof(FtStage<float>))));
+  CK(cudaFuncSetAttribute(k_field_op_tile<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(2 * sizeof(FtStage<double>))));
+  CK(cudaFuncSetAttribute(k_field_op_tile<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(2 * sizeof(FtStage<double>))));
   partial.alloc((size_t)std::max(1, lv[0].n_tiles) * 3);
   blkfac.alloc(B); blkn0.alloc(B); blkn.alloc(B);
   // coupling factors: KKT (h^2 gamma_ref omega^2) and gradient (h^2 omega^2)
@@ -743,8 +752,9 @@ void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const t
   }
   // the shared-memory staged kernel on the fine levels, the direct one on small grids
   if (level <= 1) {
-    if (cj) k_field_op_tile<T, true><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
-    else k_field_op_tile<T, false><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
+    const size_t sm = 2 * sizeof(FtStage<T>);
+    if (cj) k_field_op_tile<T, true><<<L.n_tiles, TILE_THREADS, sm, st>>>(L, mode, wj, x, b, y);
+    else k_field_op_tile<T, false><<<L.n_tiles, TILE_THREADS, sm, st>>>(L, mode, wj, x, b, y);
   } else {
     if (cj) k_field_op<T, true><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
     else k_field_op<T, false><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);

@@ -301,3 +301,33 @@ def test_kkt_solve_odd_control_size(lib):
     ref = K.delta_s(K.solve_direct())
     assert st["rel_res"] <= 1e-7 and _rel(ds, ref) < 1e-5
     f.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(torch.complex128, 1e-12), (torch.complex64, 2e-6)])
+def test_wide_grid_operator_and_cycle(lib, prec, tol):
+    """A grid wider than two 128-column chunks of the staged stencil kernel
+    (313 padded columns: chunks of 128, 128 and a ragged 57) and taller than
+    several row tiles; operator, adjoint and one multigrid cycle against the
+    oracle."""
+    import paper_2204_06489_gb300 as P
+    wl = FI.micro_workload(seed=11, nx=301, nz=29, npml=6, n_src=2, n_rec=7, freq=6.0)
+    f = P.from_workload(wl)
+    p = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    n = f.layout()["field_elems"]
+    xt, x = _rand_field(n, 12, prec)
+    xs = x if prec == torch.complex128 else xt.cpu().numpy().astype(complex)
+    A = p.operator(wl.gamma_start.ravel(), 0)
+    N = A.shape[0]
+    for adj in (False, True):
+        y = f.apply_helmholtz(xt, adjoint=adj).cpu().numpy().astype(complex)
+        for b in range(p.n_blocks):
+            xb = xs[b * N:(b + 1) * N]
+            ref = np.conj(A @ np.conj(xb)) if adj else A @ xb
+            assert _rel(y[b * N:(b + 1) * N], ref) < tol
+    opts = P.default_opts()
+    xc = f.mg_cycle(xt, opts).cpu().numpy().astype(complex)
+    h = _oracle_hier(P, wl, p, 0, opts)
+    for b in range(p.n_blocks):
+        ref = h.vcycle(xs[b * N:(b + 1) * N])
+        assert _rel(xc[b * N:(b + 1) * N], ref) < (1e-10 if prec == torch.complex128 else 2e-4)
+    f.close()
