@@ -829,6 +829,8 @@ k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typena
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);
+  // a lane sums at most ceil(nx / 32) products per dot: in the data precision,
+  // flushed into FP64 every DOT_RUN terms for complex64
   double tre[3] = {0, 0, 0}, tim[3] = {0, 0, 0};
   T rre[3] = {0, 0, 0}, rim[3] = {0, 0, 0};
   const T2 *as[3] = {a0, a1, a2};
@@ -848,20 +850,34 @@ k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typena
       }
       if (sizeof(T) == 4 && ++cnt == DOT_RUN) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) { tre[q] += rre[q]; tim[q] += rim[q]; rre[q] = 0; rim[q] = 0; }
+        for (int q = 0; q < 3; ++q)
+          if (q < nd) { tre[q] += rre[q]; tim[q] += rim[q]; rre[q] = 0; rim[q] = 0; }
         cnt = 0;
       }
     }
   }
   __shared__ double2 red[3][TILE_THREADS / 32];
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    double x = tre[q] + (double)rre[q], y = tim[q] + (double)rim[q];
-    for (int o = 16; o > 0; o >>= 1) {
-      x += __shfl_down_sync(0xffffffffu, x, o);
-      y += __shfl_down_sync(0xffffffffu, y, o);
+    if (q < nd) {
+      // lane run remainders are reduced across the warp in the data precision,
+      // the flushed FP64 parts only when a lane had more than DOT_RUN terms
+      T x = rre[q], y = rim[q];
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+      }
+      double dx = 0.0, dy = 0.0;
+      if (__any_sync(0xffffffffu, tre[q] != 0.0 || tim[q] != 0.0)) {
+        dx = tre[q]; dy = tim[q];
+        for (int o = 16; o > 0; o >>= 1) {
+          dx += __shfl_down_sync(0xffffffffu, dx, o);
+          dy += __shfl_down_sync(0xffffffffu, dy, o);
+        }
+      }
+      if (lane == 0) red[q][threadIdx.x >> 5] = make_double2(dx + (double)x, dy + (double)y);
     }
-    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = make_double2(x, y);
   }
   __syncthreads();
   if (threadIdx.x < nd) {
