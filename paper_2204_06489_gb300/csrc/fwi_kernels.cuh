@@ -598,8 +598,10 @@ struct SmemCycle {
   }
 };
 
+#define COARSE_THREADS 1024
 template <typename T, bool CJ>
-__global__ void k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restrict__ st,
+__global__ void __launch_bounds__(COARSE_THREADS, 1)
+k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restrict__ st,
                                const typename cplx<T>::t *__restrict__ dg, const typename cplx<T>::t *__restrict__ dgi,
                                const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ x) {
   typedef typename cplx<T>::t T2;

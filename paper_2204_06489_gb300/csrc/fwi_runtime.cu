@@ -306,8 +306,8 @@ template <> const double *gam_ptr<double>(Ctx &c) { return c.gam64.p; }
 template <typename T>
 void Ctx::launch_coarse(const CoarseArgs &ca, size_t smem, const typename cplx<T>::t *b, typename cplx<T>::t *x,
                         int cj) {
-  if (cj) k_coarse_cycle<T, true><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), dg_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
-  else k_coarse_cycle<T, false><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), dg_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+  if (cj) k_coarse_cycle<T, true><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), dg_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+  else k_coarse_cycle<T, false><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), dg_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
   KCHECK();
 }
 
