@@ -85,7 +85,7 @@ typedef struct {
   double shift_beta;      /* shifted operator omega^2 -> (1 + i beta) omega^2  [0.5]  */
   double sigma_cap;       /* clip sigma/omega of the shifted operator's layer  [1.0]  */
   int mg_levels;          /* 0 = automatic                                     [0]    */
-  double fwd_tol;         /* forward/adjoint wavefield residual target (FP64)  [1e-10]*/
+  double fwd_tol;         /* forward/adjoint wavefield residual target (FP64)  [1e-9] */
   int fwd_iters;          /* BiCGStab iterations of the first forward refinement sweep;
                              doubled (up to 8x) after a sweep that gains < 20x [60]   */
   int max_fwd_refine;     /* cap on forward refinement sweeps                  [20]   */

@@ -1538,7 +1538,7 @@ void fwi_default_opts(fwi_opts *o) {
   o->shift_beta = 0.5;
   o->sigma_cap = 1.0;
   o->mg_levels = 0;
-  o->fwd_tol = 1e-10;
+  o->fwd_tol = 1e-9;
   o->fwd_iters = 60;
   o->max_fwd_refine = 20;
   o->use_graph = 1;
