@@ -1189,36 +1189,50 @@ __global__ void k_update_model(const InstDev *inst, double *const *s_core, const
 #define FLAT_THREADS 256
 #define MD_CHUNK 8
 
-// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv (run accumulation as
-// above, FP64 across threads; fixed grid, deterministic).
+// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv.  complex64 data: each
+// thread accumulates FP32 runs of MD_RUN products per vector (two independent
+// chains of interleaved elements) and adds each run into an FP64 total; FP64
+// across threads.  complex128: FP64 throughout.  Fixed grid, deterministic.
+#define MD_RUN 64
 template <typename T>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, double *partial) {
   double tot[MD_CHUNK];
-  T run[MD_CHUNK];
+  T ra[MD_CHUNK], rb[MD_CHUNK];
 #pragma unroll
-  for (int v = 0; v < MD_CHUNK; ++v) { tot[v] = 0.0; run[v] = 0; }
+  for (int v = 0; v < MD_CHUNK; ++v) { tot[v] = 0.0; ra[v] = 0; rb[v] = 0; }
   const T *vp[MD_CHUNK];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) vp[v] = v < nv ? V[v] : nullptr;
+  const long long stride = (long long)gridDim.x * FLAT_THREADS;
   int cnt = 0;
-  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
-    T wi = w[i];
+  long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {
+    const T wa = w[i], wb = w[i + stride];
 #pragma unroll
     for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) run[v] = tfma(vp[v][i], wi, run[v]);
-    if (sizeof(T) == 4 && ++cnt == DOT_RUN) {
+      if (v < nv) { ra[v] = tfma(vp[v][i], wa, ra[v]); rb[v] = tfma(vp[v][i + stride], wb, rb[v]); }
+    if (sizeof(T) == 4 && (cnt += 2) >= MD_RUN) {
 #pragma unroll
-      for (int v = 0; v < MD_CHUNK; ++v) { tot[v] += run[v]; run[v] = 0; }
+      for (int v = 0; v < MD_CHUNK; ++v)
+        if (v < nv) { tot[v] += (double)(ra[v] + rb[v]); ra[v] = 0; rb[v] = 0; }
       cnt = 0;
     }
+  }
+  if (i < n) {
+    const T wa = w[i];
+#pragma unroll
+    for (int v = 0; v < MD_CHUNK; ++v)
+      if (v < nv) ra[v] = tfma(vp[v][i], wa, ra[v]);
   }
   __shared__ double red[MD_CHUNK][FLAT_THREADS / 32];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) {
-    double x = tot[v] + (double)run[v];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = x;
+    if (v < nv) {
+      double x = tot[v] + (double)(ra[v] + rb[v]);
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = x;
+    }
   }
   __syncthreads();
   if (threadIdx.x < nv) {
