@@ -94,10 +94,12 @@ def _peaks():
         return {}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one level-0 k_field_op launch
-# (ncu, profiles/k_field_op_marmousi_120blocks.md), per algorithmic byte;
-# None until a capture of the current kernel exists.
-TRAFFIC_PER_ALG_BYTE = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one level-0 k_field_op_tile
+# Jacobi launch per algorithmic byte: 203.6 MB / 229.9 MB from the ncu capture
+# summarised in profiles/k_field_op_tile_marmousi_120blocks.md (set to None
+# when the kernel changes until it is captured again).  The reported traffic
+# scales it by each timed launch's algorithmic bytes.
+TRAFFIC_PER_ALG_BYTE = 203.6 / 229.9
 
 
 def _roofline(ms, nbytes, n, peaks):
@@ -109,7 +111,7 @@ def _roofline(ms, nbytes, n, peaks):
         return None
     ach = nbytes / (ms / 1e3) / 1e9
     per_launch = nbytes / n
-    return {"kernel": "k_field_op<float> (level-0 5-point PML stencil / Jacobi sweep, all 120 blocks)",
+    return {"kernel": "k_field_op_tile<float> (level-0 5-point PML stencil / Jacobi sweep, all blocks)",
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "peak_source": src, "launches_timed": n, "avg_launch_us": ms / n * 1e3,
             "algorithmic_bytes_per_launch": per_launch,
