@@ -350,9 +350,9 @@ def main():
         from paper_2204_06489_gb300.autotune import tune_kkt
         f.set_model(0, wl.gamma_start)
         f.forward(opts, want_data=False)
-        opts, table = tune_kkt(f, opts, (6, 8, 12), (1, 2))
-        tuned = [{"inner_iters": n, "wdepth": wd, "s": round(t, 3), "outer": o, "ok": ok}
-                 for n, wd, t, o, ok in table]
+        opts, table = tune_kkt(f, opts, (6, 8, 12), (2,), (30, 60))
+        tuned = [{"inner_iters": n, "wdepth": wd, "restart": rs, "s": round(t, 3), "outer": o, "ok": ok}
+                 for n, wd, rs, t, o, ok in table]
     g0 = torch.from_numpy(wl.gamma_start).cuda()
     d_dev = torch.from_numpy(d_true[0]).cuda()
     ds_dev = torch.zeros(wl.grid.nx * wl.grid.nz, dtype=torch.float64, device="cuda")
@@ -423,7 +423,7 @@ def main():
            "dtype": "c64+f64-refine" if args.precision == 1 else "c128",
            "data": "synthetic (seeded layered-faulted model; data from the library's forward modelling)",
            "config": {"workload": WORKLOAD, "blocks": 120, "grid_padded": "441x181", "eps": opts.eps,
-                      "tol": 1e-6, "restart": 30, "inner_iters": opts.inner_iters, "mg": f"W(2,2) to level {opts.mg_wdepth}, V below",
+                      "tol": 1e-6, "restart": opts.restart, "inner_iters": opts.inner_iters, "mg": f"W(2,2) to level {opts.mg_wdepth}, V below",
                       "l2": "working set > L2 (packed KKT vector 153 MB, Krylov basis 9.4 GB)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "kkt_solve_s": per_step, "outer_iters_per_step": outer, "krylov_iters_per_s": outer / per_step,
