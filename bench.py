@@ -400,6 +400,7 @@ def main():
     inner = sum(s.inner_iters for s in stats) / len(stats)
     relres = max(s.rel_res for s in stats)
     t_fwd = sum(s.t_forward_ms for s in stats) / len(stats)
+    fwd_sweeps = sum(s.fwd_sweeps for s in stats) / len(stats)
     t_kkt = sum(s.t_solve_ms for s in stats) / len(stats)
 
     # end to end through the C ABI with host buffers (h2d model + data, d2h update)
@@ -428,7 +429,7 @@ def main():
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "kkt_solve_s": per_step, "outer_iters_per_step": outer, "krylov_iters_per_s": outer / per_step,
            "inner_block_iters_per_s": inner / per_step, "rel_res_max": relres,
-           "phase_ms": {"forward": t_fwd, "kkt_solve": t_kkt}, "autotune": tuned,
+           "phase_ms": {"forward": t_fwd, "kkt_solve": t_kkt}, "forward_sweeps": fwd_sweeps, "autotune": tuned,
            "gpu_launches": int(launches),
            "roofline": _roofline(st_ms, st_bytes, st_n, peaks),
            "clocks": ck,

@@ -78,6 +78,8 @@ template <typename T> struct LevelView {
   const T *gam;                    // gamma values (precision T)
   const typename cplx<T>::t *dg;   // diagonal of every operator (precision T)
   const typename cplx<T>::t *dgi;  // its inverse
+  const int *skip;                 // nullable: per-block flag, nonzero = block finished, do nothing
+  unsigned long long *work;        // nullable: the launch adds the number of grid nodes it processed
   int n_tiles;
   int n_blocks;
 };

@@ -149,6 +149,7 @@ k_field_op(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__restrict_
            const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
   typedef typename cplx<T>::t T2;
   const TileDev t = L.tiles[blockIdx.x];
+  if (L.skip && L.skip[t.blk]) return;
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);
@@ -238,6 +239,7 @@ k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__rest
   extern __shared__ __align__(16) unsigned char ft_raw[];
   FtStage<T> *stg = reinterpret_cast<FtStage<T> *>(ft_raw);
   const TileDev t = L.tiles[blockIdx.x];
+  if (L.skip && L.skip[t.blk]) return;
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const int nx = op.nx, nz = op.nz;
@@ -246,6 +248,7 @@ k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__rest
   const int j = j0 + warp;
   const bool row_ok = j < nz;
   const unsigned long long pol = keep_policy();
+  if (L.work && threadIdx.x == 0) atomicAdd(L.work, (unsigned long long)min(TILE_ROWS, nz - j0) * nx);
   const T2 *X = L.st + op.st;
   const T2 *iXh = X + nx;
   const T2 *Zr = iXh + nx + 1;
@@ -350,6 +353,7 @@ k_resid_restrict(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__
   typedef typename cplx<T>::t T2;
   __shared__ T2 r[RR_FR][RR_FW];
   const TileDev t = Lc.tiles[blockIdx.x];
+  if (Lc.skip && Lc.skip[t.blk]) return;
   const BlkDev bkc = Lc.blks[t.blk];
   const OpDev opc = Lc.ops[bkc.op];
   const BlkDev bkf = Lf.blks[t.blk];
@@ -403,6 +407,7 @@ k_prolong_add(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__res
               typename cplx<T>::t *__restrict__ xf) {
   typedef typename cplx<T>::t T2;
   const TileDev t = Lf.tiles[blockIdx.x];
+  if (Lf.skip && Lf.skip[t.blk]) return;
   const BlkDev bkf = Lf.blks[t.blk];
   const OpDev opf = Lf.ops[bkf.op];
   const BlkDev bkc = Lc.blks[t.blk];
@@ -447,6 +452,7 @@ struct CoarseArgs {
   const double2 *inv;               // coarsest inverses (offset per op in inv_off)
   const long long *inv_off;         // [n_ops]
   const int *inst_nlev;             // number of levels of each instance
+  const int *skip;                  // nullable: per-block "finished" flags
   int ls, nu1, nu2, cyc, cj, wdepth;
   double w;
 };
@@ -607,6 +613,7 @@ k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restrict__ st,
   typedef typename cplx<T>::t T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2 *sm = reinterpret_cast<T2 *>(smem_raw);
+  if (a.skip && a.skip[blockIdx.x]) return;
   SmemCycle<T, CJ> c(a, st, dg, dgi);
   c.blk = blockIdx.x;
   c.nlev = a.inst_nlev[a.blks[a.ls][c.blk].inst];
@@ -828,6 +835,7 @@ k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typena
              const typename cplx<T>::t *a2, const typename cplx<T>::t *b2, double2 *partial) {
   typedef typename cplx<T>::t T2;
   const TileDev t = L.tiles[blockIdx.x];
+  if (L.skip && L.skip[t.blk]) return;
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);
@@ -910,7 +918,7 @@ __device__ __forceinline__ double2 sum_tiles(const double2 *partial, int t0, int
 // stage 4: after the x/r update (q0 = <r, r>): rho_old = rho; done if omega == 0 or
 //          ||r||^2 <= tol^2 ||b||^2 (tol > 0).
 __global__ void k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1, const double2 *partial,
-                               BiState *S, int stage, double tol) {
+                               BiState *S, int stage, double tol, int *done_out) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_blocks) return;
   BiState s = S[b];
@@ -952,6 +960,7 @@ __global__ void k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1,
     if (tol > 0.0 && rr.x <= tol * tol * s.bnorm2) s.done = 1;
   }
   S[b] = s;
+  done_out[b] = s.done;
 }
 
 // BiCGStab updates on a field (per-block scalars):
@@ -966,6 +975,7 @@ k_bicg_update(LevelView<T> L, int opk, const BiState *S, typename cplx<T>::t *y,
               typename cplx<T>::t *y2, const typename cplx<T>::t *e) {
   typedef typename cplx<T>::t T2;
   const TileDev t = L.tiles[blockIdx.x];
+  if (L.skip && L.skip[t.blk]) return;
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);
@@ -1010,6 +1020,7 @@ k_kkt_rows(LevelView<T> L, const InstDev *inst, const double *cf, const typename
            const T *__restrict__ ds, typename cplx<T>::t *__restrict__ yu, typename cplx<T>::t *__restrict__ ylm) {
   typedef typename cplx<T>::t T2;
   const TileDev t = L.tiles[blockIdx.x];
+  if (L.skip && L.skip[t.blk]) return;
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const InstDev in = inst[bk.inst];
@@ -1092,6 +1103,7 @@ k_coupling_scatter(LevelView<T> L, const InstDev *inst, const double *cf, const 
                    typename cplx<T>::t *__restrict__ y) {
   typedef typename cplx<T>::t T2;
   const TileDev t = L.tiles[blockIdx.x];
+  if (L.skip && L.skip[t.blk]) return;
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const InstDev in = inst[bk.inst];
@@ -1452,6 +1464,7 @@ template <typename TI, typename TO, typename T>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_blk_scale(LevelView<T> L, const TI *x, const double *f, TO *y, int accumulate) {
   const TileDev t = L.tiles[blockIdx.x];
+  if (L.skip && L.skip[t.blk]) return;
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);

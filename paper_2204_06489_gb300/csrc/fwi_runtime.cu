@@ -130,6 +130,7 @@ template <typename T> struct Work {
   DBuf<T2> t0a, t0b;                                   // level-0 smoother buffers
   DBuf<T2> r, rh, p, v, s, t, ph, sh;                  // BiCGStab
   DBuf<BiState> bst;
+  DBuf<int> done;                                      // per-block "finished" flags of the inner solve
   DBuf<T2> u;                                          // forward wavefields (precision T)
   // FGMRES
   int m = 0;
@@ -176,6 +177,7 @@ struct Ctx {
   std::string hier_key;
   int ls = 1, nlev_max = 1;
   int ls_p[2] = {1, 1};   // first shared-memory level for complex64 / complex128
+  const int *cur_skip = nullptr;   // set inside an inner solve: per-block finished flags
   LevelTables lv[MAX_LEVELS];
   std::vector<OpDev> h_ops;
   DBuf<OpDev> d_ops;
@@ -214,16 +216,22 @@ struct Ctx {
   // direct launches on this context's stream, with the launch's algorithmic bytes
   int timer_on = 0;
   std::vector<cudaEvent_t> ev_a, ev_b;
-  std::vector<double> ev_bytes;
+  std::vector<double> ev_bytes;    // bytes per processed node of each timed launch
+  DBuf<unsigned long long> ev_work; // nodes processed by each timed launch (device counters)
   size_t ev_used = 0;
   double timer_ms = 0.0, timer_bytes = 0.0;
   long long timer_n = 0;
   void harvest() {
+    std::vector<unsigned long long> work(ev_used, 0);
+    if (ev_used) {
+      cudaMemcpy(work.data(), ev_work.p, ev_used * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+      cudaMemset(ev_work.p, 0, ev_used * sizeof(unsigned long long));
+    }
     for (size_t q = 0; q < ev_used; ++q) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ev_a[q], ev_b[q]) == cudaSuccess) {
         timer_ms += ms;
-        timer_bytes += ev_bytes[q];
+        timer_bytes += ev_bytes[q] * (double)work[q];
         ++timer_n;
       }
     }
@@ -316,6 +324,8 @@ template <typename T> LevelView<T> Ctx::viewA() {
   v.ops = d_ops.p; v.blks = lv[0].blksA.p; v.tiles = lv[0].tiles.p;
   v.st = st_ptr<T>(*this); v.gam = gam_ptr<T>(*this);
   v.dg = dg_ptr<T>(*this); v.dgi = dgi_ptr<T>(*this);
+  v.skip = cur_skip;
+  v.work = nullptr;
   v.n_tiles = lv[0].n_tiles; v.n_blocks = B;
   return v;
 }
@@ -324,6 +334,8 @@ template <typename T> LevelView<T> Ctx::viewM(int l) {
   v.ops = d_ops.p; v.blks = lv[l].blksM.p; v.tiles = lv[l].tiles.p;
   v.st = st_ptr<T>(*this); v.gam = gam_ptr<T>(*this);
   v.dg = dg_ptr<T>(*this); v.dgi = dgi_ptr<T>(*this);
+  v.skip = cur_skip;
+  v.work = nullptr;
   v.n_tiles = lv[l].n_tiles; v.n_blocks = B;
   return v;
 }
@@ -689,6 +701,7 @@ template <typename T> void Ctx::ensure_work(const fwi_opts &o) {
   w.r.alloc(F0); w.rh.alloc(F0); w.p.alloc(F0); w.v.alloc(F0);
   w.s.alloc(F0); w.t.alloc(F0); w.ph.alloc(F0); w.sh.alloc(F0);
   w.bst.alloc(B);
+  w.done.alloc(B);
   w.u.alloc(F0);
   w.vin.alloc(nkkt); w.zout.alloc(nkkt); w.tmp.alloc(nkkt);
   w.scal.alloc(8);
@@ -736,18 +749,23 @@ void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const t
                    typename cplx<T>::t *y, bool opA, int level) {
   LevelView<T> L = opA ? viewA<T>() : viewM<T>(level);
   bool timed = false;
-  if (timer_on && level == 0) {
+  if (timer_on && level == 0 && sizeof(T) == 4) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(st, &cs));
     timed = cs == cudaStreamCaptureStatusNone;
   }
   if (timed) {
+    if (!ev_work.p) {
+      ev_work.alloc(4096);
+      ev_work.zero(st);
+    }
     if (ev_used == ev_a.size()) {
       cudaEvent_t a, b2;
       CK(cudaEventCreate(&a));
       CK(cudaEventCreate(&b2));
       ev_a.push_back(a); ev_b.push_back(b2); ev_bytes.push_back(0.0);
     }
+    L.work = ev_work.p + ev_used;
     CK(cudaEventRecord(ev_a[ev_used], st));
   }
   // the shared-memory staged kernel on the fine levels, the direct one on small grids
@@ -762,9 +780,9 @@ void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const t
   KCHECK();
   if (timed) {
     CK(cudaEventRecord(ev_b[ev_used], st));
-    // algorithmic bytes: each complex element read/written once
+    // algorithmic bytes per processed node: each complex operand / result once
     int streams = (mode == FM_APPLY || mode == FM_JACOBI0) ? 2 : 3;
-    ev_bytes[ev_used] = (double)streams * (double)F0 * sizeof(typename cplx<T>::t);
+    ev_bytes[ev_used] = (double)streams * sizeof(typename cplx<T>::t);
     ++ev_used;
     if (ev_used >= 4096) sync();
   }
@@ -789,6 +807,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
   CoarseArgs ca;
   for (int l = 0; l < MAX_LEVELS; ++l) ca.blks[l] = l < nlev_max ? lv[l].blksM.p : nullptr;
   ca.ops = d_ops.p; ca.inv = inv.p; ca.inv_off = inv_off.p; ca.inst_nlev = d_inst_nlev.p;
+  ca.skip = cur_skip;
   const int ls = ls_p[sizeof(T) == 8];
   ca.ls = ls; ca.nu1 = o.nu1; ca.nu2 = o.nu2; ca.cyc = o.mg_cycle; ca.cj = cj; ca.w = o.omega_jac;
   ca.wdepth = o.mg_wdepth;
@@ -842,6 +861,7 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
   CoarseArgs ca;
   for (int l = 0; l < MAX_LEVELS; ++l) ca.blks[l] = l < nlev_max ? lv[l].blksM.p : nullptr;
   ca.ops = d_ops.p; ca.inv = inv.p; ca.inv_off = inv_off.p; ca.inst_nlev = d_inst_nlev.p;
+  ca.skip = cur_skip;
   const int ls = ls_p[sizeof(T) == 8];
   ca.ls = ls; ca.nu1 = o.nu1; ca.nu2 = o.nu2; ca.cyc = o.mg_cycle; ca.cj = cj; ca.w = o.omega_jac;
   ca.wdepth = o.mg_wdepth;
@@ -897,7 +917,7 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
     KCHECK();
   };
   auto scal = [&](int stage) {
-    k_bicg_scalars<<<sb, 128, 0, st>>>(B, lv[0].t0.p, lv[0].t1.p, partial.p, w.bst.p, stage, tol);
+    k_bicg_scalars<<<sb, 128, 0, st>>>(B, lv[0].t0.p, lv[0].t1.p, partial.p, w.bst.p, stage, tol, w.done.p);
     KCHECK();
   };
   // x = 0, r = b, rh = b, p = v = 0
@@ -908,6 +928,15 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   upd(4, w.v.p, nullptr, nullptr, nullptr, nullptr, nullptr);
   block_dots<T>(1, b, b, nullptr, nullptr, nullptr, nullptr);
   scal(0);
+  // from here on, kernels skip the blocks whose solve has finished (zero
+  // right-hand side, breakdown, or tolerance reached): their x and r no longer
+  // change, exactly as when the iteration stops
+  struct SkipGuard {
+    Ctx &c;
+    ~SkipGuard() { c.cur_skip = nullptr; }
+  } guard{*this};
+  cur_skip = w.done.p;
+  L = viewA<T>();
   for (int it = 0; it < iters; ++it) {
     block_dots<T>(1, w.rh.p, w.r.p, nullptr, nullptr, nullptr, nullptr);
     scal(1);
