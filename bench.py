@@ -94,12 +94,11 @@ def _peaks():
         return {}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one level-0 k_field_op_tile
-# Jacobi launch per algorithmic byte: 203.6 MB / 229.9 MB from the ncu capture
-# summarised in profiles/k_field_op_tile_marmousi_120blocks.md (set to None
-# when the kernel changes until it is captured again).  The reported traffic
-# scales it by each timed launch's algorithmic bytes.
-TRAFFIC_PER_ALG_BYTE = 203.6 / 229.9
+# dram__bytes_read.sum + dram__bytes_write.sum of the level-0 stencil launches
+# per algorithmic byte, from the ncu capture summarised under profiles/ (None
+# while the kernels have changed since the last capture).  The reported
+# traffic scales it by each timed launch's algorithmic bytes.
+TRAFFIC_PER_ALG_BYTE = None
 
 
 def _roofline(ms, nbytes, n, peaks):
@@ -111,7 +110,8 @@ def _roofline(ms, nbytes, n, peaks):
         return None
     ach = nbytes / (ms / 1e3) / 1e9
     per_launch = nbytes / n
-    return {"kernel": "k_field_op_tile<float> (level-0 5-point PML stencil / Jacobi sweep, all blocks)",
+    return {"kernel": "level-0 5-point PML stencil kernels, all blocks: k_jacobi2_march "
+                      "(two fused damped-Jacobi sweeps) and k_field_op_march (operator apply)",
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "peak_source": src, "launches_timed": n, "avg_launch_us": ms / n * 1e3,
             "algorithmic_bytes_per_launch": per_launch,

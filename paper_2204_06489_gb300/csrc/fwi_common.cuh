@@ -16,6 +16,13 @@
 #define TILE_ROWS 8
 #define TILE_THREADS (TILE_ROWS * 32)
 #define MAX_LEVELS 12
+#define MARCH_COLS 30
+#define MARCH2_COLS 28
+#ifndef MARCH_ROWS
+#define MARCH_ROWS 16
+#endif
+#define MARCH_THREADS 256
+#define MARCH_LEVEL_MAX 1   // levels 0 .. MARCH_LEVEL_MAX get column-strip tables
 
 namespace fwi {
 
@@ -69,11 +76,19 @@ struct TileDev {
   int row0;              // first row of the tile
 };
 
+// A column strip walked by one warp (register-marching stencil kernel):
+// columns col0 .. col0 + MARCH_COLS - 1 (clipped to the grid), rows row0 .. row1 - 1.
+struct StripDev {
+  int blk, col0, row0, row1;
+};
+
 // Everything a field kernel needs to know about one level of the batch.
 template <typename T> struct LevelView {
   const OpDev *ops;
   const BlkDev *blks;
   const TileDev *tiles;
+  const StripDev *strips;          // column strips (fine levels only; else null)
+  const StripDev *strips2;         // narrower strips of the two-sweep smoother
   const typename cplx<T>::t *st;   // stretch arrays (precision T)
   const T *gam;                    // gamma values (precision T)
   const typename cplx<T>::t *dg;   // diagonal of every operator (precision T)
@@ -81,6 +96,8 @@ template <typename T> struct LevelView {
   const int *skip;                 // nullable: per-block flag, nonzero = block finished, do nothing
   unsigned long long *work;        // nullable: the launch adds the number of grid nodes it processed
   int n_tiles;
+  int n_strips;
+  int n_strips2;
   int n_blocks;
 };
 

@@ -337,6 +337,268 @@ k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__rest
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-marching variant for the fine levels.  A warp owns a strip of
+// MARCH_COLS columns and up to MARCH_ROWS rows of one block and walks down it:
+// lane l holds column col0 - 1 + l, so lanes 0 and 31 carry the strip's halo
+// columns and lanes 1 .. MARCH_COLS compute.  The three rows of x the stencil
+// needs (north, centre, south) stay in registers, east / west neighbours come
+// from the neighbouring lanes by shuffles, and the loads of row j + 1 are in
+// flight while row j is computed.  Every x element is loaded once per strip
+// (plus two halo rows per strip and two halo columns per row), no shared
+// memory and no block barrier.  Nodes outside the grid are zeros (Dirichlet
+// ghosts), so the strip's own bounds give the boundary rows and columns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+template <typename T2> __device__ __forceinline__ T2 shfl_down1(T2 v) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+  return v;
+}
+template <typename T2> __device__ __forceinline__ T2 shfl_up1(T2 v) {
+  v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
+  return v;
+}
+
+// With ND > 0 (FM_APPLY only) the kernel also forms the strip's share of dot
+// products with its output y and the vector passed as b (a):
+//   ND = 1: partial[strip][0] = <a, y>;   ND = 2: <y, a>, <y, y>
+// (<u, v> = sum conj(u) v; data-precision sums per lane and warp, FP64 per strip).
+template <typename T, bool CJ, int MODE, int ND = 0>
+__global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 4 : 2)
+k_field_op_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
+                 const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y,
+                 double2 *partial = nullptr) {
+  typedef typename cplx<T>::t T2;
+  static_assert(ND == 0 || MODE == FM_APPLY, "dots only with the operator apply");
+  constexpr bool need_x = MODE != FM_JACOBI0;
+  constexpr bool need_b = MODE != FM_APPLY || ND > 0;
+  constexpr bool need_dgi = MODE == FM_JACOBI || MODE == FM_JACOBI0;
+  const int gw = blockIdx.x * (MARCH_THREADS / 32) + (threadIdx.x >> 5);
+  if (gw >= L.n_strips) return;                       // whole warps leave together
+  const StripDev s = L.strips[gw];
+  if (L.skip && L.skip[s.blk]) return;
+  const BlkDev bk = L.blks[s.blk];
+  const OpDev op = L.ops[bk.op];
+  const int nx = op.nx, nz = op.nz;
+  const int lane = threadIdx.x & 31;
+  const int i = s.col0 - 1 + lane;
+  const bool in_grid = i >= 0 && i < nx;
+  const bool own = lane >= 1 && lane <= MARCH_COLS && i < nx;
+  if (L.work && s.col0 == 0 && lane == 0)
+    atomicAdd(L.work, (unsigned long long)(s.row1 - s.row0) * nx);
+  const unsigned long long pol = keep_policy();
+  const T2 zero = mk<T2>(0, 0);
+  const T2 *X = L.st + op.st;
+  const T2 *iXh = X + nx;
+  const T2 *Zr = iXh + nx + 1;
+  const T2 *iZh = Zr + nz;
+  T2 Xi = zero, iw = zero, ie = zero;
+  if (need_x && own) {
+    Xi = cmaybe_conj(X[i], CJ);
+    iw = cmaybe_conj(iXh[i], CJ);
+    ie = cmaybe_conj(iXh[i + 1], CJ);
+  }
+  // element offsets of (row j, column i) in the field and in the operator arrays
+  const int ic = in_grid ? i : 0;
+  long long ef = bk.off + ic + (long long)s.row0 * nx;
+  long long eo = op.dg + ic + (long long)s.row0 * nx;
+  const bool ldx_ok = need_x && in_grid;
+  // L2 prefetch of the strip's band (x rows row0-1 .. row1, b rows row0 ..
+  // row1-1): DRAM latency is paid once per strip, the row loop waits on L2 hits
+  {
+    const int r_lo = max(s.row0 - 1, 0), r_hi = min(s.row1 + 1, nz);
+    if (ldx_ok)
+      for (int r = r_lo; r < r_hi; ++r) prefetch_l2(x + ef + (long long)(r - s.row0) * nx);
+    if (need_b && own)
+      for (int r = s.row0; r < s.row1; ++r) prefetch_l2(b + ef + (long long)(r - s.row0) * nx);
+  }
+
+  int j = s.row0;
+  T2 xn = (ldx_ok && j > 0) ? x[ef - nx] : zero;
+  T2 xc = ldx_ok ? x[ef] : zero;
+  T2 xs = (ldx_ok && j + 1 < nz) ? x[ef + nx] : zero;
+  T2 bv = (need_b && own) ? b[ef] : zero;
+  T2 dv = (need_x && own) ? ld_keep_p(L.dg + eo, pol) : zero;
+  T2 div = (need_dgi && own) ? ld_keep_p(L.dgi + eo, pol) : zero;
+  T2 Zj = zero, iZn = zero, iZs = zero;
+  if (need_x) {
+    Zj = cmaybe_conj(Zr[j], CJ);
+    iZn = cmaybe_conj(iZh[j], CJ);
+    iZs = cmaybe_conj(iZh[j + 1], CJ);
+  }
+  T d0r = 0, d0i = 0, d1r = 0;   // dot sums of this lane (ND > 0)
+  for (; j < s.row1; ++j) {
+    // loads of the next row first
+    const bool more = j + 1 < s.row1;
+    const long long ef1 = ef + nx, eo1 = eo + nx;
+    const T2 xs2 = (more && ldx_ok && j + 2 < nz) ? x[ef1 + nx] : zero;
+    const T2 bv2 = (more && need_b && own) ? b[ef1] : zero;
+    const T2 dv2 = (more && need_x && own) ? ld_keep_p(L.dg + eo1, pol) : zero;
+    const T2 div2 = (more && need_dgi && own) ? ld_keep_p(L.dgi + eo1, pol) : zero;
+    T2 Zj2 = zero, iZs2 = zero;
+    if (need_x && more) {
+      Zj2 = cmaybe_conj(Zr[j + 1], CJ);
+      iZs2 = cmaybe_conj(iZh[j + 2], CJ);
+    }
+    T2 out = zero;
+    if (MODE == FM_JACOBI0) {
+      out = cscale(cmul(bv, cmaybe_conj(div, CJ)), w);
+    } else {
+      const T2 xe = shfl_down1(xc);
+      const T2 xw = shfl_up1(xc);
+      const T2 hx = cadd(cmul(ie, xe), cmul(iw, xw));
+      const T2 hz = cadd(cmul(iZs, xs), cmul(iZn, xn));
+      const T2 ax = csub(csub(cmul(cmaybe_conj(dv, CJ), xc), cmul(Zj, hx)), cmul(Xi, hz));
+      if (MODE == FM_APPLY) out = ax;
+      else if (MODE == FM_RESID) out = csub(bv, ax);
+      else out = cadd(xc, cscale(cmul(csub(bv, ax), cmaybe_conj(div, CJ)), w));
+    }
+    if (own) {
+      y[ef] = out;
+      if (ND == 1) {            // conj(a) y
+        d0r = tfma(bv.x, out.x, tfma(bv.y, out.y, d0r));
+        d0i = tfma(bv.x, out.y, tfma(-bv.y, out.x, d0i));
+      } else if (ND == 2) {     // conj(y) a, conj(y) y
+        d0r = tfma(out.x, bv.x, tfma(out.y, bv.y, d0r));
+        d0i = tfma(out.x, bv.y, tfma(-out.y, bv.x, d0i));
+        d1r = tfma(out.x, out.x, tfma(out.y, out.y, d1r));
+      }
+    }
+    xn = xc; xc = xs; xs = xs2;
+    bv = bv2; dv = dv2; div = div2;
+    Zj = Zj2; iZn = iZs; iZs = iZs2;
+    ef = ef1; eo = eo1;
+  }
+  if (ND > 0) {
+    for (int o = 16; o > 0; o >>= 1) {
+      d0r += __shfl_down_sync(0xffffffffu, d0r, o);
+      d0i += __shfl_down_sync(0xffffffffu, d0i, o);
+      if (ND == 2) d1r += __shfl_down_sync(0xffffffffu, d1r, o);
+    }
+    if (lane == 0) {
+      partial[(long long)gw * 3] = make_double2((double)d0r, (double)d0i);
+      if (ND == 2) partial[(long long)gw * 3 + 1] = make_double2((double)d1r, 0.0);
+    }
+  }
+}
+
+// Two damped-Jacobi sweeps in one pass (temporal blocking of the smoother):
+//   ZERO:  x1 = w b / cc                     (first sweep from x = 0)
+//   else:  x1 = x + w (b - Op x) / cc
+//   y = x1 + w (b - Op x1) / cc
+// A warp walks a strip as in k_field_op_march, with two halo columns on each
+// side: lane l holds column col0 - 2 + l, x1 is formed on lanes 1 .. 30 and
+// y on lanes 2 .. 29 (MARCH2_COLS columns).  Going down row k, the warp forms
+// x1 on row k from x on rows k-1 .. k+1 and y on row k-1 from x1 on rows
+// k-2 .. k, so x1 lives only in registers (one halo row of x1 above and
+// below the strip is formed twice).  Traffic per node: x, b in, y out (b in,
+// y out for ZERO) instead of five (or six) streams for two separate sweeps.
+// x1 is zero outside the grid (Dirichlet ghosts), like x.
+template <typename T, bool CJ, bool ZERO>
+__global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 3 : 1)
+k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
+                const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
+  typedef typename cplx<T>::t T2;
+  const int gw = blockIdx.x * (MARCH_THREADS / 32) + (threadIdx.x >> 5);
+  if (gw >= L.n_strips2) return;                      // whole warps leave together
+  const StripDev s = L.strips2[gw];
+  if (L.skip && L.skip[s.blk]) return;
+  const BlkDev bk = L.blks[s.blk];
+  const OpDev op = L.ops[bk.op];
+  const int nx = op.nx, nz = op.nz;
+  const int lane = threadIdx.x & 31;
+  const int i = s.col0 - 2 + lane;
+  const bool in_grid = i >= 0 && i < nx;
+  const bool mid = lane >= 1 && lane <= 30 && in_grid;
+  const bool own = lane >= 2 && lane <= MARCH2_COLS + 1 && in_grid;
+  if (L.work && s.col0 == 0 && lane == 0)
+    atomicAdd(L.work, (unsigned long long)(s.row1 - s.row0) * nx);
+  const unsigned long long pol = keep_policy();
+  const T2 zero = mk<T2>(0, 0);
+  const T2 *X = L.st + op.st;
+  const T2 *iXh = X + nx;
+  const T2 *Zr = iXh + nx + 1;
+  const T2 *iZh = Zr + nz;
+  T2 Xi = zero, iw = zero, ie = zero;
+  if (mid) {
+    Xi = cmaybe_conj(X[i], CJ);
+    iw = cmaybe_conj(iXh[i], CJ);
+    ie = cmaybe_conj(iXh[i + 1], CJ);
+  }
+  const int ic = in_grid ? i : 0;
+  const long long ef0 = bk.off + ic;     // field element of (row 0, column i)
+  const long long eo0 = op.dg + ic;      // operator-array element of (row 0, column i)
+  const bool ldx_ok = !ZERO && in_grid;
+  const int kb = s.row0 - 1, ke = s.row1;          // x1 rows formed: kb .. ke
+  {
+    const int r_lo = max(kb - 1, 0), r_hi = min(ke + 2, nz);
+    if (ldx_ok)
+      for (int r = r_lo; r < r_hi; ++r) prefetch_l2(x + ef0 + (long long)r * nx);
+    if (mid)
+      for (int r = max(kb, 0); r < min(ke + 1, nz); ++r) prefetch_l2(b + ef0 + (long long)r * nx);
+  }
+  // row data of row k (zero outside the grid)
+  auto ldxr = [&](int k) -> T2 { return (ldx_ok && k >= 0 && k < nz) ? x[ef0 + (long long)k * nx] : zero; };
+  auto ldbr = [&](int k) -> T2 { return (mid && k >= 0 && k < nz) ? b[ef0 + (long long)k * nx] : zero; };
+  auto lddr = [&](int k) -> T2 {
+    return (mid && k >= 0 && k < nz) ? cmaybe_conj(ld_keep_p(L.dg + eo0 + (long long)k * nx, pol), CJ) : zero;
+  };
+  auto lddir = [&](int k) -> T2 {
+    return (mid && k >= 0 && k < nz) ? cmaybe_conj(ld_keep_p(L.dgi + eo0 + (long long)k * nx, pol), CJ) : zero;
+  };
+  auto ldZ = [&](int k) -> T2 { return (k >= 0 && k < nz) ? cmaybe_conj(Zr[k], CJ) : zero; };
+  auto ldiZ = [&](int k) -> T2 { return (k >= 0 && k <= nz) ? cmaybe_conj(iZh[k], CJ) : zero; };
+  // one damped-Jacobi update at a node: u + w (bb - (d uc - Zj (ie ue + iw uw) - Xi (iZs us + iZn un))) dinv
+  auto jac = [&](T2 u, T2 uw, T2 ue, T2 un, T2 us, T2 bb, T2 d, T2 dinv, T2 Zj, T2 iZn, T2 iZs) -> T2 {
+    const T2 hx = cadd(cmul(ie, ue), cmul(iw, uw));
+    const T2 hz = cadd(cmul(iZs, us), cmul(iZn, un));
+    const T2 au = csub(csub(cmul(d, u), cmul(Zj, hx)), cmul(Xi, hz));
+    return cadd(u, cscale(cmul(csub(bb, au), dinv), w));
+  };
+
+  // pipeline state at the top of iteration k
+  T2 xm = ldxr(kb - 1), x0 = ldxr(kb), xp = ldxr(kb + 1);
+  T2 bm = zero, dm = zero, dim = zero;                     // row k-1
+  T2 b0 = ldbr(kb), d0 = ZERO ? zero : lddr(kb), di0 = lddir(kb);   // row k
+  T2 Zm = zero, Z0 = ldZ(kb);
+  T2 iZm = zero, iZ0 = ldiZ(kb), iZ1 = ldiZ(kb + 1);       // 1/Z at half rows k-1/2 (iZ0), k+1/2 (iZ1)
+  T2 ym2 = zero, ym1 = zero;                               // x1 on rows k-2, k-1
+  for (int k = kb; k <= ke; ++k) {
+    // loads for row k + 1
+    const bool more = k < ke;
+    const T2 xn = more ? ldxr(k + 2) : zero;
+    const T2 bn = more ? ldbr(k + 1) : zero;
+    const T2 dn = more ? lddr(k + 1) : zero;
+    const T2 din = more ? lddir(k + 1) : zero;
+    const T2 Zn = more ? ldZ(k + 1) : zero;
+    const T2 iZ2 = more ? ldiZ(k + 2) : zero;
+    // x1 on row k (lanes 1 .. 30)
+    T2 y1 = zero;
+    if (ZERO) {
+      if (mid && k >= 0 && k < nz) y1 = cscale(cmul(b0, di0), w);
+    } else {
+      const T2 xe = shfl_down1(x0), xw = shfl_up1(x0);
+      if (mid && k >= 0 && k < nz) y1 = jac(x0, xw, xe, xm, xp, b0, d0, di0, Z0, iZ0, iZ1);
+    }
+    // y on row k - 1 (lanes 2 .. 29)
+    const T2 ye = shfl_down1(ym1), yw = shfl_up1(ym1);
+    if (k - 1 >= s.row0 && own) {
+      // row k - 1: 1/Z at half rows k-3/2 (iZm) and k-1/2 (iZ0)
+      y[ef0 + (long long)(k - 1) * nx] = jac(ym1, yw, ye, ym2, y1, bm, dm, dim, Zm, iZm, iZ0);
+    }
+    xm = x0; x0 = xp; xp = xn;
+    bm = b0; dm = d0; dim = di0;
+    b0 = bn; d0 = dn; di0 = din;
+    Zm = Z0; Z0 = Zn;
+    iZm = iZ0; iZ0 = iZ1; iZ1 = iZ2;
+    ym2 = ym1; ym1 = y1;
+  }
+}
+
 // Fused residual + restriction (R = P^T, i.e. 4x full weighting):
 //   bc[J][I] = sum_{a,b in -1..1} w_a w_b (bf - Op xf)[2J+1+b][2I+1+a],  w = (1/2, 1, 1/2).
 // A CTA takes one coarse row tile (8 coarse rows) and walks it in chunks of
@@ -457,6 +719,7 @@ struct CoarseArgs {
   double w;
 };
 
+#define SC_UNROLL 4
 template <typename T, bool CJ>
 struct SmemCycle {
   typedef typename cplx<T>::t T2;
@@ -468,21 +731,33 @@ struct SmemCycle {
   __device__ SmemCycle(const CoarseArgs &a_, const T2 *st_, const T2 *dg_, const T2 *dgi_)
       : a(a_), st(st_), dg(dg_), dgi(dgi_) {}
 
+  // A warp takes a row; a lane handles columns lane + 32 q, q < SC_UNROLL, at
+  // a time, so that the L2 loads of the operator arrays (diagonal, stretch
+  // factors) of those nodes are in flight together; results are stored after
+  // all of them are formed.
   __device__ void jacobi(int l, bool from_zero) {
-    const OpDev &o = op[l];
+    const OpDev o = op[l];
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const T w = (T)a.w;
+    const T2 *xl = xs[l], *bl = bs[l];
+    T2 *tl = ts[l];
     for (int j = threadIdx.x >> 5; j < o.nz; j += nw) {
       const RowOp<T, CJ> R(o, st, dg, dgi, j);
-      const T2 *xr = xs[l] + j * o.nx;
-      for (int i = lane; i < o.nx; i += 32) {
-        int k = j * o.nx + i;
-        if (from_zero) {
-          ts[l][k] = cscale(cmul(bs[l][k], R.dinv(i)), w);
-        } else {
-          T2 ax = R.apply(xr, i);
-          ts[l][k] = cadd(xr[i], cscale(cmul(csub(bs[l][k], ax), R.dinv(i)), w));
+      const T2 *xr = xl + j * o.nx;
+      const T2 *br = bl + j * o.nx;
+      for (int i0 = lane; i0 < o.nx; i0 += 32 * SC_UNROLL) {
+        T2 out[SC_UNROLL];
+#pragma unroll
+        for (int q = 0; q < SC_UNROLL; ++q) {
+          const int i = i0 + 32 * q;
+          if (i < o.nx) {
+            if (from_zero) out[q] = cscale(cmul(br[i], R.dinv(i)), w);
+            else out[q] = cadd(xr[i], cscale(cmul(csub(br[i], R.apply(xr, i)), R.dinv(i)), w));
+          }
         }
+#pragma unroll
+        for (int q = 0; q < SC_UNROLL; ++q)
+          if (i0 + 32 * q < o.nx) tl[j * o.nx + i0 + 32 * q] = out[q];
       }
     }
     __syncthreads();
@@ -494,7 +769,19 @@ struct SmemCycle {
     for (int j = threadIdx.x >> 5; j < o.nz; j += nw) {
       const RowOp<T, CJ> R(o, st, dg, dgi, j);
       const T2 *xr = xs[l] + j * o.nx;
-      for (int i = lane; i < o.nx; i += 32) ts[l][j * o.nx + i] = csub(bs[l][j * o.nx + i], R.apply(xr, i));
+      const T2 *br = bs[l] + j * o.nx;
+      T2 *tr = ts[l] + j * o.nx;
+      for (int i0 = lane; i0 < o.nx; i0 += 32 * SC_UNROLL) {
+        T2 out[SC_UNROLL];
+#pragma unroll
+        for (int q = 0; q < SC_UNROLL; ++q) {
+          const int i = i0 + 32 * q;
+          if (i < o.nx) out[q] = csub(br[i], R.apply(xr, i));
+        }
+#pragma unroll
+        for (int q = 0; q < SC_UNROLL; ++q)
+          if (i0 + 32 * q < o.nx) tr[i0 + 32 * q] = out[q];
+      }
     }
     __syncthreads();
     const OpDev &c = op[l + 1];
@@ -604,7 +891,7 @@ struct SmemCycle {
   }
 };
 
-#define COARSE_THREADS 1024
+#define COARSE_THREADS 512
 template <typename T, bool CJ>
 __global__ void __launch_bounds__(COARSE_THREADS, 1)
 k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restrict__ st,
@@ -828,6 +1115,44 @@ __global__ void k_gauss_jordan(const int *dims, const long long *aug_off, const 
 // ---------------------------------------------------------------------------
 // partial[tile][q] = sum over the tile of conj(a_q) b_q (q < nd): per-thread
 // run accumulation (see DOT_RUN), FP64 across threads; fixed order, no atomics.
+// End of a tile's dot products (one CTA = one row tile, one warp per row):
+// each lane's run remainder (data precision) and flushed FP64 part are
+// reduced across the warp, then the tile's warps in fixed order, into
+// partial[tile * 3 + q], q < nd.  Every thread of the CTA must call it.
+template <typename T>
+__device__ __forceinline__ void tile_dots_store(int nd, const T *rre, const T *rim, const double *tre,
+                                                const double *tim, double2 *partial) {
+  __shared__ double2 red[3][TILE_THREADS / 32];
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (q < nd) {
+      // lane run remainders are reduced across the warp in the data precision,
+      // the flushed FP64 parts only when a lane had more than DOT_RUN terms
+      T x = rre[q], y = rim[q];
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+      }
+      double dx = 0.0, dy = 0.0;
+      if (__any_sync(0xffffffffu, tre[q] != 0.0 || tim[q] != 0.0)) {
+        dx = tre[q]; dy = tim[q];
+        for (int o = 16; o > 0; o >>= 1) {
+          dx += __shfl_down_sync(0xffffffffu, dx, o);
+          dy += __shfl_down_sync(0xffffffffu, dy, o);
+        }
+      }
+      if (lane == 0) red[q][threadIdx.x >> 5] = make_double2(dx + (double)x, dy + (double)y);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nd) {
+    double2 s = make_double2(0, 0);
+    for (int wi = 0; wi < TILE_THREADS / 32; ++wi) { s.x += red[threadIdx.x][wi].x; s.y += red[threadIdx.x][wi].y; }
+    partial[(long long)blockIdx.x * 3 + threadIdx.x] = s;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typename cplx<T>::t *b0,
@@ -866,35 +1191,7 @@ k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typena
       }
     }
   }
-  __shared__ double2 red[3][TILE_THREADS / 32];
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    if (q < nd) {
-      // lane run remainders are reduced across the warp in the data precision,
-      // the flushed FP64 parts only when a lane had more than DOT_RUN terms
-      T x = rre[q], y = rim[q];
-      for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_down_sync(0xffffffffu, x, o);
-        y += __shfl_down_sync(0xffffffffu, y, o);
-      }
-      double dx = 0.0, dy = 0.0;
-      if (__any_sync(0xffffffffu, tre[q] != 0.0 || tim[q] != 0.0)) {
-        dx = tre[q]; dy = tim[q];
-        for (int o = 16; o > 0; o >>= 1) {
-          dx += __shfl_down_sync(0xffffffffu, dx, o);
-          dy += __shfl_down_sync(0xffffffffu, dy, o);
-        }
-      }
-      if (lane == 0) red[q][threadIdx.x >> 5] = make_double2(dx + (double)x, dy + (double)y);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < nd) {
-    double2 s = make_double2(0, 0);
-    for (int wi = 0; wi < TILE_THREADS / 32; ++wi) { s.x += red[threadIdx.x][wi].x; s.y += red[threadIdx.x][wi].y; }
-    partial[(long long)blockIdx.x * 3 + threadIdx.x] = s;
-  }
+  tile_dots_store<T>(nd, rre, rim, tre, tim, partial);
 }
 
 // Per-block BiCGStab scalars (double2 = complex FP64):
@@ -917,6 +1214,8 @@ __device__ __forceinline__ double2 sum_tiles(const double2 *partial, int t0, int
 // stage 3: omega = <t, s>/<t, t> (q0, q1); omega = 0 if <t,t> == 0.
 // stage 4: after the x/r update (q0 = <r, r>): rho_old = rho; done if omega == 0 or
 //          ||r||^2 <= tol^2 ||b||^2 (tol > 0).
+// stage 5: stage 4, then (if not done) stage 1 of the next iteration with
+//          q1 = <rh, r>.
 __global__ void k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1, const double2 *partial,
                                BiState *S, int stage, double tol, int *done_out) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -951,13 +1250,22 @@ __global__ void k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1,
     double2 ts = sum_tiles(partial, t0, t1, 0);
     double2 tt = sum_tiles(partial, t0, t1, 1);
     s.omega = tt.x > 0.0 ? cscale(ts, 1.0 / tt.x) : make_double2(0, 0);
-  } else if (stage == 4) {
+  } else if (stage == 4 || stage == 5) {
     double2 rr = sum_tiles(partial, t0, t1, 0);
     s.rnorm2 = rr.x;
     s.rho_old = s.rho;
     s.it += 1;
     if (s.omega.x == 0.0 && s.omega.y == 0.0) s.done = 1;
     if (tol > 0.0 && rr.x <= tol * tol * s.bnorm2) s.done = 1;
+    if (stage == 5 && !s.done) {
+      // the next iteration's stage 1 from q1 = <rh, r>
+      s.rho = sum_tiles(partial, t0, t1, 1);
+      if (s.rho.x == 0.0 && s.rho.y == 0.0) {
+        s.done = 1; s.alpha = s.omega = s.beta = make_double2(0, 0);
+      } else {
+        s.beta = cmul(cdiv(s.rho, s.rho_old), cdiv(s.alpha, s.omega));
+      }
+    }
   }
   S[b] = s;
   done_out[b] = s.done;
@@ -999,6 +1307,48 @@ k_bicg_update(LevelView<T> L, int opk, const BiState *S, typename cplx<T>::t *y,
       y[k] = mk<T2>(0, 0);
     }
   }
+}
+
+// The last update of a BiCGStab iteration fused with the dots that follow it:
+//   x += alpha ph + omega sh;  r = s - omega t;
+//   partial[tile][0] = <r, r>,  partial[tile][1] = <rh, r>   (new r)
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_bicg_xr(LevelView<T> L, const BiState *S, typename cplx<T>::t *__restrict__ x,
+          const typename cplx<T>::t *__restrict__ ph, const typename cplx<T>::t *__restrict__ sh,
+          const typename cplx<T>::t *__restrict__ sv, typename cplx<T>::t *__restrict__ r,
+          const typename cplx<T>::t *__restrict__ t, const typename cplx<T>::t *__restrict__ rh,
+          double2 *partial) {
+  typedef typename cplx<T>::t T2;
+  const TileDev tl = L.tiles[blockIdx.x];
+  if (L.skip && L.skip[tl.blk]) return;               // whole CTA
+  const BlkDev bk = L.blks[tl.blk];
+  const OpDev op = L.ops[bk.op];
+  const int j = tl.row0 + (threadIdx.x >> 5);
+  double tre[3] = {0, 0, 0}, tim[3] = {0, 0, 0};
+  T rre[3] = {0, 0, 0}, rim[3] = {0, 0, 0};
+  if (j < op.nz) {
+    const BiState st = S[tl.blk];
+    const T2 al = mk<T2>(st.alpha.x, st.alpha.y), om = mk<T2>(st.omega.x, st.omega.y);
+    const long long base = bk.off + (long long)j * op.nx;
+    int cnt = 0;
+    for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
+      const long long k = base + i;
+      x[k] = cadd(x[k], cadd(cmul(al, ph[k]), cmul(om, sh[k])));
+      const T2 rn = csub(sv[k], cmul(om, t[k]));
+      r[k] = rn;
+      const T2 a = rh[k];
+      rre[0] = tfma(rn.x, rn.x, tfma(rn.y, rn.y, rre[0]));
+      rre[1] = tfma(a.x, rn.x, tfma(a.y, rn.y, rre[1]));
+      rim[1] = tfma(a.x, rn.y, tfma(-a.y, rn.x, rim[1]));
+      if (sizeof(T) == 4 && ++cnt == DOT_RUN) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) { tre[q] += rre[q]; tim[q] += rim[q]; rre[q] = 0; rim[q] = 0; }
+        cnt = 0;
+      }
+    }
+  }
+  tile_dots_store<T>(2, rre, rim, tre, tim, partial);
 }
 
 // ---------------------------------------------------------------------------

@@ -114,12 +114,16 @@ struct Instance {
 struct LevelTables {
   std::vector<BlkDev> hM, hA;
   std::vector<TileDev> htiles;
-  std::vector<int> ht0, ht1;
+  std::vector<StripDev> hstrips, hstrips2;
+  std::vector<int> ht0, ht1, hs0, hs1;
   DBuf<BlkDev> blksM, blksA;
   DBuf<TileDev> tiles;
-  DBuf<int> t0, t1;
+  DBuf<StripDev> strips, strips2;
+  DBuf<int> t0, t1, s0, s1;   // per block: its row tiles [t0, t1), its column strips [s0, s1)
   long long field = 0;  // complex elements of one field on this level
   int n_tiles = 0;
+  int n_strips = 0;
+  int n_strips2 = 0;
 };
 
 template <typename T> struct Work {
@@ -205,6 +209,7 @@ struct Ctx {
   DBuf<double> seg_partial, inst_norm2, inst_fac;
   DBuf<int> d_flag;
   DBuf<double2> partial;   // per-tile partial sums [n_tiles0 * 3]
+  DBuf<double2> partial_s; // per-strip partial sums [n_strips0 * 3]
   DBuf<double> blkfac, blkn0, blkn;   // per-block factors / norms
   DBuf<double> misfit_d, inst_gref;
   int u_version32 = -1, u_version64 = -1;
@@ -270,6 +275,14 @@ struct Ctx {
                                            const fwi_opts &o, typename cplx<T>::t *const *lx,
                                            typename cplx<T>::t *const *lb, typename cplx<T>::t *const *lt,
                                            typename cplx<T>::t *t0);
+  template <typename T> bool timer_begin(int level, LevelView<T> &L);
+  template <typename T> void smooth(int nu, bool zero, int cj, T wj, const typename cplx<T>::t *bl,
+                                    typename cplx<T>::t *&cur, typename cplx<T>::t *&oth, int l);
+  void timer_end(int streams, size_t elem_bytes);
+  template <typename T> void apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *y,
+                                        const typename cplx<T>::t *a, int nd);
+  template <typename T> void jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
+                                     typename cplx<T>::t *y, int level);
   template <typename T> void field_op(int mode, int cj, T w, const typename cplx<T>::t *x,
                                       const typename cplx<T>::t *b, typename cplx<T>::t *y, bool opA,
                                       int level);
@@ -327,6 +340,8 @@ template <typename T> LevelView<T> Ctx::viewA() {
   v.skip = cur_skip;
   v.work = nullptr;
   v.n_tiles = lv[0].n_tiles; v.n_blocks = B;
+  v.strips = lv[0].strips.p; v.n_strips = lv[0].n_strips;
+  v.strips2 = lv[0].strips2.p; v.n_strips2 = lv[0].n_strips2;
   return v;
 }
 template <typename T> LevelView<T> Ctx::viewM(int l) {
@@ -337,6 +352,8 @@ template <typename T> LevelView<T> Ctx::viewM(int l) {
   v.skip = cur_skip;
   v.work = nullptr;
   v.n_tiles = lv[l].n_tiles; v.n_blocks = B;
+  v.strips = lv[l].strips.p; v.n_strips = lv[l].n_strips;
+  v.strips2 = lv[l].strips2.p; v.n_strips2 = lv[l].n_strips2;
   return v;
 }
 
@@ -637,7 +654,8 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
     LevelTables &T = lv[l];
     T.hM.assign(B, BlkDev{0, 0, 0});
     T.hA.assign(B, BlkDev{0, 0, 0});
-    T.htiles.clear(); T.ht0.assign(B, 0); T.ht1.assign(B, 0);
+    T.htiles.clear(); T.hstrips.clear(); T.hstrips2.clear(); T.ht0.assign(B, 0); T.ht1.assign(B, 0);
+    T.hs0.assign(B, 0); T.hs1.assign(B, 0);
     long long off = 0;
     for (int b = 0; b < B; ++b) {
       int i = blk_inst[b];
@@ -654,15 +672,33 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
       if (l <= ls)
         for (int r0 = 0; r0 < nz; r0 += TILE_ROWS) T.htiles.push_back(TileDev{b, r0});
       T.ht1[b] = (int)T.htiles.size();
+      // column strips of the register-marching stencil kernel (fine levels):
+      // block-major, then row band, then column, so that neighbouring strips
+      // (which share halo rows and columns) run close together
+      T.hs0[b] = (int)T.hstrips.size();
+      if (l <= MARCH_LEVEL_MAX)
+        for (int r0 = 0; r0 < nz; r0 += MARCH_ROWS) {
+          for (int c0 = 0; c0 < nx; c0 += MARCH_COLS)
+            T.hstrips.push_back(StripDev{b, c0, r0, std::min(r0 + MARCH_ROWS, nz)});
+          for (int c0 = 0; c0 < nx; c0 += MARCH2_COLS)
+            T.hstrips2.push_back(StripDev{b, c0, r0, std::min(r0 + MARCH_ROWS, nz)});
+        }
+      T.hs1[b] = (int)T.hstrips.size();
       off += (long long)nx * nz;
     }
     T.field = off;
     T.n_tiles = (int)T.htiles.size();
+    T.n_strips = (int)T.hstrips.size();
+    T.strips.upload(T.hstrips, st);
+    T.n_strips2 = (int)T.hstrips2.size();
+    T.strips2.upload(T.hstrips2, st);
     T.blksM.upload(T.hM, st);
     T.blksA.upload(T.hA, st);
     T.tiles.upload(T.htiles, st);
     T.t0.upload(T.ht0, st);
     T.t1.upload(T.ht1, st);
+    T.s0.upload(T.hs0, st);
+    T.s1.upload(T.hs1, st);
   }
   // dynamic shared memory of the double-buffered stencil kernels (both precisions)
   CK(cudaFuncSetAttribute(k_field_op_tile<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -674,6 +710,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   CK(cudaFuncSetAttribute(k_field_op_tile<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(2 * sizeof(FtStage<double>))));
   partial.alloc((size_t)std::max(1, lv[0].n_tiles) * 3);
+  partial_s.alloc((size_t)std::max(1, lv[0].n_strips) * 3);
   blkfac.alloc(B); blkn0.alloc(B); blkn.alloc(B);
   // coupling factors: KKT (h^2 gamma_ref omega^2) and gradient (h^2 omega^2)
   std::vector<double> cK(B), cG(B);
@@ -744,48 +781,112 @@ template <typename T> void Ctx::ensure_krylov(const fwi_opts &o) {
 // --------------------------------------------------------------------------
 // field operations
 // --------------------------------------------------------------------------
+template <typename T, bool CJ>
+static void launch_march_cj(int grid, cudaStream_t st, const LevelView<T> &L, int mode, T wj,
+                            const typename cplx<T>::t *x, const typename cplx<T>::t *b, typename cplx<T>::t *y) {
+  switch (mode) {
+    case FM_APPLY: k_field_op_march<T, CJ, FM_APPLY><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y); break;
+    case FM_RESID: k_field_op_march<T, CJ, FM_RESID><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y); break;
+    case FM_JACOBI: k_field_op_march<T, CJ, FM_JACOBI><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y); break;
+    default: k_field_op_march<T, CJ, FM_JACOBI0><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y); break;
+  }
+}
+
 template <typename T>
 void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
                    typename cplx<T>::t *y, bool opA, int level) {
   LevelView<T> L = opA ? viewA<T>() : viewM<T>(level);
-  bool timed = false;
-  if (timer_on && level == 0 && sizeof(T) == 4) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    CK(cudaStreamIsCapturing(st, &cs));
-    timed = cs == cudaStreamCaptureStatusNone;
-  }
-  if (timed) {
-    if (!ev_work.p) {
-      ev_work.alloc(4096);
-      ev_work.zero(st);
-    }
-    if (ev_used == ev_a.size()) {
-      cudaEvent_t a, b2;
-      CK(cudaEventCreate(&a));
-      CK(cudaEventCreate(&b2));
-      ev_a.push_back(a); ev_b.push_back(b2); ev_bytes.push_back(0.0);
-    }
-    L.work = ev_work.p + ev_used;
-    CK(cudaEventRecord(ev_a[ev_used], st));
-  }
-  // the shared-memory staged kernel on the fine levels, the direct one on small grids
+  const bool timed = timer_begin<T>(level, L);
+  // the register-marching kernel on the fine levels, the direct one on small grids
+#ifdef FWI_STENCIL_TILE
   if (level <= 1) {
     const size_t sm = 2 * sizeof(FtStage<T>);
     if (cj) k_field_op_tile<T, true><<<L.n_tiles, TILE_THREADS, sm, st>>>(L, mode, wj, x, b, y);
     else k_field_op_tile<T, false><<<L.n_tiles, TILE_THREADS, sm, st>>>(L, mode, wj, x, b, y);
   } else {
+#else
+  if (level <= MARCH_LEVEL_MAX) {
+    const int grid = std::max(1, (L.n_strips + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
+    if (cj) launch_march_cj<T, true>(grid, st, L, mode, wj, x, b, y);
+    else launch_march_cj<T, false>(grid, st, L, mode, wj, x, b, y);
+  } else {
+#endif
     if (cj) k_field_op<T, true><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
     else k_field_op<T, false><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
   }
   KCHECK();
-  if (timed) {
-    CK(cudaEventRecord(ev_b[ev_used], st));
-    // algorithmic bytes per processed node: each complex operand / result once
-    int streams = (mode == FM_APPLY || mode == FM_JACOBI0) ? 2 : 3;
-    ev_bytes[ev_used] = (double)streams * sizeof(typename cplx<T>::t);
-    ++ev_used;
-    if (ev_used >= 4096) sync();
+  // algorithmic bytes per processed node: each complex operand / result once
+  if (timed) timer_end((mode == FM_APPLY || mode == FM_JACOBI0) ? 2 : 3, sizeof(typename cplx<T>::t));
+}
+
+// Live timing of the level-0 complex64 stencil launches that are not being
+// captured into a graph (CUDA events on the context's stream; the kernels
+// count the nodes they processed into L.work).
+template <typename T>
+bool Ctx::timer_begin(int level, LevelView<T> &L) {
+  if (!timer_on || level != 0 || sizeof(T) != 4) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return false;
+  if (!ev_work.p) {
+    ev_work.alloc(4096);
+    ev_work.zero(st);
   }
+  if (ev_used == ev_a.size()) {
+    cudaEvent_t a, b2;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b2));
+    ev_a.push_back(a); ev_b.push_back(b2); ev_bytes.push_back(0.0);
+  }
+  L.work = ev_work.p + ev_used;
+  CK(cudaEventRecord(ev_a[ev_used], st));
+  return true;
+}
+
+void Ctx::timer_end(int streams, size_t elem_bytes) {
+  CK(cudaEventRecord(ev_b[ev_used], st));
+  ev_bytes[ev_used] = (double)streams * (double)elem_bytes;
+  ++ev_used;
+  if (ev_used >= 4096) sync();
+}
+
+// y = A' x (cj: A'^H) on level 0 with nd = 1: partial_s[strip][0] = <a, y>,
+// nd = 2: <y, a>, <y, y> (per-strip shares of the BiCGStab dot products).
+template <typename T>
+void Ctx::apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *y, const typename cplx<T>::t *a,
+                     int nd) {
+  LevelView<T> L = viewA<T>();
+  const bool timed = timer_begin<T>(0, L);
+  const int grid = std::max(1, (L.n_strips + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
+  const T w = 0;
+  if (nd == 1) {
+    if (cj) k_field_op_march<T, true, FM_APPLY, 1><<<grid, MARCH_THREADS, 0, st>>>(L, w, x, a, y, partial_s.p);
+    else k_field_op_march<T, false, FM_APPLY, 1><<<grid, MARCH_THREADS, 0, st>>>(L, w, x, a, y, partial_s.p);
+  } else {
+    if (cj) k_field_op_march<T, true, FM_APPLY, 2><<<grid, MARCH_THREADS, 0, st>>>(L, w, x, a, y, partial_s.p);
+    else k_field_op_march<T, false, FM_APPLY, 2><<<grid, MARCH_THREADS, 0, st>>>(L, w, x, a, y, partial_s.p);
+  }
+  KCHECK();
+  if (timed) timer_end(3, sizeof(typename cplx<T>::t));
+}
+
+// Two damped-Jacobi sweeps in one pass on a fine level (x == nullptr: the
+// first sweep starts from zero); y must not alias x or b.
+template <typename T>
+void Ctx::jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
+                  typename cplx<T>::t *y, int level) {
+  LevelView<T> L = viewM<T>(level);
+  const bool timed = timer_begin<T>(level, L);
+  const int grid = std::max(1, (L.n_strips2 + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
+  if (x == nullptr) {
+    if (cj) k_jacobi2_march<T, true, true><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
+    else k_jacobi2_march<T, false, true><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
+  } else {
+    if (cj) k_jacobi2_march<T, true, false><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
+    else k_jacobi2_march<T, false, false><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
+  }
+  KCHECK();
+  if (timed) timer_end(x == nullptr ? 2 : 3, sizeof(typename cplx<T>::t));
 }
 
 template <typename T>
@@ -799,6 +900,33 @@ void Ctx::block_dots(int nd, const typename cplx<T>::t *a0, const typename cplx<
 
 // One multigrid cycle for the shifted operator, x = cycle(b) (Sec. 5: the
 // shifted-Laplacian preconditioner; levels >= ls run in shared memory).
+// nu damped-Jacobi sweeps on level l (from x = 0 when zero, else from cur);
+// the result ends in cur (oth is the other buffer).  Sweeps go in fused pairs
+// on the fine levels.
+template <typename T>
+void Ctx::smooth(int nu, bool zero, int cj, T wj, const typename cplx<T>::t *bl, typename cplx<T>::t *&cur,
+                 typename cplx<T>::t *&oth, int l) {
+  int s = 0;
+  if (l <= MARCH_LEVEL_MAX) {
+    if (zero && nu >= 2) {
+      jacobi2<T>(cj, wj, nullptr, bl, cur, l);
+      s = 2;
+    }
+    for (; s + 1 < nu; s += 2) {
+      jacobi2<T>(cj, wj, cur, bl, oth, l);
+      std::swap(cur, oth);
+    }
+  }
+  for (; s < nu; ++s) {
+    if (zero && s == 0) {
+      field_op<T>(FM_JACOBI0, cj, wj, nullptr, bl, cur, false, l);
+    } else {
+      field_op<T>(FM_JACOBI, cj, wj, cur, bl, oth, false, l);
+      std::swap(cur, oth);
+    }
+  }
+}
+
 template <typename T>
 void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj, const fwi_opts &o) {
   typedef typename cplx<T>::t T2;
@@ -826,10 +954,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
     }
     T2 *cur = xa, *oth = xb;
     if (o.nu1 == 0) CK(cudaMemsetAsync(cur, 0, lv[l].field * sizeof(T2), st));
-    for (int s = 0; s < o.nu1; ++s) {
-      field_op<T>(s == 0 ? FM_JACOBI0 : FM_JACOBI, cj, wj, s == 0 ? nullptr : cur, bl, s == 0 ? cur : oth, false, l);
-      if (s > 0) std::swap(cur, oth);
-    }
+    smooth<T>(o.nu1, true, cj, wj, bl, cur, oth, l);
     int reps = (l > 0 && l <= o.mg_wdepth) ? o.mg_cycle : 1;
     for (int r = 0; r < reps; ++r) {
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
@@ -840,10 +965,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
       k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
       KCHECK();
     }
-    for (int s = 0; s < o.nu2; ++s) {
-      field_op<T>(FM_JACOBI, cj, wj, cur, bl, oth, false, l);
-      std::swap(cur, oth);
-    }
+    smooth<T>(o.nu2, false, cj, wj, bl, cur, oth, l);
     return cur;
   };
   T2 *res = cyc(0, b, x, w.t0a.p);
@@ -878,10 +1000,7 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
     }
     T2 *cur = xa, *oth = xb;
     if (o.nu1 == 0) CK(cudaMemsetAsync(cur, 0, lv[l].field * sizeof(T2), st));
-    for (int s = 0; s < o.nu1; ++s) {
-      field_op<T>(s == 0 ? FM_JACOBI0 : FM_JACOBI, cj, wj, s == 0 ? nullptr : cur, bl, s == 0 ? cur : oth, false, l);
-      if (s > 0) std::swap(cur, oth);
-    }
+    smooth<T>(o.nu1, true, cj, wj, bl, cur, oth, l);
     int reps = (l > 0 && l <= o.mg_wdepth) ? o.mg_cycle : 1;
     for (int r = 0; r < reps; ++r) {
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
@@ -892,10 +1011,7 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
       k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
       KCHECK();
     }
-    for (int s = 0; s < o.nu2; ++s) {
-      field_op<T>(FM_JACOBI, cj, wj, cur, bl, oth, false, l);
-      std::swap(cur, oth);
-    }
+    smooth<T>(o.nu2, false, cj, wj, bl, cur, oth, l);
     return cur;
   };
   T2 *res = cyc(0, b, x, t0);
@@ -920,6 +1036,11 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
     k_bicg_scalars<<<sb, 128, 0, st>>>(B, lv[0].t0.p, lv[0].t1.p, partial.p, w.bst.p, stage, tol, w.done.p);
     KCHECK();
   };
+  // stages whose dots come from the strip kernels (operator apply fused with dots)
+  auto scal_s = [&](int stage) {
+    k_bicg_scalars<<<sb, 128, 0, st>>>(B, lv[0].s0.p, lv[0].s1.p, partial_s.p, w.bst.p, stage, tol, w.done.p);
+    KCHECK();
+  };
   // x = 0, r = b, rh = b, p = v = 0
   upd(4, x, nullptr, nullptr, nullptr, nullptr, nullptr);
   upd(3, w.r.p, b, nullptr, nullptr, nullptr, nullptr);
@@ -937,22 +1058,22 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   } guard{*this};
   cur_skip = w.done.p;
   L = viewA<T>();
+  // rho = <rh, r> = <b, b> for the first iteration: the partials still hold <b, b>
+  scal(1);
   for (int it = 0; it < iters; ++it) {
-    block_dots<T>(1, w.rh.p, w.r.p, nullptr, nullptr, nullptr, nullptr);
-    scal(1);
     upd(0, w.p.p, w.r.p, w.v.p, nullptr, nullptr, nullptr);          // p = r + beta (p - omega v)
     mg_cycle<T>(w.p.p, w.ph.p, cj, o);                                 // ph = K p
-    field_op<T>(FM_APPLY, cj, (T)0, w.ph.p, nullptr, w.v.p, true, 0);  // v = A ph
-    block_dots<T>(1, w.rh.p, w.v.p, nullptr, nullptr, nullptr, nullptr);
-    scal(2);
+    apply_dots<T>(cj, w.ph.p, w.v.p, w.rh.p, 1);                       // v = A ph, <rh, v>
+    scal_s(2);
     upd(1, w.s.p, w.r.p, w.v.p, nullptr, nullptr, nullptr);          // s = r - alpha v
     mg_cycle<T>(w.s.p, w.sh.p, cj, o);                                 // sh = K s
-    field_op<T>(FM_APPLY, cj, (T)0, w.sh.p, nullptr, w.t.p, true, 0);  // t = A sh
-    block_dots<T>(2, w.t.p, w.s.p, w.t.p, w.t.p, nullptr, nullptr);
-    scal(3);
-    upd(2, x, w.ph.p, w.sh.p, w.s.p, w.r.p, w.t.p);                   // x += a ph + w sh; r = s - w t
-    block_dots<T>(1, w.r.p, w.r.p, nullptr, nullptr, nullptr, nullptr);
-    scal(4);
+    apply_dots<T>(cj, w.sh.p, w.t.p, w.s.p, 2);                        // t = A sh, <t, s>, <t, t>
+    scal_s(3);
+    // x += alpha ph + omega sh; r = s - omega t; <r, r>, <rh, r>
+    k_bicg_xr<T><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, x, w.ph.p, w.sh.p, w.s.p, w.r.p, w.t.p, w.rh.p,
+                                              partial.p);
+    KCHECK();
+    scal(5);                                                           // stage 4, then the next stage 1
     if (count) *count += B;
   }
 }
