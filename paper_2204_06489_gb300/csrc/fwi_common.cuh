@@ -22,7 +22,6 @@
 #define MARCH_ROWS 16
 #endif
 #define MARCH_THREADS 256
-#define MARCH_LEVEL_MAX 1   // levels 0 .. MARCH_LEVEL_MAX get column-strip tables
 
 namespace fwi {
 

@@ -720,70 +720,114 @@ struct CoarseArgs {
 };
 
 #define SC_UNROLL 4
+// The levels of one block held in shared memory: x, b and a scratch vector
+// per level, plus the level's operator data (stretch factors X, 1/X_{i-1/2},
+// Z, 1/Z_{j-1/2} and gamma), so that a sweep reads nothing from global
+// memory; the diagonal is formed at each node from them,
+//   cc = Z_j (1/X_{i+1/2} + 1/X_{i-1/2}) + X_i (1/Z_{j+1/2} + 1/Z_{j-1/2} - m gamma Z_j),
+// m = (1 + i beta)(omega h_l)^2 (the same expression the set-up kernel
+// evaluates in FP64), conjugated when CJ.
+template <typename T> struct SmemLevel {
+  typedef typename cplx<T>::t T2;
+  T2 *x, *b, *t;           // level vectors (t: scratch, ping-pong with x)
+  const T2 *X, *iXh, *Z, *iZh;
+  const T *g;
+  int nx, nz;
+  T2 mass;
+};
+
+// Shared memory of the coarse levels of one block (bytes): what
+// k_coarse_cycle lays out per level, rounded as it rounds.
+__host__ __device__ __forceinline__ size_t smem_level_bytes(int nx, int nz, size_t elem) {
+  const size_t n = (size_t)nx * nz;
+  return 3 * n * elem + (size_t)(2 * nx + 2 * nz + 2) * elem + ((n + 3) / 4 * 4) * (elem / 2);
+}
+
 template <typename T, bool CJ>
 struct SmemCycle {
   typedef typename cplx<T>::t T2;
   const CoarseArgs &a;
-  const T2 *st, *dg, *dgi;
-  T2 *xs[MAX_LEVELS], *bs[MAX_LEVELS], *ts[MAX_LEVELS];
+  SmemLevel<T> lvl[MAX_LEVELS];
   OpDev op[MAX_LEVELS];
   int blk, nlev;
-  __device__ SmemCycle(const CoarseArgs &a_, const T2 *st_, const T2 *dg_, const T2 *dgi_)
-      : a(a_), st(st_), dg(dg_), dgi(dgi_) {}
+  __device__ SmemCycle(const CoarseArgs &a_) : a(a_) {}
 
-  // A warp takes a row; a lane handles columns lane + 32 q, q < SC_UNROLL, at
-  // a time, so that the L2 loads of the operator arrays (diagonal, stretch
-  // factors) of those nodes are in flight together; results are stored after
-  // all of them are formed.
+  // (Op u) at node (j, i) of level L and its diagonal; urow points at row j.
+  struct Node { T2 au, cc; };
+  __device__ __forceinline__ static Node node(const SmemLevel<T> &L, const T2 *urow, int j, int i, T2 Zj,
+                                              T2 iZn, T2 iZs, T2 szm) {
+    const T2 Xi = cmaybe_conj(L.X[i], CJ);
+    const T2 iw = cmaybe_conj(L.iXh[i], CJ);
+    const T2 ie = cmaybe_conj(L.iXh[i + 1], CJ);
+    const T g = L.g[j * L.nx + i];
+    Node r;
+    // cc = Zj (ie + iw) + Xi (iZs + iZn - g m Zj); szm = (iZs + iZn, m Zj)
+    r.cc = cadd(cmul(Zj, cadd(ie, iw)), cmul(Xi, csub(szm, cscale(cmul(L.mass, Zj), g))));
+    const T2 zero = mk<T2>(0, 0);
+    const T2 uc = urow[i];
+    const T2 ue = i + 1 < L.nx ? urow[i + 1] : zero;
+    const T2 uw = i > 0 ? urow[i - 1] : zero;
+    const T2 us = j + 1 < L.nz ? urow[i + L.nx] : zero;
+    const T2 un = j > 0 ? urow[i - L.nx] : zero;
+    const T2 hx = cadd(cmul(ie, ue), cmul(iw, uw));
+    const T2 hz = cadd(cmul(iZs, us), cmul(iZn, un));
+    r.au = csub(csub(cmul(r.cc, uc), cmul(Zj, hx)), cmul(Xi, hz));
+    return r;
+  }
+  // A warp takes a row, a lane the columns lane + 32 q (q < SC_UNROLL) at a
+  // time; results are stored after all of them are formed.
   __device__ void jacobi(int l, bool from_zero) {
-    const OpDev o = op[l];
+    const SmemLevel<T> L = lvl[l];     // a copy: kept in registers across the shared-memory stores
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const T w = (T)a.w;
-    const T2 *xl = xs[l], *bl = bs[l];
-    T2 *tl = ts[l];
-    for (int j = threadIdx.x >> 5; j < o.nz; j += nw) {
-      const RowOp<T, CJ> R(o, st, dg, dgi, j);
-      const T2 *xr = xl + j * o.nx;
-      const T2 *br = bl + j * o.nx;
-      for (int i0 = lane; i0 < o.nx; i0 += 32 * SC_UNROLL) {
+    for (int j = threadIdx.x >> 5; j < L.nz; j += nw) {
+      const T2 Zj = cmaybe_conj(L.Z[j], CJ), iZn = cmaybe_conj(L.iZh[j], CJ), iZs = cmaybe_conj(L.iZh[j + 1], CJ);
+      const T2 szm = cadd(iZn, iZs);
+      const T2 *xr = L.x + j * L.nx;
+      const T2 *br = L.b + j * L.nx;
+      for (int i0 = lane; i0 < L.nx; i0 += 32 * SC_UNROLL) {
         T2 out[SC_UNROLL];
 #pragma unroll
         for (int q = 0; q < SC_UNROLL; ++q) {
           const int i = i0 + 32 * q;
-          if (i < o.nx) {
-            if (from_zero) out[q] = cscale(cmul(br[i], R.dinv(i)), w);
-            else out[q] = cadd(xr[i], cscale(cmul(csub(br[i], R.apply(xr, i)), R.dinv(i)), w));
+          if (i < L.nx) {
+            const Node nd = node(L, xr, j, i, Zj, iZn, iZs, szm);
+            const T2 d = cinv(nd.cc);
+            if (from_zero) out[q] = cscale(cmul(br[i], d), w);
+            else out[q] = cadd(xr[i], cscale(cmul(csub(br[i], nd.au), d), w));
           }
         }
 #pragma unroll
         for (int q = 0; q < SC_UNROLL; ++q)
-          if (i0 + 32 * q < o.nx) tl[j * o.nx + i0 + 32 * q] = out[q];
+          if (i0 + 32 * q < L.nx) L.t[j * L.nx + i0 + 32 * q] = out[q];
       }
     }
     __syncthreads();
-    T2 *tmp = xs[l]; xs[l] = ts[l]; ts[l] = tmp;   // ping-pong
+    lvl[l].x = L.t; lvl[l].t = L.x;   // ping-pong
   }
   __device__ void restrict_to(int l) {  // b_{l+1} = P^T (b_l - M_l x_l)
-    const OpDev &o = op[l];
+    const SmemLevel<T> L = lvl[l];
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int j = threadIdx.x >> 5; j < o.nz; j += nw) {
-      const RowOp<T, CJ> R(o, st, dg, dgi, j);
-      const T2 *xr = xs[l] + j * o.nx;
-      const T2 *br = bs[l] + j * o.nx;
-      T2 *tr = ts[l] + j * o.nx;
-      for (int i0 = lane; i0 < o.nx; i0 += 32 * SC_UNROLL) {
+    for (int j = threadIdx.x >> 5; j < L.nz; j += nw) {
+      const T2 Zj = cmaybe_conj(L.Z[j], CJ), iZn = cmaybe_conj(L.iZh[j], CJ), iZs = cmaybe_conj(L.iZh[j + 1], CJ);
+      const T2 szm = cadd(iZn, iZs);
+      const T2 *xr = L.x + j * L.nx;
+      const T2 *br = L.b + j * L.nx;
+      T2 *tr = L.t + j * L.nx;
+      for (int i0 = lane; i0 < L.nx; i0 += 32 * SC_UNROLL) {
         T2 out[SC_UNROLL];
 #pragma unroll
         for (int q = 0; q < SC_UNROLL; ++q) {
           const int i = i0 + 32 * q;
-          if (i < o.nx) out[q] = csub(br[i], R.apply(xr, i));
+          if (i < L.nx) out[q] = csub(br[i], node(L, xr, j, i, Zj, iZn, iZs, szm).au);
         }
 #pragma unroll
         for (int q = 0; q < SC_UNROLL; ++q)
-          if (i0 + 32 * q < o.nx) tr[i0 + 32 * q] = out[q];
+          if (i0 + 32 * q < L.nx) tr[i0 + 32 * q] = out[q];
       }
     }
     __syncthreads();
+    const OpDev &o = op[l];
     const OpDev &c = op[l + 1];
     int nc = c.nx * c.nz;
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
@@ -797,10 +841,10 @@ struct SmemCycle {
           int i = 2 * I + 1 + da;
           if (i < 0 || i >= o.nx) continue;
           T wx = da == 0 ? T(1) : T(0.5);
-          acc = cadd(acc, cscale(ts[l][j * o.nx + i], wz * wx));
+          acc = cadd(acc, cscale(lvl[l].t[j * o.nx + i], wz * wx));
         }
       }
-      bs[l + 1][k] = acc;
+      lvl[l + 1].b[k] = acc;
     }
     __syncthreads();
   }
@@ -821,10 +865,10 @@ struct SmemCycle {
           if (i & 1) { if (p) continue; I = (i - 1) >> 1; wx = 1; }
           else { I = (i >> 1) - 1 + p; wx = 0.5; }
           if (I < 0 || I >= c.nx) continue;
-          acc = cadd(acc, cscale(xs[l + 1][J * c.nx + I], wz * wx));
+          acc = cadd(acc, cscale(lvl[l + 1].x[J * c.nx + I], wz * wx));
         }
       }
-      xs[l][k] = cadd(xs[l][k], acc);
+      lvl[l].x[k] = cadd(lvl[l].x[k], acc);
     }
     __syncthreads();
   }
@@ -839,7 +883,7 @@ struct SmemCycle {
       for (int c = lane; c < n; c += 32) {
         double2 m = M[(long long)r * n + c];
         if (CJ) m.y = -m.y;
-        double2 v = to_d2(bs[l][c]);
+        double2 v = to_d2(lvl[l].b[c]);
         ax += m.x * v.x - m.y * v.y;
         ay += m.x * v.y + m.y * v.x;
       }
@@ -847,7 +891,7 @@ struct SmemCycle {
         ax += __shfl_down_sync(0xffffffffu, ax, q);
         ay += __shfl_down_sync(0xffffffffu, ay, q);
       }
-      if (lane == 0) xs[l][r] = mk<T2>(ax, ay);
+      if (lane == 0) lvl[l].x[r] = mk<T2>(ax, ay);
     }
     __syncthreads();
   }
@@ -855,7 +899,7 @@ struct SmemCycle {
     for (int s = 0; s < a.nu1; ++s) jacobi(l, s == 0);
     if (a.nu1 == 0) {
       int n = op[l].nx * op[l].nz;
-      for (int k = threadIdx.x; k < n; k += blockDim.x) xs[l][k] = mk<T2>(0, 0);
+      for (int k = threadIdx.x; k < n; k += blockDim.x) lvl[l].x[k] = mk<T2>(0, 0);
       __syncthreads();
     }
   }
@@ -894,30 +938,44 @@ struct SmemCycle {
 #define COARSE_THREADS 512
 template <typename T, bool CJ>
 __global__ void __launch_bounds__(COARSE_THREADS, 1)
-k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restrict__ st,
-                               const typename cplx<T>::t *__restrict__ dg, const typename cplx<T>::t *__restrict__ dgi,
-                               const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ x) {
+k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restrict__ st, const T *__restrict__ gam,
+               const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ x) {
   typedef typename cplx<T>::t T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2 *sm = reinterpret_cast<T2 *>(smem_raw);
   if (a.skip && a.skip[blockIdx.x]) return;
-  SmemCycle<T, CJ> c(a, st, dg, dgi);
+  SmemCycle<T, CJ> c(a);
   c.blk = blockIdx.x;
   c.nlev = a.inst_nlev[a.blks[a.ls][c.blk].inst];
+  // per level (layout of smem_level_bytes): x, b, t [n]; X [nx]; 1/Xh [nx+1];
+  // Z [nz]; 1/Zh [nz+1]; gamma [n rounded up to 4]
   size_t off = 0;
   for (int l = a.ls; l < c.nlev; ++l) {
-    c.op[l] = a.ops[a.blks[l][c.blk].op];
-    int n = c.op[l].nx * c.op[l].nz;
-    c.xs[l] = sm + off; off += n;
-    c.bs[l] = sm + off; off += n;
-    c.ts[l] = sm + off; off += n;
+    const OpDev o = a.ops[a.blks[l][c.blk].op];
+    c.op[l] = o;
+    SmemLevel<T> &L = c.lvl[l];
+    const int n = o.nx * o.nz;
+    L.nx = o.nx; L.nz = o.nz;
+    L.mass = cmaybe_conj(mk<T2>(o.mass_re, o.mass_im), CJ);
+    L.x = sm + off; off += n;
+    L.b = sm + off; off += n;
+    L.t = sm + off; off += n;
+    T2 *stc = sm + off;
+    const int nst = 2 * o.nx + 2 * o.nz + 2;
+    off += nst;
+    for (int k = threadIdx.x; k < nst; k += blockDim.x) stc[k] = st[o.st + k];
+    L.X = stc; L.iXh = stc + o.nx; L.Z = stc + 2 * o.nx + 1; L.iZh = L.Z + o.nz;
+    T *gs = reinterpret_cast<T *>(sm + off);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) gs[k] = gam[o.gam + k];
+    L.g = gs;
+    off += (n + 3) / 4 * 2;   // gamma: (n rounded up to 4) reals = half as many complex slots
   }
   const BlkDev bk = a.blks[a.ls][c.blk];
   int n = c.op[a.ls].nx * c.op[a.ls].nz;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) c.bs[a.ls][k] = b[bk.off + k];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) c.lvl[a.ls].b[k] = b[bk.off + k];
   __syncthreads();
   c.run(a.ls);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) x[bk.off + k] = c.xs[a.ls][k];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) x[bk.off + k] = c.lvl[a.ls].x[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -1202,9 +1260,18 @@ struct BiState {
   int done, it;
 };
 
+// Sum of partial[t][q] over t0 <= t < t1 by one warp: lane-strided sums, then
+// a fixed-order butterfly, so every lane gets the same (deterministic) value.
 __device__ __forceinline__ double2 sum_tiles(const double2 *partial, int t0, int t1, int q) {
   double2 s = make_double2(0, 0);
-  for (int t = t0; t < t1; ++t) { s.x += partial[(long long)t * 3 + q].x; s.y += partial[(long long)t * 3 + q].y; }
+  for (int t = t0 + (int)(threadIdx.x & 31); t < t1; t += 32) {
+    const double2 v = partial[(long long)t * 3 + q];
+    s.x += v.x; s.y += v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
   return s;
 }
 
@@ -1216,10 +1283,14 @@ __device__ __forceinline__ double2 sum_tiles(const double2 *partial, int t0, int
 //          ||r||^2 <= tol^2 ||b||^2 (tol > 0).
 // stage 5: stage 4, then (if not done) stage 1 of the next iteration with
 //          q1 = <rh, r>.
-__global__ void k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1, const double2 *partial,
-                               BiState *S, int stage, double tol, int *done_out) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n_blocks) return;
+// One warp per block (BICG_WARPS warps per CTA): the warp sums the block's
+// partials, every lane then holds the same state and lane 0 writes it.
+#define BICG_WARPS 4
+__global__ void __launch_bounds__(BICG_WARPS * 32)
+k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1, const double2 *partial,
+               BiState *S, int stage, double tol, int *done_out) {
+  const int b = blockIdx.x * BICG_WARPS + (threadIdx.x >> 5);
+  if (b >= n_blocks) return;                          // whole warps
   BiState s = S[b];
   int t0 = tile0[b], t1 = tile1[b];
   if (stage == 0) {
@@ -1267,8 +1338,10 @@ __global__ void k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1,
       }
     }
   }
-  S[b] = s;
-  done_out[b] = s.done;
+  if ((threadIdx.x & 31) == 0) {
+    S[b] = s;
+    done_out[b] = s.done;
+  }
 }
 
 // BiCGStab updates on a field (per-block scalars):
@@ -1332,6 +1405,7 @@ k_bicg_xr(LevelView<T> L, const BiState *S, typename cplx<T>::t *__restrict__ x,
     const T2 al = mk<T2>(st.alpha.x, st.alpha.y), om = mk<T2>(st.omega.x, st.omega.y);
     const long long base = bk.off + (long long)j * op.nx;
     int cnt = 0;
+#pragma unroll 2
     for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
       const long long k = base + i;
       x[k] = cadd(x[k], cadd(cmul(al, ph[k]), cmul(om, sh[k])));

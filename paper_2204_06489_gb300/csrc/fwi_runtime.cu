@@ -327,8 +327,8 @@ template <> const double *gam_ptr<double>(Ctx &c) { return c.gam64.p; }
 template <typename T>
 void Ctx::launch_coarse(const CoarseArgs &ca, size_t smem, const typename cplx<T>::t *b, typename cplx<T>::t *x,
                         int cj) {
-  if (cj) k_coarse_cycle<T, true><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), dg_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
-  else k_coarse_cycle<T, false><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), dg_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+  if (cj) k_coarse_cycle<T, true><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
+  else k_coarse_cycle<T, false><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
   KCHECK();
 }
 
@@ -498,14 +498,15 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
     for (int q = 0; q < l; ++q) { nx /= 2; nz /= 2; }
   };
   // shared-memory start level: the first level from which every instance's
-  // remaining levels (3 vectors each) fit in the per-CTA budget (c64);
+  // remaining levels (3 vectors and the operator data each) fit in the per-CTA
+  // budget (c64);
   // complex128 may need a coarser start.
   const size_t budget = 200 * 1024;
   auto smem_from = [&](int l0, size_t elem) {
     size_t mx = 0;
     for (auto &I : inst) {
       size_t s = 0;
-      for (int l = l0; l < I.nlev; ++l) { int nx, nz; dims(I, l, nx, nz); s += 3 * (size_t)nx * nz * elem; }
+      for (int l = l0; l < I.nlev; ++l) { int nx, nz; dims(I, l, nx, nz); s += smem_level_bytes(nx, nz, elem); }
       mx = std::max(mx, s);
     }
     return mx;
@@ -515,6 +516,9 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   for (int p = 0; p < 2; ++p) {
     size_t elem = p ? sizeof(double2) : sizeof(float2);
     int l0 = 1;
+#ifdef FWI_LS_MIN
+    l0 = std::max(l0, std::min(FWI_LS_MIN, minlev - 1));
+#endif
     while (l0 < minlev - 1 && smem_from(l0, elem) > budget) ++l0;
     if (minlev < 2) l0 = 0;  // single-level instances: the whole cycle is the coarse solve
     ls_p[p] = l0;
@@ -676,7 +680,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
       // block-major, then row band, then column, so that neighbouring strips
       // (which share halo rows and columns) run close together
       T.hs0[b] = (int)T.hstrips.size();
-      if (l <= MARCH_LEVEL_MAX)
+      if (l < ls)
         for (int r0 = 0; r0 < nz; r0 += MARCH_ROWS) {
           for (int c0 = 0; c0 < nx; c0 += MARCH_COLS)
             T.hstrips.push_back(StripDev{b, c0, r0, std::min(r0 + MARCH_ROWS, nz)});
@@ -805,7 +809,7 @@ void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const t
     else k_field_op_tile<T, false><<<L.n_tiles, TILE_THREADS, sm, st>>>(L, mode, wj, x, b, y);
   } else {
 #else
-  if (level <= MARCH_LEVEL_MAX) {
+  if (L.n_strips > 0) {
     const int grid = std::max(1, (L.n_strips + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
     if (cj) launch_march_cj<T, true>(grid, st, L, mode, wj, x, b, y);
     else launch_march_cj<T, false>(grid, st, L, mode, wj, x, b, y);
@@ -907,7 +911,7 @@ template <typename T>
 void Ctx::smooth(int nu, bool zero, int cj, T wj, const typename cplx<T>::t *bl, typename cplx<T>::t *&cur,
                  typename cplx<T>::t *&oth, int l) {
   int s = 0;
-  if (l <= MARCH_LEVEL_MAX) {
+  if (lv[l].n_strips2 > 0) {
     if (zero && nu >= 2) {
       jacobi2<T>(cj, wj, nullptr, bl, cur, l);
       s = 2;
@@ -1027,18 +1031,18 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   Work<T> &w = work<T>();
   LevelView<T> L = viewA<T>();
   const int nt = L.n_tiles;
-  const int sb = (B + 127) / 128;
+  const int sb = (B + BICG_WARPS - 1) / BICG_WARPS;
   auto upd = [&](int opk, T2 *y, const T2 *a, const T2 *c, const T2 *d, T2 *y2, const T2 *e) {
     k_bicg_update<T><<<nt, TILE_THREADS, 0, st>>>(L, opk, w.bst.p, y, a, c, d, y2, e);
     KCHECK();
   };
   auto scal = [&](int stage) {
-    k_bicg_scalars<<<sb, 128, 0, st>>>(B, lv[0].t0.p, lv[0].t1.p, partial.p, w.bst.p, stage, tol, w.done.p);
+    k_bicg_scalars<<<sb, BICG_WARPS * 32, 0, st>>>(B, lv[0].t0.p, lv[0].t1.p, partial.p, w.bst.p, stage, tol, w.done.p);
     KCHECK();
   };
   // stages whose dots come from the strip kernels (operator apply fused with dots)
   auto scal_s = [&](int stage) {
-    k_bicg_scalars<<<sb, 128, 0, st>>>(B, lv[0].s0.p, lv[0].s1.p, partial_s.p, w.bst.p, stage, tol, w.done.p);
+    k_bicg_scalars<<<sb, BICG_WARPS * 32, 0, st>>>(B, lv[0].s0.p, lv[0].s1.p, partial_s.p, w.bst.p, stage, tol, w.done.p);
     KCHECK();
   };
   // x = 0, r = b, rh = b, p = v = 0
