@@ -17,7 +17,9 @@
 #define TILE_THREADS (TILE_ROWS * 32)
 #define MAX_LEVELS 12
 #define MARCH_COLS 30
-#define MARCH2_COLS 28
+#define MARCH2_COLS 60     // output columns per strip of the two-sweep smoother (two per lane)
+#define RM_COLS 14          // coarse columns per strip of the residual-restriction kernel
+#define RM_ROWS 8           // coarse rows per strip
 #ifndef MARCH_ROWS
 #define MARCH_ROWS 16
 #endif

@@ -490,16 +490,34 @@ k_field_op_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
 //   ZERO:  x1 = w b / cc                     (first sweep from x = 0)
 //   else:  x1 = x + w (b - Op x) / cc
 //   y = x1 + w (b - Op x1) / cc
-// A warp walks a strip as in k_field_op_march, with two halo columns on each
-// side: lane l holds column col0 - 2 + l, x1 is formed on lanes 1 .. 30 and
-// y on lanes 2 .. 29 (MARCH2_COLS columns).  Going down row k, the warp forms
-// x1 on row k from x on rows k-1 .. k+1 and y on row k-1 from x1 on rows
-// k-2 .. k, so x1 lives only in registers (one halo row of x1 above and
-// below the strip is formed twice).  Traffic per node: x, b in, y out (b in,
-// y out for ZERO) instead of five (or six) streams for two separate sweeps.
-// x1 is zero outside the grid (Dirichlet ghosts), like x.
+// A warp walks a strip of MARCH2_COLS columns with two halo columns on each
+// side; lane l holds the two columns col0 - 2 + l and col0 + 30 + l, so the
+// per-row work that does not depend on the column (row constants, loop,
+// address and bounds arithmetic) is shared by two nodes.  x1 is formed on
+// columns col0 - 1 .. col0 + 60 and y on col0 .. col0 + 59.  Going down row
+// k, the warp forms x1 on row k from x on rows k-1 .. k+1 and y on row k-1
+// from x1 on rows k-2 .. k, so x1 lives only in registers (one halo row of
+// x1 above and below the strip is formed twice).  Traffic per node: x, b in,
+// y out (b in, y out for ZERO) instead of five (or six) streams for two
+// separate sweeps.  x1 is zero outside the grid (Dirichlet ghosts), like x.
+template <typename T2> __device__ __forceinline__ T2 shfl_from(T2 v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  return v;
+}
+// east / west neighbours of the column pair (v[0] at col0 - 2 + l, v[1] at
+// col0 + 30 + l) held across the warp
+template <typename T2> __device__ __forceinline__ void pair_neighbours(const T2 *v, int lane, T2 *e, T2 *w) {
+  const T2 a = shfl_from(v[0], (lane + 1) & 31), c = shfl_from(v[1], (lane + 1) & 31);
+  const T2 p = shfl_from(v[0], (lane + 31) & 31), q = shfl_from(v[1], (lane + 31) & 31);
+  e[0] = lane == 31 ? c : a;
+  e[1] = c;
+  w[0] = p;
+  w[1] = lane == 0 ? p : q;
+}
+
 template <typename T, bool CJ, bool ZERO>
-__global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 2 : 1)
 k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
                 const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
   typedef typename cplx<T>::t T2;
@@ -511,15 +529,163 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
   const OpDev op = L.ops[bk.op];
   const int nx = op.nx, nz = op.nz;
   const int lane = threadIdx.x & 31;
-  const int i = s.col0 - 2 + lane;
-  const bool in_grid = i >= 0 && i < nx;
-  const bool mid = lane >= 1 && lane <= 30 && in_grid;
-  const bool own = lane >= 2 && lane <= MARCH2_COLS + 1 && in_grid;
+  const int ii[2] = {s.col0 - 2 + lane, s.col0 + 30 + lane};
+  bool in[2], mid[2], own[2];
+  in[0] = ii[0] >= 0 && ii[0] < nx;
+  in[1] = ii[1] < nx;
+  mid[0] = lane >= 1 && in[0];
+  mid[1] = lane <= 30 && in[1];
+  own[0] = lane >= 2 && in[0];
+  own[1] = lane <= 29 && in[1];
   if (L.work && s.col0 == 0 && lane == 0)
     atomicAdd(L.work, (unsigned long long)(s.row1 - s.row0) * nx);
   const unsigned long long pol = keep_policy();
   const T2 zero = mk<T2>(0, 0);
   const T2 *X = L.st + op.st;
+  const T2 *iXh = X + nx;
+  const T2 *Zr = iXh + nx + 1;
+  const T2 *iZh = Zr + nz;
+  T2 Xi[2], iw[2], ie[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    Xi[c] = iw[c] = ie[c] = zero;
+    if (mid[c]) {
+      Xi[c] = cmaybe_conj(X[ii[c]], CJ);
+      iw[c] = cmaybe_conj(iXh[ii[c]], CJ);
+      ie[c] = cmaybe_conj(iXh[ii[c] + 1], CJ);
+    }
+  }
+  // column pointers (row 0); column 1 is 32 elements to the right of column 0
+  const int ic = in[0] ? ii[0] : (in[1] ? ii[1] - 32 : 0);
+  const T2 *xb = ZERO ? nullptr : x + bk.off + ic;
+  const T2 *bb = b + bk.off + ic;
+  T2 *yb = y + bk.off + ic;
+  const T2 *db = L.dg + op.dg + ic;
+  const T2 *dib = L.dgi + op.dg + ic;
+  const int kb = s.row0 - 1, ke = s.row1;          // x1 rows formed: kb .. ke
+  {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (!ZERO && in[c])
+        for (int r = max(kb - 1, 0); r < min(ke + 2, nz); ++r) prefetch_l2(xb + 32 * c + r * nx);
+      if (mid[c])
+        for (int r = max(kb, 0); r < min(ke + 1, nz); ++r) prefetch_l2(bb + 32 * c + r * nx);
+    }
+  }
+  auto inside = [&](int k) { return k >= 0 && k < nz; };
+  // one damped-Jacobi update at a node of column c
+  auto jac = [&](int c, T2 u, T2 uw, T2 ue, T2 un, T2 us, T2 bv, T2 d, T2 dinv, T2 Zj, T2 iZn, T2 iZs) -> T2 {
+    const T2 hx = cadd(cmul(ie[c], ue), cmul(iw[c], uw));
+    const T2 hz = cadd(cmul(iZs, us), cmul(iZn, un));
+    const T2 au = csub(csub(cmul(d, u), cmul(Zj, hx)), cmul(Xi[c], hz));
+    return cadd(u, cscale(cmul(csub(bv, au), dinv), w));
+  };
+  // pipeline state at the top of iteration k (per column c)
+  T2 xm[2], x0[2], xp[2], bm[2], dm[2], dim[2], b0[2], d0[2], di0[2], ym2[2], ym1[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const bool okx = !ZERO && in[c];
+    xm[c] = (okx && inside(kb - 1)) ? xb[32 * c + (kb - 1) * nx] : zero;
+    x0[c] = (okx && inside(kb)) ? xb[32 * c + kb * nx] : zero;
+    xp[c] = (okx && inside(kb + 1)) ? xb[32 * c + (kb + 1) * nx] : zero;
+    const bool okr = mid[c] && inside(kb);
+    b0[c] = okr ? bb[32 * c + kb * nx] : zero;
+    d0[c] = okr ? cmaybe_conj(ld_keep_p(db + 32 * c + kb * nx, pol), CJ) : zero;
+    di0[c] = okr ? cmaybe_conj(ld_keep_p(dib + 32 * c + kb * nx, pol), CJ) : zero;
+    bm[c] = dm[c] = dim[c] = ym2[c] = ym1[c] = zero;
+  }
+  T2 Zm = zero, Z0 = inside(kb) ? cmaybe_conj(Zr[kb], CJ) : zero;
+  T2 iZm = zero;
+  T2 iZ0 = (kb >= 0 && kb <= nz) ? cmaybe_conj(iZh[kb], CJ) : zero;         // 1/Z at half row k - 1/2
+  T2 iZ1 = (kb + 1 >= 0 && kb + 1 <= nz) ? cmaybe_conj(iZh[kb + 1], CJ) : zero;   // k + 1/2
+  for (int k = kb; k <= ke; ++k) {
+    // loads for row k + 1
+    const bool more = k < ke;
+    const bool rn = more && inside(k + 1);
+    const bool xn_ok = more && k + 2 < nz;
+    const int o1 = (k + 1) * nx;
+    T2 xn[2], bn[2], dn[2], din[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      xn[c] = (!ZERO && xn_ok && in[c]) ? xb[32 * c + o1 + nx] : zero;
+      const bool okr = rn && mid[c];
+      bn[c] = okr ? bb[32 * c + o1] : zero;
+      dn[c] = okr ? cmaybe_conj(ld_keep_p(db + 32 * c + o1, pol), CJ) : zero;   // (the second sweep needs it)
+      din[c] = okr ? cmaybe_conj(ld_keep_p(dib + 32 * c + o1, pol), CJ) : zero;
+    }
+    const T2 Zn = rn ? cmaybe_conj(Zr[k + 1], CJ) : zero;
+    const T2 iZ2 = (more && k + 2 <= nz) ? cmaybe_conj(iZh[k + 2], CJ) : zero;
+    // x1 on row k
+    T2 y1[2];
+    const bool rk = inside(k);
+    if (ZERO) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) y1[c] = (mid[c] && rk) ? cscale(cmul(b0[c], di0[c]), w) : zero;
+    } else {
+      T2 xe[2], xw[2];
+      pair_neighbours(x0, lane, xe, xw);
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+        y1[c] = (mid[c] && rk) ? jac(c, x0[c], xw[c], xe[c], xm[c], xp[c], b0[c], d0[c], di0[c], Z0, iZ0, iZ1)
+                               : zero;
+    }
+    // y on row k - 1
+    {
+      T2 ye[2], yw[2];
+      pair_neighbours(ym1, lane, ye, yw);
+      if (k - 1 >= s.row0) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          if (own[c])
+            yb[32 * c + (k - 1) * nx] = jac(c, ym1[c], yw[c], ye[c], ym2[c], y1[c], bm[c], dm[c], dim[c], Zm, iZm, iZ0);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      xm[c] = x0[c]; x0[c] = xp[c]; xp[c] = xn[c];
+      bm[c] = b0[c]; dm[c] = d0[c]; dim[c] = di0[c];
+      b0[c] = bn[c]; d0[c] = dn[c]; di0[c] = din[c];
+      ym2[c] = ym1[c]; ym1[c] = y1[c];
+    }
+    Zm = Z0; Z0 = Zn;
+    iZm = iZ0; iZ0 = iZ1; iZ1 = iZ2;
+  }
+}
+
+// Residual + restriction by column strips (R = P^T, 4x full weighting):
+//   bc[J][I] = sum_{a,b in -1..1} w_a w_b (bf - Op xf)[2J+1+b][2I+1+a],  w = (1/2, 1, 1/2).
+// A warp owns coarse columns C0 .. C0 + RM_COLS - 1 and coarse rows J0 .. J1 - 1
+// of one block (a StripDev in coarse coordinates).  Lane l holds fine column
+// 2 C0 - 1 + l; the warp walks the fine rows 2 J0 .. 2 J1 keeping three rows of
+// x in registers, forms the residual on lanes 1 .. 30, combines it across
+// columns with shuffles (lane 2m + 2 is the fine column 2I + 1 of coarse column
+// I = C0 + m) and across rows in two running sums, and stores a coarse row
+// every second fine row.  Fine nodes outside the grid have zero residual.
+template <typename T, bool CJ>
+__global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 4 : 2)
+k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__restrict__ xf,
+                       const typename cplx<T>::t *__restrict__ bf, typename cplx<T>::t *__restrict__ bc,
+                       const StripDev *__restrict__ rstrips, int n_rstrips) {
+  typedef typename cplx<T>::t T2;
+  const int gw = blockIdx.x * (MARCH_THREADS / 32) + (threadIdx.x >> 5);
+  if (gw >= n_rstrips) return;                        // whole warps leave together
+  const StripDev s = rstrips[gw];
+  if (Lf.skip && Lf.skip[s.blk]) return;
+  const BlkDev bkf = Lf.blks[s.blk];
+  const OpDev op = Lf.ops[bkf.op];
+  const BlkDev bkc = Lc.blks[s.blk];
+  const OpDev opc = Lc.ops[bkc.op];
+  const int nx = op.nx, nz = op.nz;
+  const int lane = threadIdx.x & 31;
+  const int i = 2 * s.col0 - 1 + lane;
+  const bool in_grid = i >= 0 && i < nx;
+  const bool mid = lane >= 1 && lane <= 30 && in_grid;
+  const int m = (lane - 2) >> 1;                      // coarse column of an even lane 2 .. 2 RM_COLS
+  const int I = s.col0 + m;
+  const bool cown = lane >= 2 && !(lane & 1) && m < RM_COLS && I < opc.nx;
+  const unsigned long long pol = keep_policy();
+  const T2 zero = mk<T2>(0, 0);
+  const T2 *X = Lf.st + op.st;
   const T2 *iXh = X + nx;
   const T2 *Zr = iXh + nx + 1;
   const T2 *iZh = Zr + nz;
@@ -530,72 +696,51 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
     ie = cmaybe_conj(iXh[i + 1], CJ);
   }
   const int ic = in_grid ? i : 0;
-  const long long ef0 = bk.off + ic;     // field element of (row 0, column i)
-  const long long eo0 = op.dg + ic;      // operator-array element of (row 0, column i)
-  const bool ldx_ok = !ZERO && in_grid;
-  const int kb = s.row0 - 1, ke = s.row1;          // x1 rows formed: kb .. ke
+  const long long ef0 = bkf.off + ic;
+  const long long eo0 = op.dg + ic;
+  const int jb = 2 * s.row0, je = 2 * s.row1;       // fine rows with residual: jb .. je
   {
-    const int r_lo = max(kb - 1, 0), r_hi = min(ke + 2, nz);
-    if (ldx_ok)
-      for (int r = r_lo; r < r_hi; ++r) prefetch_l2(x + ef0 + (long long)r * nx);
+    if (in_grid)
+      for (int r = max(jb - 1, 0); r < min(je + 2, nz); ++r) prefetch_l2(xf + ef0 + (long long)r * nx);
     if (mid)
-      for (int r = max(kb, 0); r < min(ke + 1, nz); ++r) prefetch_l2(b + ef0 + (long long)r * nx);
+      for (int r = jb; r < min(je + 1, nz); ++r) prefetch_l2(bf + ef0 + (long long)r * nx);
   }
-  // row data of row k (zero outside the grid)
-  auto ldxr = [&](int k) -> T2 { return (ldx_ok && k >= 0 && k < nz) ? x[ef0 + (long long)k * nx] : zero; };
-  auto ldbr = [&](int k) -> T2 { return (mid && k >= 0 && k < nz) ? b[ef0 + (long long)k * nx] : zero; };
-  auto lddr = [&](int k) -> T2 {
-    return (mid && k >= 0 && k < nz) ? cmaybe_conj(ld_keep_p(L.dg + eo0 + (long long)k * nx, pol), CJ) : zero;
-  };
-  auto lddir = [&](int k) -> T2 {
-    return (mid && k >= 0 && k < nz) ? cmaybe_conj(ld_keep_p(L.dgi + eo0 + (long long)k * nx, pol), CJ) : zero;
-  };
-  auto ldZ = [&](int k) -> T2 { return (k >= 0 && k < nz) ? cmaybe_conj(Zr[k], CJ) : zero; };
-  auto ldiZ = [&](int k) -> T2 { return (k >= 0 && k <= nz) ? cmaybe_conj(iZh[k], CJ) : zero; };
-  // one damped-Jacobi update at a node: u + w (bb - (d uc - Zj (ie ue + iw uw) - Xi (iZs us + iZn un))) dinv
-  auto jac = [&](T2 u, T2 uw, T2 ue, T2 un, T2 us, T2 bb, T2 d, T2 dinv, T2 Zj, T2 iZn, T2 iZs) -> T2 {
-    const T2 hx = cadd(cmul(ie, ue), cmul(iw, uw));
-    const T2 hz = cadd(cmul(iZs, us), cmul(iZn, un));
-    const T2 au = csub(csub(cmul(d, u), cmul(Zj, hx)), cmul(Xi, hz));
-    return cadd(u, cscale(cmul(csub(bb, au), dinv), w));
-  };
-
-  // pipeline state at the top of iteration k
-  T2 xm = ldxr(kb - 1), x0 = ldxr(kb), xp = ldxr(kb + 1);
-  T2 bm = zero, dm = zero, dim = zero;                     // row k-1
-  T2 b0 = ldbr(kb), d0 = ZERO ? zero : lddr(kb), di0 = lddir(kb);   // row k
-  T2 Zm = zero, Z0 = ldZ(kb);
-  T2 iZm = zero, iZ0 = ldiZ(kb), iZ1 = ldiZ(kb + 1);       // 1/Z at half rows k-1/2 (iZ0), k+1/2 (iZ1)
-  T2 ym2 = zero, ym1 = zero;                               // x1 on rows k-2, k-1
-  for (int k = kb; k <= ke; ++k) {
-    // loads for row k + 1
-    const bool more = k < ke;
-    const T2 xn = more ? ldxr(k + 2) : zero;
-    const T2 bn = more ? ldbr(k + 1) : zero;
-    const T2 dn = more ? lddr(k + 1) : zero;
-    const T2 din = more ? lddir(k + 1) : zero;
-    const T2 Zn = more ? ldZ(k + 1) : zero;
-    const T2 iZ2 = more ? ldiZ(k + 2) : zero;
-    // x1 on row k (lanes 1 .. 30)
-    T2 y1 = zero;
-    if (ZERO) {
-      if (mid && k >= 0 && k < nz) y1 = cscale(cmul(b0, di0), w);
-    } else {
+  auto ldx = [&](int k) -> T2 { return (in_grid && k >= 0 && k < nz) ? xf[ef0 + (long long)k * nx] : zero; };
+  T2 xm = ldx(jb - 1), x0 = ldx(jb), xp = ldx(jb + 1);
+  T2 acc0 = zero;                // running sum of the coarse row being formed
+  T2 *cout = bc + bkc.off + (cown ? I : 0);
+  for (int j = jb; j <= je; ++j) {
+    const T2 xn = (j < je) ? ldx(j + 2) : zero;
+    const bool rk = mid && j < nz;
+    T2 r = zero;
+    {
       const T2 xe = shfl_down1(x0), xw = shfl_up1(x0);
-      if (mid && k >= 0 && k < nz) y1 = jac(x0, xw, xe, xm, xp, b0, d0, di0, Z0, iZ0, iZ1);
+      if (rk) {
+        const long long k = (long long)j * nx;
+        const T2 Zj = cmaybe_conj(Zr[j], CJ), iZn = cmaybe_conj(iZh[j], CJ), iZs = cmaybe_conj(iZh[j + 1], CJ);
+        const T2 d = cmaybe_conj(ld_keep_p(Lf.dg + eo0 + k, pol), CJ);
+        const T2 hx = cadd(cmul(ie, xe), cmul(iw, xw));
+        const T2 hz = cadd(cmul(iZs, xp), cmul(iZn, xm));
+        const T2 ax = csub(csub(cmul(d, x0), cmul(Zj, hx)), cmul(Xi, hz));
+        r = csub(bf[ef0 + k], ax);
+      }
     }
-    // y on row k - 1 (lanes 2 .. 29)
-    const T2 ye = shfl_down1(ym1), yw = shfl_up1(ym1);
-    if (k - 1 >= s.row0 && own) {
-      // row k - 1: 1/Z at half rows k-3/2 (iZm) and k-1/2 (iZ0)
-      y[ef0 + (long long)(k - 1) * nx] = jac(ym1, yw, ye, ym2, y1, bm, dm, dim, Zm, iZm, iZ0);
+    // horizontal weights at the centre lanes: (r[l-1] + r[l+1]) / 2 + r[l]
+    const T2 re = shfl_down1(r), rw = shfl_up1(r);
+    const T2 h = cadd(r, cscale(cadd(re, rw), (T)0.5));
+    // fine row j = 2J: first (half) term of coarse row J, last (half) term of J - 1;
+    // j = 2J + 1: middle term of coarse row J
+    if (!(j & 1)) {
+      const int J = (j >> 1) - 1;                     // coarse row completed by this fine row
+      if (j > jb) {
+        acc0 = cadd(acc0, cscale(h, (T)0.5));
+        if (cown && J < opc.nz) cout[(long long)J * opc.nx] = acc0;
+      }
+      acc0 = cscale(h, (T)0.5);
+    } else {
+      acc0 = cadd(acc0, h);
     }
     xm = x0; x0 = xp; xp = xn;
-    bm = b0; dm = d0; dim = di0;
-    b0 = bn; d0 = dn; di0 = din;
-    Zm = Z0; Z0 = Zn;
-    iZm = iZ0; iZ0 = iZ1; iZ1 = iZ2;
-    ym2 = ym1; ym1 = y1;
   }
 }
 

@@ -114,16 +114,17 @@ struct Instance {
 struct LevelTables {
   std::vector<BlkDev> hM, hA;
   std::vector<TileDev> htiles;
-  std::vector<StripDev> hstrips, hstrips2;
+  std::vector<StripDev> hstrips, hstrips2, hrstrips;
   std::vector<int> ht0, ht1, hs0, hs1;
   DBuf<BlkDev> blksM, blksA;
   DBuf<TileDev> tiles;
-  DBuf<StripDev> strips, strips2;
+  DBuf<StripDev> strips, strips2, rstrips;   // rstrips: coarse-column strips of the restriction to l + 1
   DBuf<int> t0, t1, s0, s1;   // per block: its row tiles [t0, t1), its column strips [s0, s1)
   long long field = 0;  // complex elements of one field on this level
   int n_tiles = 0;
   int n_strips = 0;
   int n_strips2 = 0;
+  int n_rstrips = 0;
 };
 
 template <typename T> struct Work {
@@ -278,6 +279,8 @@ struct Ctx {
   template <typename T> bool timer_begin(int level, LevelView<T> &L);
   template <typename T> void smooth(int nu, bool zero, int cj, T wj, const typename cplx<T>::t *bl,
                                     typename cplx<T>::t *&cur, typename cplx<T>::t *&oth, int l);
+  template <typename T> void resid_restrict(int cj, int l, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
+                                            typename cplx<T>::t *bc);
   void timer_end(int streams, size_t elem_bytes);
   template <typename T> void apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *y,
                                         const typename cplx<T>::t *a, int nd);
@@ -658,7 +661,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
     LevelTables &T = lv[l];
     T.hM.assign(B, BlkDev{0, 0, 0});
     T.hA.assign(B, BlkDev{0, 0, 0});
-    T.htiles.clear(); T.hstrips.clear(); T.hstrips2.clear(); T.ht0.assign(B, 0); T.ht1.assign(B, 0);
+    T.htiles.clear(); T.hstrips.clear(); T.hstrips2.clear(); T.hrstrips.clear(); T.ht0.assign(B, 0); T.ht1.assign(B, 0);
     T.hs0.assign(B, 0); T.hs1.assign(B, 0);
     long long off = 0;
     for (int b = 0; b < B; ++b) {
@@ -688,6 +691,12 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
             T.hstrips2.push_back(StripDev{b, c0, r0, std::min(r0 + MARCH_ROWS, nz)});
         }
       T.hs1[b] = (int)T.hstrips.size();
+      if (l < ls) {
+        const int ncx = nx / 2, ncz = nz / 2;   // level l + 1 (dims halve per level)
+        for (int J0 = 0; J0 < ncz; J0 += RM_ROWS)
+          for (int C0 = 0; C0 < ncx; C0 += RM_COLS)
+            T.hrstrips.push_back(StripDev{b, C0, J0, std::min(J0 + RM_ROWS, ncz)});
+      }
       off += (long long)nx * nz;
     }
     T.field = off;
@@ -696,6 +705,8 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
     T.strips.upload(T.hstrips, st);
     T.n_strips2 = (int)T.hstrips2.size();
     T.strips2.upload(T.hstrips2, st);
+    T.n_rstrips = (int)T.hrstrips.size();
+    T.rstrips.upload(T.hrstrips, st);
     T.blksM.upload(T.hM, st);
     T.blksA.upload(T.hA, st);
     T.tiles.upload(T.htiles, st);
@@ -890,7 +901,25 @@ void Ctx::jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cpl
     else k_jacobi2_march<T, false, false><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
   }
   KCHECK();
+  // algorithmic bytes per node: b, y (and x)
   if (timed) timer_end(x == nullptr ? 2 : 3, sizeof(typename cplx<T>::t));
+}
+
+// b_{l+1} = P^T (b_l - M_l x_l) on every block.
+template <typename T>
+void Ctx::resid_restrict(int cj, int l, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
+                         typename cplx<T>::t *bc) {
+  LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
+  const int n = lv[l].n_rstrips;
+  if (n > 0) {
+    const int grid = (n + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32);
+    if (cj) k_resid_restrict_march<T, true><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
+    else k_resid_restrict_march<T, false><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
+  } else {
+    if (cj) k_resid_restrict<T, true><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, x, b, bc);
+    else k_resid_restrict<T, false><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, x, b, bc);
+  }
+  KCHECK();
 }
 
 template <typename T>
@@ -962,9 +991,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
     int reps = (l > 0 && l <= o.mg_wdepth) ? o.mg_cycle : 1;
     for (int r = 0; r < reps; ++r) {
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
-      if (cj) k_resid_restrict<T, true><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cur, bl, w.lb[l + 1].p);
-      else k_resid_restrict<T, false><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cur, bl, w.lb[l + 1].p);
-      KCHECK();
+      resid_restrict<T>(cj, l, cur, bl, w.lb[l + 1].p);
       T2 *xc = cyc(l + 1, w.lb[l + 1].p, w.lx[l + 1].p, w.lt[l + 1].p);
       k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
       KCHECK();
@@ -1008,9 +1035,7 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
     int reps = (l > 0 && l <= o.mg_wdepth) ? o.mg_cycle : 1;
     for (int r = 0; r < reps; ++r) {
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
-      if (cj) k_resid_restrict<T, true><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cur, bl, lb[l + 1]);
-      else k_resid_restrict<T, false><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, cur, bl, lb[l + 1]);
-      KCHECK();
+      resid_restrict<T>(cj, l, cur, bl, lb[l + 1]);
       T2 *xc = cyc(l + 1, lb[l + 1], lx[l + 1], lt[l + 1]);
       k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
       KCHECK();
