@@ -252,15 +252,16 @@ int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info);
  * has no counterpart. */
 unsigned long long fwi_kernel_launches(void);
 
-/* Live timing of the complex64 level-0 stencil / smoother kernel (the
- * 5-point operator of Sec. 2 applied to every block): while enabled, every
- * launch of it that is not inside a CUDA graph is bracketed by CUDA events on
- * the context's stream, and the kernel counts the grid nodes it processed
- * (blocks whose inner solve has finished are skipped).  Writes (nullable) the
- * accumulated time (ms), algorithmic bytes (each complex element of the
- * operands and result of every processed node counted once) and launch count
- * since the last reset; then enable = 1 resets and turns timing on, 0 resets
- * and turns it off, -1 only reads.  Diagnostics; the paper has no counterpart. */
+/* Live timing of the complex64 level-0 smoother kernel (two damped-Jacobi
+ * sweeps of the shifted 5-point operator of Sec. 2 in one pass, every block):
+ * while enabled, every launch of it that is not inside a CUDA graph is
+ * bracketed by CUDA events on the context's stream, and the kernel counts the
+ * grid nodes it processed (blocks whose inner solve has finished are
+ * skipped).  Writes (nullable) the accumulated time (ms), algorithmic bytes
+ * (per processed node: b and the result, plus x unless the sweeps start from
+ * zero, one complex element each) and launch count since the last reset;
+ * then enable = 1 resets and turns timing on, 0 resets and turns it off, -1
+ * only reads.  Diagnostics; the paper has no counterpart. */
 int fwi_stencil_timer(fwi_ctx *ctx, int enable, double *ms, double *bytes, long long *launches);
 
 /* Message of the last failure on this context ("" if none). NULL ctx: the

@@ -182,31 +182,7 @@ k_field_op(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__restrict_
   }
 }
 
-// ---------------------------------------------------------------------------
-// Shared-memory staged variant of k_field_op for the big levels: a CTA stages
-// its 8 rows plus one halo row above and below, in chunks of FT_CW columns
-// plus a one-column halo, with asynchronous 8/16-byte copies (cp.async, all
-// loads in flight at once), then applies the stencil from shared memory.
-// Nodes outside the grid are staged as zeros (Dirichlet ghosts).
-// ---------------------------------------------------------------------------
-#define FT_CW 128
-#define FT_W (FT_CW + 2)
-#define FT_R (TILE_ROWS + 2)
-static_assert(TILE_THREADS == 2 * FT_CW, "stretch staging assumes two threads per chunk column");
-
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
-}
-template <typename T2> __device__ __forceinline__ void cp_async_elem(T2 *smem, const T2 *gmem);
-template <> __device__ __forceinline__ void cp_async_elem<float2>(float2 *smem, const float2 *gmem) { cp_async8(smem, gmem); }
-template <> __device__ __forceinline__ void cp_async_elem<double2>(double2 *smem, const double2 *gmem) { cp_async16(smem, gmem); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
+// L2-evict-last loads with a policy created once per thread.
 __device__ __forceinline__ float2 ld_keep_p(const float2 *p, unsigned long long pol) {
   float2 v;
   asm("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
@@ -216,125 +192,6 @@ __device__ __forceinline__ double2 ld_keep_p(const double2 *p, unsigned long lon
   double2 v;
   asm("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
   return v;
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-// Two shared-memory stages: the copies of chunk k+1 are in flight while chunk
-// k is computed.
-template <typename T> struct FtStage {
-  typedef typename cplx<T>::t T2;
-  T2 xs[FT_R][FT_W];
-  T2 bs[TILE_ROWS][FT_CW];
-  T2 sX[FT_CW];
-  T2 siX[FT_CW + 1];
-};
-
-template <typename T, bool CJ>
-__global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 5 : 2)
-k_field_op_tile(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__restrict__ x,
-                const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
-  typedef typename cplx<T>::t T2;
-  extern __shared__ __align__(16) unsigned char ft_raw[];
-  FtStage<T> *stg = reinterpret_cast<FtStage<T> *>(ft_raw);
-  const TileDev t = L.tiles[blockIdx.x];
-  if (L.skip && L.skip[t.blk]) return;
-  const BlkDev bk = L.blks[t.blk];
-  const OpDev op = L.ops[bk.op];
-  const int nx = op.nx, nz = op.nz;
-  const int j0 = t.row0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = j0 + warp;
-  const bool row_ok = j < nz;
-  const unsigned long long pol = keep_policy();
-  if (L.work && threadIdx.x == 0) atomicAdd(L.work, (unsigned long long)min(TILE_ROWS, nz - j0) * nx);
-  const T2 *X = L.st + op.st;
-  const T2 *iXh = X + nx;
-  const T2 *Zr = iXh + nx + 1;
-  const T2 *iZh = Zr + nz;
-  T2 Zj = mk<T2>(0, 0), iZn = Zj, iZs = Zj;
-  if (row_ok) {
-    Zj = cmaybe_conj(Zr[j], CJ);
-    iZn = cmaybe_conj(iZh[j], CJ);
-    iZs = cmaybe_conj(iZh[j + 1], CJ);
-  }
-  const T2 *blk_x = x ? x + bk.off : nullptr;
-  const T2 *brow = b ? b + bk.off + (long long)j * nx : nullptr;
-  T2 *yrow = y + bk.off + (long long)j * nx;
-  const T2 *dgr = L.dg + op.dg + (long long)j * nx;
-  const T2 *dgir = L.dgi + op.dg + (long long)j * nx;
-
-  auto stage = [&](FtStage<T> &S, int c0) {
-    if (mode != FM_JACOBI0) {
-      // x rows j0-1 .. j0+8, columns c0-1 .. c0+FT_CW: warp per row, lane per column
-      for (int r = warp; r < FT_R; r += TILE_ROWS) {
-        const int jj = j0 - 1 + r;
-        const bool rok = jj >= 0 && jj < nz;
-        const T2 *src = blk_x + (long long)(rok ? jj : 0) * nx + (c0 - 1);
-        for (int c = lane; c < FT_W; c += 32) {
-          const int ii = c0 - 1 + c;
-          if (rok && ii >= 0 && ii < nx) cp_async_elem(&S.xs[r][c], src + c);
-          else S.xs[r][c] = mk<T2>(0, 0);
-        }
-      }
-      // per-column stretch factors of the chunk (threads 0..127: X; 128..255:
-      // 1/X at half nodes 0..127; thread 0 also half node 128; iXh has nx + 1 entries)
-      if (threadIdx.x < FT_CW) {
-        const int ii = c0 + threadIdx.x;
-        if (ii < nx) cp_async_elem(&S.sX[threadIdx.x], X + ii);
-        if (threadIdx.x == 0 && c0 + FT_CW <= nx) cp_async_elem(&S.siX[FT_CW], iXh + c0 + FT_CW);
-      } else {
-        const int c = threadIdx.x - FT_CW;
-        if (c0 + c <= nx) cp_async_elem(&S.siX[c], iXh + c0 + c);
-      }
-    }
-    if (mode != FM_APPLY && row_ok) {
-      for (int c = lane; c < FT_CW; c += 32)
-        if (c0 + c < nx) cp_async_elem(&S.bs[warp][c], brow + c0 + c);
-    }
-    cp_async_commit();
-  };
-
-  const int nchunk = (nx + FT_CW - 1) / FT_CW;
-  stage(stg[0], 0);
-  for (int k = 0; k < nchunk; ++k) {
-    const int c0 = k * FT_CW;
-    if (k + 1 < nchunk) {
-      stage(stg[(k + 1) & 1], c0 + FT_CW);
-      cp_async_wait_prev();          // chunk k has landed; chunk k+1 may still be in flight
-    } else {
-      cp_async_wait_all();
-    }
-    __syncthreads();
-    FtStage<T> &S = stg[k & 1];
-    if (row_ok) {
-#pragma unroll
-      for (int q = 0; q < FT_CW / 32; ++q) {
-        const int c = lane + 32 * q;
-        const int i = c0 + c;
-        if (i < nx) {
-          T2 out;
-          if (mode == FM_JACOBI0) {
-            out = cscale(cmul(S.bs[warp][c], cmaybe_conj(ld_keep_p(dgir + i, pol), CJ)), w);
-          } else {
-            const T2 Xi = cmaybe_conj(S.sX[c], CJ);
-            const T2 iw = cmaybe_conj(S.siX[c], CJ);
-            const T2 ie = cmaybe_conj(S.siX[c + 1], CJ);
-            const T2 *xc = &S.xs[warp + 1][c + 1];
-            const T2 hx = cadd(cmul(ie, xc[1]), cmul(iw, xc[-1]));
-            const T2 hz = cadd(cmul(iZs, xc[FT_W]), cmul(iZn, xc[-FT_W]));
-            const T2 ax = csub(csub(cmul(cmaybe_conj(ld_keep_p(dgr + i, pol), CJ), xc[0]), cmul(Zj, hx)), cmul(Xi, hz));
-            if (mode == FM_APPLY) out = ax;
-            else if (mode == FM_RESID) out = csub(S.bs[warp][c], ax);
-            else out = cadd(xc[0], cscale(cmul(csub(S.bs[warp][c], ax), cmaybe_conj(ld_keep_p(dgir + i, pol), CJ)), w));
-          }
-          yrow[i] = out;
-        }
-      }
-    }
-    __syncthreads();                 // stage k & 1 is refilled two chunks later
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1492,13 +1349,12 @@ k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1, const double2 *
 // BiCGStab updates on a field (per-block scalars):
 //  op 0: p = r + beta (p - omega v)
 //  op 1: s = r - alpha v
-//  op 2: x += alpha ph + omega sh;  r = s - omega t
 //  op 3: y = a (copy)            op 4: y = 0
+// (the x / r update is k_bicg_xr, fused with the dots that follow it)
 template <typename T>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_bicg_update(LevelView<T> L, int opk, const BiState *S, typename cplx<T>::t *y,
-              const typename cplx<T>::t *a, const typename cplx<T>::t *c, const typename cplx<T>::t *d,
-              typename cplx<T>::t *y2, const typename cplx<T>::t *e) {
+              const typename cplx<T>::t *a, const typename cplx<T>::t *c) {
   typedef typename cplx<T>::t T2;
   const TileDev t = L.tiles[blockIdx.x];
   if (L.skip && L.skip[t.blk]) return;
@@ -1516,9 +1372,6 @@ k_bicg_update(LevelView<T> L, int opk, const BiState *S, typename cplx<T>::t *y,
       y[k] = cadd(a[k], cmul(be, csub(y[k], cmul(om, c[k]))));
     } else if (opk == 1) {
       y[k] = csub(a[k], cmul(al, c[k]));
-    } else if (opk == 2) {
-      y[k] = cadd(y[k], cadd(cmul(al, a[k]), cmul(om, c[k])));
-      y2[k] = csub(d[k], cmul(om, e[k]));
     } else if (opk == 3) {
       y[k] = a[k];
     } else {

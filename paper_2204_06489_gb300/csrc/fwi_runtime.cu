@@ -519,9 +519,6 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   for (int p = 0; p < 2; ++p) {
     size_t elem = p ? sizeof(double2) : sizeof(float2);
     int l0 = 1;
-#ifdef FWI_LS_MIN
-    l0 = std::max(l0, std::min(FWI_LS_MIN, minlev - 1));
-#endif
     while (l0 < minlev - 1 && smem_from(l0, elem) > budget) ++l0;
     if (minlev < 2) l0 = 0;  // single-level instances: the whole cycle is the coarse solve
     ls_p[p] = l0;
@@ -715,15 +712,6 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
     T.s0.upload(T.hs0, st);
     T.s1.upload(T.hs1, st);
   }
-  // dynamic shared memory of the double-buffered stencil kernels (both precisions)
-  CK(cudaFuncSetAttribute(k_field_op_tile<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)(2 * sizeof(FtStage<float>))));
-  CK(cudaFuncSetAttribute(k_field_op_tile<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)(2 * sizeof(FtStage<float>))));
-  CK(cudaFuncSetAttribute(k_field_op_tile<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)(2 * sizeof(FtStage<double>))));
-  CK(cudaFuncSetAttribute(k_field_op_tile<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)(2 * sizeof(FtStage<double>))));
   partial.alloc((size_t)std::max(1, lv[0].n_tiles) * 3);
   partial_s.alloc((size_t)std::max(1, lv[0].n_strips) * 3);
   blkfac.alloc(B); blkn0.alloc(B); blkn.alloc(B);
@@ -811,32 +799,21 @@ template <typename T>
 void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
                    typename cplx<T>::t *y, bool opA, int level) {
   LevelView<T> L = opA ? viewA<T>() : viewM<T>(level);
-  const bool timed = timer_begin<T>(level, L);
   // the register-marching kernel on the fine levels, the direct one on small grids
-#ifdef FWI_STENCIL_TILE
-  if (level <= 1) {
-    const size_t sm = 2 * sizeof(FtStage<T>);
-    if (cj) k_field_op_tile<T, true><<<L.n_tiles, TILE_THREADS, sm, st>>>(L, mode, wj, x, b, y);
-    else k_field_op_tile<T, false><<<L.n_tiles, TILE_THREADS, sm, st>>>(L, mode, wj, x, b, y);
-  } else {
-#else
   if (L.n_strips > 0) {
     const int grid = std::max(1, (L.n_strips + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
     if (cj) launch_march_cj<T, true>(grid, st, L, mode, wj, x, b, y);
     else launch_march_cj<T, false>(grid, st, L, mode, wj, x, b, y);
   } else {
-#endif
     if (cj) k_field_op<T, true><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
     else k_field_op<T, false><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
   }
   KCHECK();
-  // algorithmic bytes per processed node: each complex operand / result once
-  if (timed) timer_end((mode == FM_APPLY || mode == FM_JACOBI0) ? 2 : 3, sizeof(typename cplx<T>::t));
 }
 
-// Live timing of the level-0 complex64 stencil launches that are not being
-// captured into a graph (CUDA events on the context's stream; the kernels
-// count the nodes they processed into L.work).
+// Live timing of the level-0 complex64 two-sweep smoother launches that are
+// not being captured into a graph (CUDA events on the context's stream; the
+// kernel counts the nodes it processed into L.work).
 template <typename T>
 bool Ctx::timer_begin(int level, LevelView<T> &L) {
   if (!timer_on || level != 0 || sizeof(T) != 4) return false;
@@ -871,7 +848,6 @@ template <typename T>
 void Ctx::apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *y, const typename cplx<T>::t *a,
                      int nd) {
   LevelView<T> L = viewA<T>();
-  const bool timed = timer_begin<T>(0, L);
   const int grid = std::max(1, (L.n_strips + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
   const T w = 0;
   if (nd == 1) {
@@ -882,7 +858,6 @@ void Ctx::apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *
     else k_field_op_march<T, false, FM_APPLY, 2><<<grid, MARCH_THREADS, 0, st>>>(L, w, x, a, y, partial_s.p);
   }
   KCHECK();
-  if (timed) timer_end(3, sizeof(typename cplx<T>::t));
 }
 
 // Two damped-Jacobi sweeps in one pass on a fine level (x == nullptr: the
@@ -1057,8 +1032,8 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   LevelView<T> L = viewA<T>();
   const int nt = L.n_tiles;
   const int sb = (B + BICG_WARPS - 1) / BICG_WARPS;
-  auto upd = [&](int opk, T2 *y, const T2 *a, const T2 *c, const T2 *d, T2 *y2, const T2 *e) {
-    k_bicg_update<T><<<nt, TILE_THREADS, 0, st>>>(L, opk, w.bst.p, y, a, c, d, y2, e);
+  auto upd = [&](int opk, T2 *y, const T2 *a, const T2 *c) {
+    k_bicg_update<T><<<nt, TILE_THREADS, 0, st>>>(L, opk, w.bst.p, y, a, c);
     KCHECK();
   };
   auto scal = [&](int stage) {
@@ -1071,11 +1046,11 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
     KCHECK();
   };
   // x = 0, r = b, rh = b, p = v = 0
-  upd(4, x, nullptr, nullptr, nullptr, nullptr, nullptr);
-  upd(3, w.r.p, b, nullptr, nullptr, nullptr, nullptr);
-  upd(3, w.rh.p, b, nullptr, nullptr, nullptr, nullptr);
-  upd(4, w.p.p, nullptr, nullptr, nullptr, nullptr, nullptr);
-  upd(4, w.v.p, nullptr, nullptr, nullptr, nullptr, nullptr);
+  upd(4, x, nullptr, nullptr);
+  upd(3, w.r.p, b, nullptr);
+  upd(3, w.rh.p, b, nullptr);
+  upd(4, w.p.p, nullptr, nullptr);
+  upd(4, w.v.p, nullptr, nullptr);
   block_dots<T>(1, b, b, nullptr, nullptr, nullptr, nullptr);
   scal(0);
   // from here on, kernels skip the blocks whose solve has finished (zero
@@ -1090,11 +1065,11 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   // rho = <rh, r> = <b, b> for the first iteration: the partials still hold <b, b>
   scal(1);
   for (int it = 0; it < iters; ++it) {
-    upd(0, w.p.p, w.r.p, w.v.p, nullptr, nullptr, nullptr);          // p = r + beta (p - omega v)
+    upd(0, w.p.p, w.r.p, w.v.p);          // p = r + beta (p - omega v)
     mg_cycle<T>(w.p.p, w.ph.p, cj, o);                                 // ph = K p
     apply_dots<T>(cj, w.ph.p, w.v.p, w.rh.p, 1);                       // v = A ph, <rh, v>
     scal_s(2);
-    upd(1, w.s.p, w.r.p, w.v.p, nullptr, nullptr, nullptr);          // s = r - alpha v
+    upd(1, w.s.p, w.r.p, w.v.p);          // s = r - alpha v
     mg_cycle<T>(w.s.p, w.sh.p, cj, o);                                 // sh = K s
     apply_dots<T>(cj, w.sh.p, w.t.p, w.s.p, 2);                        // t = A sh, <t, s>, <t, t>
     scal_s(3);
