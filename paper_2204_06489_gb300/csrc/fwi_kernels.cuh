@@ -245,8 +245,6 @@ k_field_op_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
   const int i = s.col0 - 1 + lane;
   const bool in_grid = i >= 0 && i < nx;
   const bool own = lane >= 1 && lane <= MARCH_COLS && i < nx;
-  if (L.work && s.col0 == 0 && lane == 0)
-    atomicAdd(L.work, (unsigned long long)(s.row1 - s.row0) * nx);
   const unsigned long long pol = keep_policy();
   const T2 zero = mk<T2>(0, 0);
   const T2 *X = L.st + op.st;
@@ -598,69 +596,6 @@ k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>:
       acc0 = cadd(acc0, h);
     }
     xm = x0; x0 = xp; xp = xn;
-  }
-}
-
-// Fused residual + restriction (R = P^T, i.e. 4x full weighting):
-//   bc[J][I] = sum_{a,b in -1..1} w_a w_b (bf - Op xf)[2J+1+b][2I+1+a],  w = (1/2, 1, 1/2).
-// A CTA takes one coarse row tile (8 coarse rows) and walks it in chunks of
-// 64 coarse columns: the 17 x 129 fine residuals of a chunk are computed once
-// into shared memory (one warp per fine row), then every coarse node sums its
-// nine weighted neighbours from there.
-#define RR_CW 64
-#define RR_FW (2 * RR_CW + 1)
-#define RR_FR (2 * TILE_ROWS + 1)
-template <typename T, bool CJ>
-__global__ void __launch_bounds__(TILE_THREADS)
-k_resid_restrict(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__restrict__ xf,
-                 const typename cplx<T>::t *__restrict__ bf, typename cplx<T>::t *__restrict__ bc) {
-  typedef typename cplx<T>::t T2;
-  __shared__ T2 r[RR_FR][RR_FW];
-  const TileDev t = Lc.tiles[blockIdx.x];
-  if (Lc.skip && Lc.skip[t.blk]) return;
-  const BlkDev bkc = Lc.blks[t.blk];
-  const OpDev opc = Lc.ops[bkc.op];
-  const BlkDev bkf = Lf.blks[t.blk];
-  const OpDev opf = Lf.ops[bkf.op];
-  const T2 *xb = xf + bkf.off;
-  const T2 *bb = bf + bkf.off;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int J0 = t.row0;
-  const int jf0 = 2 * J0;
-  for (int I0 = 0; I0 < opc.nx; I0 += RR_CW) {
-    const int if0 = 2 * I0;
-    for (int rr = warp; rr < RR_FR; rr += TILE_ROWS) {
-      int j = jf0 + rr;
-      if (j < opf.nz) {
-        const RowOp<T, CJ> R(opf, Lf.st, Lf.dg, Lf.dgi, j);
-        const T2 *xr = xb + (long long)j * opf.nx;
-        const T2 *br = bb + (long long)j * opf.nx;
-        for (int c = lane; c < RR_FW; c += 32) {
-          int i = if0 + c;
-          T2 v = mk<T2>(0, 0);
-          if (i < opf.nx) v = csub(br[i], R.apply(xr, i));
-          r[rr][c] = v;
-        }
-      } else {
-        for (int c = lane; c < RR_FW; c += 32) r[rr][c] = mk<T2>(0, 0);
-      }
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < TILE_ROWS * RR_CW; q += TILE_THREADS) {
-      int jl = q / RR_CW, il = q - jl * RR_CW;
-      int J = J0 + jl, I = I0 + il;
-      if (J < opc.nz && I < opc.nx) {
-        // fine rows 2jl..2jl+2 and columns 2il..2il+2 of the chunk
-        const T2 *r0 = r[2 * jl] + 2 * il;
-        const T2 *r1 = r[2 * jl + 1] + 2 * il;
-        const T2 *r2 = r[2 * jl + 2] + 2 * il;
-        T2 e0 = cadd(cadd(cscale(r0[0], (T)0.5), r0[1]), cscale(r0[2], (T)0.5));
-        T2 e1 = cadd(cadd(cscale(r1[0], (T)0.5), r1[1]), cscale(r1[2], (T)0.5));
-        T2 e2 = cadd(cadd(cscale(r2[0], (T)0.5), r2[1]), cscale(r2[2], (T)0.5));
-        bc[bkc.off + (long long)J * opc.nx + I] = cadd(cadd(cscale(e0, (T)0.5), e1), cscale(e2, (T)0.5));
-      }
-    }
-    __syncthreads();
   }
 }
 

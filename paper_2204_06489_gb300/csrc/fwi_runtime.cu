@@ -680,7 +680,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
       // block-major, then row band, then column, so that neighbouring strips
       // (which share halo rows and columns) run close together
       T.hs0[b] = (int)T.hstrips.size();
-      if (l < ls)
+      if (l < std::max(ls, 1))   // level 0 always (operator apply, dots), the other global levels
         for (int r0 = 0; r0 < nz; r0 += MARCH_ROWS) {
           for (int c0 = 0; c0 < nx; c0 += MARCH_COLS)
             T.hstrips.push_back(StripDev{b, c0, r0, std::min(r0 + MARCH_ROWS, nz)});
@@ -885,15 +885,11 @@ template <typename T>
 void Ctx::resid_restrict(int cj, int l, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
                          typename cplx<T>::t *bc) {
   LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
-  const int n = lv[l].n_rstrips;
-  if (n > 0) {
-    const int grid = (n + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32);
-    if (cj) k_resid_restrict_march<T, true><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
-    else k_resid_restrict_march<T, false><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
-  } else {
-    if (cj) k_resid_restrict<T, true><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, x, b, bc);
-    else k_resid_restrict<T, false><<<Lc.n_tiles ? Lc.n_tiles : 1, TILE_THREADS, 0, st>>>(Lf, Lc, x, b, bc);
-  }
+  const int n = lv[l].n_rstrips;   // built for every global level l < ls, the only levels that restrict
+  if (n == 0) fail(FWI_E_INVAL, "internal: no restriction strips on a global multigrid level");
+  const int grid = (n + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32);
+  if (cj) k_resid_restrict_march<T, true><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
+  else k_resid_restrict_march<T, false><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
   KCHECK();
 }
 

@@ -176,3 +176,21 @@ def test_autotuner_picks_a_converging_schedule(lib):
     assert rates[(best.nu1, best.mg_wdepth)] == max(rates.values())
     assert all(t[4] < 1.0 for t in table)
     f.close()
+
+
+def test_single_level_grid_kkt_solve(lib):
+    """A padded grid of at most 256 nodes has one multigrid level: the whole
+    cycle is the shared-memory kernel's exact coarsest solve, and the level-0
+    strip kernels (operator apply with the BiCGStab dots) still run.  The KKT
+    solution must match the oracle's direct solve."""
+    wl = FI.micro_workload(seed=11, nx=7, nz=5, npml=4, n_src=2, n_rec=3)
+    assert (wl.grid.nx + 2 * wl.grid.npml) * (wl.grid.nz + 2 * wl.grid.npml) <= 256
+    P, f, prob, d = _setup(wl)
+    opts = P.default_opts(eps=1e-2, tol=1e-7)
+    f.forward(opts)
+    ds, st = f.kkt_solve(opts)
+    K = kkt.KKT(prob, wl.gamma_start.ravel(), d, 1e-2, include_Ls_n=True)
+    ref = K.delta_s(K.solve_direct())
+    assert st["rel_res"] <= 1e-7
+    assert _rel(ds, ref) < 1e-5
+    f.close()
