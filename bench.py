@@ -40,6 +40,24 @@ def _dist():
     return ws, rank
 
 
+def replica_throughput(seconds: float, steps: int, device: str = "cuda"):
+    """Whole-job throughput of N independent replicas (one per rank, each doing
+    ``steps`` Newton steps of the same workload): the timed region of the job
+    is the slowest rank's, so the seconds are reduced by MAX over the process
+    group (when one is initialised) and value = ranks / (max seconds / steps).
+    Returns (value, per-step seconds)."""
+    import torch
+    import torch.distributed as dist
+    ws = 1
+    if dist.is_available() and dist.is_initialized():
+        ws = dist.get_world_size()
+        t = torch.tensor([seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = t.item()
+    per_step = seconds / steps
+    return ws / per_step, per_step
+
+
 class Clocks:
     """nvidia-smi sampler running during the timed region."""
 
@@ -395,12 +413,7 @@ def main():
     dev_s = e0.elapsed_time(e1) / 1e3
     launches = f._L.fwi_kernel_launches() - launches0
     st_ms, st_bytes, st_n = f.stencil_timer(0)
-    if ws > 1:
-        t = torch.tensor([dev_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = t.item()
-    per_step = dev_s / args.steps
-    value = ws / per_step
+    value, per_step = replica_throughput(dev_s, args.steps)
     outer = sum(s.outer_iters for s in stats) / len(stats)
     inner = sum(s.inner_iters for s in stats) / len(stats)
     relres = max(s.rel_res for s in stats)
