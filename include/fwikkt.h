@@ -187,6 +187,20 @@ int fwi_kkt_solve(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device,
 int fwi_newton_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device,
                     fwi_stats *stats);
 
+/* One reduced-space Gauss-Newton step (Sec. 3, "RSGN-CG": the normal equations
+ * eq. normal_system_discrete_sum solved by conjugate gradients), the paper's
+ * comparison method: set-up, forward modelling, CG on
+ *   (eps I + Re(P~^H A'^{-H} Q^T W^T W Q A'^{-1} P~)) ds~ = b_s + Re(P~^H A'^{-H} Q^T W^T W r)
+ * in the scaled variables of fwi_kkt_solve (same ds), one forward and one
+ * adjoint refined block solve (to opts->fwd_tol) per CG iteration, stopping at
+ * ||g - H ds~|| / ||g|| <= opts->tol or opts->max_outer iterations; then the
+ * full step s <- s + ds.  ds as in fwi_kkt_solve (nullable);
+ * stats->outer_iters = CG iterations.  FWI_E_NOCONV (with the step applied) at
+ * the iteration cap or when a block solve misses fwd_tol; FWI_E_NUMERIC if
+ * p^T H p is not positive. */
+int fwi_rsgn_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device,
+                  fwi_stats *stats);
+
 /* ---- operator-level entry points (device buffers, for checks and tools) ----
  * x, y: device field buffers in the given precision (float2 or double2
  * elements, field layout).  The operators use the current models and, where

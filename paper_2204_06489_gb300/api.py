@@ -104,6 +104,7 @@ def load(build_if_missing: bool = False):
         "fwi_gradient": (C.c_int, [P, C.POINTER(Opts), DP, P, C.c_int, C.POINTER(Stats)]),
         "fwi_kkt_solve": (C.c_int, [P, C.POINTER(Opts), P, C.c_int, C.POINTER(Stats)]),
         "fwi_newton_step": (C.c_int, [P, C.POINTER(Opts), P, C.c_int, C.POINTER(Stats)]),
+        "fwi_rsgn_step": (C.c_int, [P, C.POINTER(Opts), P, C.c_int, C.POINTER(Stats)]),
         "fwi_apply_helmholtz": (C.c_int, [P, P, P, C.c_int, C.c_int]),
         "fwi_apply_kkt": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
         "fwi_apply_precond": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
@@ -289,6 +290,16 @@ class FWI:
         ds = np.zeros(self.layout()["ctrl_elems"])
         rc = self._L.fwi_newton_step(self._h, C.byref(opts) if opts else None, ds.ctypes.data_as(P), 0,
                                      C.byref(st))
+        self._check(rc, allow_noconv)
+        return ds, st.as_dict()
+
+    def rsgn_step(self, opts: Optional[Opts] = None, allow_noconv: bool = False):
+        """One reduced-space Gauss-Newton step (normal equations by CG); same
+        outputs as ``newton_step`` (stats["outer_iters"] counts CG iterations)."""
+        st = Stats()
+        ds = np.zeros(self.layout()["ctrl_elems"])
+        rc = self._L.fwi_rsgn_step(self._h, C.byref(opts) if opts else None, ds.ctypes.data_as(P), 0,
+                                   C.byref(st))
         self._check(rc, allow_noconv)
         return ds, st.as_dict()
 

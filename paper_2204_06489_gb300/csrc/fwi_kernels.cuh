@@ -1418,6 +1418,7 @@ __global__ void k_kkt_F(int n, const long long *node, const double *w2, const ty
 // mode 0 (KKT row 2):      out_c = eps * ds_c - acc_c
 // mode 1 (preconditioner): out_c = (v_c + acc_c) / eps
 // mode 2 (gradient):       out_c = -acc_c   (cf_b = omega_b^2 h^2, lm = lambda')
+// mode 3 (normal matrix):  out_c = eps * v_c + acc_c
 // Block partitions: threadIdx.y takes blocks b = blk0 + ty, ty + 4, ...; the 4
 // partial sums are combined in a fixed order.
 template <typename T, typename TO>
@@ -1447,6 +1448,7 @@ __global__ void k_coupling_reduce(const InstDev *inst, int Nx_stride_unused, con
     double r;
     if (mode == 0) r = eps * (double)v[o] - s;
     else if (mode == 1) r = ((double)v[o] + s) / eps;
+    else if (mode == 3) r = eps * (double)v[o] + s;
     else r = -s;
     out[o] = (TO)r;
   }

@@ -267,6 +267,9 @@ struct Ctx {
   template <typename T> const typename cplx<T>::t *u_T();
   int gradient(const fwi_opts &o, double *misfit_out, double *grad, int on_device, fwi_stats *stats);
   int newton_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats);
+  int rsgn_solve(const fwi_opts &o, fwi_stats *stats);
+  int rsgn_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats);
+  void apply_update(double *ds, int on_device);
   void write_ctrl(const double *src_ctrl_dev, double *dst, int on_device, const double *fac);
   template <typename T> void mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
                                       const fwi_opts &o);
@@ -1604,6 +1607,12 @@ int Ctx::newton_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *st
   if (stats) stats->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   forward(o, stats);
   int rc = kkt_solve(o, stats);
+  apply_update(ds, on_device);
+  return rc;
+}
+
+// The update of a Gauss-Newton step from the scaled control in xi64's ds slot.
+void Ctx::apply_update(double *ds, int on_device) {
   // ds = gamma_ref * ds~ ; s += ds
   std::vector<double> gr;
   for (auto &I : inst) gr.push_back(I.gamma_ref);
@@ -1625,6 +1634,143 @@ int Ctx::newton_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *st
   sync();
   ++model_version;
   have_fwd = false;
+}
+
+// Reduced-space Gauss-Newton (Sec. 3, eq. normal_system_discrete_sum) by
+// conjugate gradients, on the same scaled variables as the KKT solve:
+//   (eps I + Re(P~^H A'^{-H} F A'^{-1} P~)) ds~ = b_s + Re(P~^H A'^{-H} Q^T W^T W r),
+// F = Q^T W^T W Q, which is the KKT system with du and lambda eliminated, so
+// its solution is the KKT solution's ds~.  Every CG iteration makes one
+// forward and one adjoint refined solve of every block (FP64 fields, complex64
+// inner solves, fwd_tol).  The result goes to xi64's ds slot; stats->outer_iters
+// counts CG iterations, stats->rel_res is the final ||g - H ds~|| / ||g||
+// (the recursively updated CG residual).
+int Ctx::rsgn_solve(const fwi_opts &o, fwi_stats *stats) {
+  if (!have_fwd) fail(FWI_E_INVAL, "the reduced-space step needs fwi_forward at the current model");
+  bool have_d = true;
+  for (auto &I : inst) have_d = have_d && I.has_data;
+  if (!have_d) fail(FWI_E_INVAL, "observed data missing");
+  if (!(o.eps > 0.0)) fail(FWI_E_INVAL, "eps must be > 0");
+  auto t0 = std::chrono::steady_clock::now();
+  const long long nc = Nc;
+  xi64.alloc(nkkt);
+  CK(cudaMemsetAsync(xi64.p, 0, nkkt * sizeof(double), st));
+  double *x = xi64.p + 4 * F0;             // ds~ (the KKT layout's control slot)
+  DBuf<double> g, rr, p, hp, bs, part;
+  g.alloc(nc); rr.alloc(nc); p.alloc(nc); hp.alloc(nc); bs.alloc(nc); part.alloc(FLAT_BLOCKS);
+  DBuf<double2> fa, fb, zero;
+  fa.alloc(F0); fb.alloc(F0); zero.alloc(F0);
+  zero.zero(st);
+  long long mx = 0;
+  for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
+  const dim3 gr((unsigned)((mx + 127) / 128), (unsigned)inst.size());
+  LevelView<double> L64 = viewA<double>();
+  int solve_rc = FWI_OK;
+  auto solve = [&](const double2 *rhs, double2 *sol, int cj) {
+    int rc = o.precision == FWI_C128 ? refined_solve<double>(rhs, sol, cj, o, stats)
+                                     : refined_solve<float>(rhs, sol, cj, o, stats);
+    if (rc != FWI_OK) solve_rc = rc;
+  };
+  // out = eps * v + Re(P~^H lambda)  (per core node, fixed block order)
+  auto couple = [&](const double2 *lam, const double *v, double eps, double *out) {
+    k_coupling_reduce<double, double><<<gr, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfK.p, u64.p,
+                                                                   lam, v, eps, 3, out);
+    KCHECK();
+  };
+  // lambda = A'^{-H} Q^T W^T W (values at the receivers q)
+  auto adjoint_of_receivers = [&](const double2 *q, double2 *lam) {
+    CK(cudaMemsetAsync(fa.p, 0, F0 * sizeof(double2), st));
+    if (n_unique)
+      k_rec_scatter<<<grid_for(n_unique, 128, 1 << 20), 128, 0, st>>>(n_unique, d_unode.p, d_uoff.p, d_uidx.p,
+                                                                      d_rec_w.p, q, fa.p);
+    KCHECK();
+    solve(fa.p, lam, 1);
+  };
+  auto dot = [&](const double *a, const double *b) {
+    k_dot2<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, a, b, part.p);
+    KCHECK();
+    std::vector<double> h(FLAT_BLOCKS);
+    CK(cudaMemcpyAsync(h.data(), part.p, FLAT_BLOCKS * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    double acc = 0.0;
+    for (double v : h) acc += v;
+    return acc;
+  };
+  const int nrec = (int)rec_node.size();
+  DBuf<double2> qv, rdummy;
+  qv.alloc(std::max(nrec, 1)); rdummy.alloc(std::max(nrec, 1));
+  // H~ v
+  auto normal = [&](const double *v, double *out) {
+    k_coupling_scatter<double><<<L64.n_tiles, TILE_THREADS, 0, st>>>(L64, d_inst.p, cfK.p, u64.p, zero.p, v, fb.p);
+    KCHECK();
+    solve(fb.p, fa.p, 0);                                  // du = A'^{-1} P~ v
+    if (nrec)
+      k_rec_residual<<<grid_for(nrec, 128, 1 << 20), 128, 0, st>>>(nrec, d_rec_node.p, fa.p, nullptr, qv.p,
+                                                                   rdummy.p, 0);
+    KCHECK();
+    adjoint_of_receivers(qv.p, fb.p);                      // lambda = A'^{-H} F du
+    couple(fb.p, v, o.eps, out);
+  };
+  // right-hand side g = b_s + Re(P~^H A'^{-H} Q^T W^T W r)
+  {
+    std::vector<const double *> sp;
+    std::vector<double> gref;
+    for (auto &I : inst) { sp.push_back(I.s.p); gref.push_back(I.gamma_ref); }
+    DBuf<const double *> dsp;
+    dsp.upload(sp, st);
+    inst_gref.upload(gref, st);
+    DBuf<double> bsfull;
+    bsfull.alloc(nkkt);
+    k_ctrl_rhs<<<dim3(grid_for(mx, 256), (unsigned)inst.size()), 256, 0, st>>>(d_inst.p, dsp.p, inst_gref.p, o.eps,
+                                                                              o.include_Ls_n, bsfull.p + 4 * F0);
+    KCHECK();
+    CK(cudaMemcpyAsync(bs.p, bsfull.p + 4 * F0, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    adjoint_of_receivers(r.p, fb.p);
+    couple(fb.p, bs.p, 1.0, g.p);
+    sync();
+  }
+  // CG from ds~ = 0
+  CK(cudaMemcpyAsync(rr.p, g.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(p.p, g.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const double gn = std::sqrt(dot(g.p, g.p));
+  double rho = gn * gn;
+  int it = 0;
+  int status = FWI_E_NOCONV;
+  double rel = gn > 0.0 ? 1.0 : 0.0;
+  if (!(gn > 0.0)) status = FWI_OK;
+  while (status != FWI_OK && it < o.max_outer) {
+    normal(p.p, hp.p);
+    const double php = dot(p.p, hp.p);
+    if (!std::isfinite(php) || !(php > 0.0)) fail(FWI_E_NUMERIC, "reduced-space CG: p^T H p is not positive");
+    const double alpha = rho / php;
+    k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, alpha, p.p, 1.0, x);
+    k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, -alpha, hp.p, 1.0, rr.p);
+    KCHECK();
+    const double rho_new = dot(rr.p, rr.p);
+    ++it;
+    rel = std::sqrt(rho_new) / gn;
+    if (rel <= o.tol) { status = FWI_OK; break; }
+    k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, 1.0, rr.p, rho_new / rho, p.p);
+    KCHECK();
+    rho = rho_new;
+  }
+  sync();
+  if (stats) {
+    stats->outer_iters += it;
+    stats->rel_res = rel;
+    stats->t_solve_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (solve_rc != FWI_OK && status == FWI_OK) status = solve_rc;
+  return status;
+}
+
+int Ctx::rsgn_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  build_hierarchy(o);
+  if (stats) stats->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  forward(o, stats);
+  int rc = rsgn_solve(o, stats);
+  apply_update(ds, on_device);
   return rc;
 }
 
@@ -1926,6 +2072,20 @@ int fwi_newton_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_devic
   if (stats) std::memset(stats, 0, sizeof(*stats));
   int rc = c.newton_step(o, ds, on_device, stats);
   if (rc != FWI_OK) c.err = "KKT solve stopped at the iteration cap";
+  return rc;
+  API_END(ctx)
+}
+
+int fwi_rsgn_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device, fwi_stats *stats) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid options");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  int rc = c.rsgn_step(o, ds, on_device, stats);
+  if (rc == FWI_E_NOCONV) c.err = "reduced-space CG stopped at the iteration cap (or a block solve missed fwd_tol)";
   return rc;
   API_END(ctx)
 }

@@ -194,3 +194,22 @@ def test_single_level_grid_kkt_solve(lib):
     assert st["rel_res"] <= 1e-7
     assert _rel(ds, ref) < 1e-5
     f.close()
+
+
+def test_reduced_space_cg_step_equals_the_kkt_solution(lib):
+    """RSGN-CG (the paper's reduced-space comparison method): the normal
+    equations by CG give the same unique update as the KKT system; checked
+    against the oracle's direct KKT solve and against the library's own
+    full-space step from the same model."""
+    wl = FI.micro_workload(seed=12, nx=31, nz=17, npml=6, n_src=2, n_rec=6)
+    P, f, prob, d = _setup(wl)
+    opts = P.default_opts(eps=1e-2, tol=1e-9, max_outer=400)
+    K = kkt.KKT(prob, wl.gamma_start.ravel(), d, 1e-2, include_Ls_n=True)
+    ref = K.delta_s(K.solve_direct())
+    ds_cg, st = f.rsgn_step(opts)
+    assert st["outer_iters"] > 1 and st["rel_res"] <= 1e-9
+    assert _rel(ds_cg, ref) < 1e-6, _rel(ds_cg, ref)
+    f.set_model(0, wl.gamma_start)
+    ds_kkt, _ = f.newton_step(P.default_opts(eps=1e-2, tol=1e-7))
+    assert _rel(ds_cg, ds_kkt) < 1e-5
+    f.close()
