@@ -188,6 +188,10 @@ def run_extra_case(args):
       large     1601x561 h=5 m, 128 sources, one frequency (4 Hz)
       autograd  801x281 h=10 m, 64 sources, 6 Hz: misfit + gradient through
                 torch.autograd, with central-difference checks
+      rsgn      the benchmark workload (401x141, 120 blocks): one reduced-space
+                Gauss-Newton step (normal equations by CG, two refined block
+                solves per CG iteration), capped at ``--max-outer`` CG
+                iterations, next to one full-space step from the same model
     batch3a/3b/large run one Newton step with a cap of ``--max-outer`` outer
     iterations and report throughput (outer and inner iterations per second)."""
     import numpy as np
@@ -204,11 +208,14 @@ def run_extra_case(args):
         wls = FI.uneven_workloads()
     elif args.case == "large":
         wls = [FI.large_workload(freqs=(4.0,))]
+    elif args.case == "rsgn":
+        wls = [_workload()]
     else:
         wls = [FI.autograd_workload()]
-    from paper_2204_06489_gb300.autotune import auto_wdepth
-    opts.mg_wdepth = auto_wdepth([w.grid for w in wls], [w.survey.freqs_hz for w in wls],
-                                 [w.gamma_start for w in wls])
+    if args.case != "rsgn":
+        from paper_2204_06489_gb300.autotune import auto_wdepth
+        opts.mg_wdepth = auto_wdepth([w.grid for w in wls], [w.survey.freqs_hz for w in wls],
+                                     [w.gamma_start for w in wls])
     t0 = time.perf_counter()
     f = _setup_ctx(P, wls, opts, stream)
     t_setup = time.perf_counter() - t0
@@ -238,6 +245,24 @@ def run_extra_case(args):
             an = float(np.sum(grad * dirn))
             errs.append(abs((fp - fm) / 2 - an) / abs(an))
         out.update(misfit=phi.item(), fd_rel_err_max=max(errs), fd_directions=len(errs))
+    elif args.case == "rsgn":
+        o = P.Opts.from_buffer_copy(opts)
+        o.max_outer = args.max_outer
+        res = {}
+        for name, step in (("fsgn", f.newton_step), ("rsgn", f.rsgn_step)):
+            f.set_model(0, wls[0].gamma_start)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ds, st = step(o if name == "rsgn" else opts, allow_noconv=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            res[name] = {"step_s": dt, "iters": st["outer_iters"], "rel_res": st["rel_res"],
+                         "forward_ms": st["t_forward_ms"], "solve_ms": st["t_solve_ms"],
+                         "s_per_iter": st["t_solve_ms"] / 1e3 / max(st["outer_iters"], 1)}
+            res[name + "_ds"] = ds
+        dk, dr = res.pop("fsgn_ds"), res.pop("rsgn_ds")
+        res["rel_diff_ds"] = float(np.linalg.norm(dr - dk) / np.linalg.norm(dk))
+        out.update(res)
     else:
         o = P.Opts.from_buffer_copy(opts)
         o.max_outer = args.max_outer
@@ -324,7 +349,8 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--case", default="newton", choices=["newton", "inner", "batch3a", "batch3b", "large", "autograd"])
+    ap.add_argument("--case", default="newton",
+                    choices=["newton", "inner", "batch3a", "batch3b", "large", "autograd", "rsgn"])
     ap.add_argument("--max-outer", type=int, default=60)
     ap.add_argument("--fd-dirs", type=int, default=4)
     ap.add_argument("--inner-iters", type=int, default=None)
