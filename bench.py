@@ -188,6 +188,10 @@ def run_extra_case(args):
       large     1601x561 h=5 m, 128 sources, one frequency (4 Hz)
       autograd  801x281 h=10 m, 64 sources, 6 Hz: misfit + gradient through
                 torch.autograd, with central-difference checks
+      tradeoff  the benchmark workload: one KKT solve per inner-iteration count
+                (2 .. 48 BiCGStab iterations per block solve, W to level 2),
+                outer FGMRES iterations against time: the inexactness
+                trade-off of the preconditioner's block solves
       rsgn      the benchmark workload (401x141, 120 blocks): one reduced-space
                 Gauss-Newton step (normal equations by CG, two refined block
                 solves per CG iteration), capped at ``--max-outer`` CG
@@ -208,11 +212,11 @@ def run_extra_case(args):
         wls = FI.uneven_workloads()
     elif args.case == "large":
         wls = [FI.large_workload(freqs=(4.0,))]
-    elif args.case == "rsgn":
+    elif args.case in ("rsgn", "tradeoff"):
         wls = [_workload()]
     else:
         wls = [FI.autograd_workload()]
-    if args.case != "rsgn":
+    if args.case not in ("rsgn", "tradeoff"):
         from paper_2204_06489_gb300.autotune import auto_wdepth
         opts.mg_wdepth = auto_wdepth([w.grid for w in wls], [w.survey.freqs_hz for w in wls],
                                      [w.gamma_start for w in wls])
@@ -245,6 +249,15 @@ def run_extra_case(args):
             an = float(np.sum(grad * dirn))
             errs.append(abs((fp - fm) / 2 - an) / abs(an))
         out.update(misfit=phi.item(), fd_rel_err_max=max(errs), fd_directions=len(errs))
+    elif args.case == "tradeoff":
+        from paper_2204_06489_gb300.autotune import tune_kkt
+        f.set_model(0, wls[0].gamma_start)
+        f.forward(opts, want_data=False)
+        o = P.Opts.from_buffer_copy(opts)
+        o.max_outer = args.max_outer
+        _, table = tune_kkt(f, o, (2, 4, 6, 8, 12, 16, 24, 48), (2,), (30,))
+        out["sweep"] = [{"inner_iters": n, "kkt_s": round(t, 3), "outer": k, "converged": ok}
+                        for n, wd, rs, t, k, ok in table]
     elif args.case == "rsgn":
         o = P.Opts.from_buffer_copy(opts)
         o.max_outer = args.max_outer
@@ -350,7 +363,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--case", default="newton",
-                    choices=["newton", "inner", "batch3a", "batch3b", "large", "autograd", "rsgn"])
+                    choices=["newton", "inner", "batch3a", "batch3b", "large", "autograd", "rsgn", "tradeoff"])
     ap.add_argument("--max-outer", type=int, default=60)
     ap.add_argument("--fd-dirs", type=int, default=4)
     ap.add_argument("--inner-iters", type=int, default=None)
@@ -399,7 +412,7 @@ def main():
         from paper_2204_06489_gb300.autotune import tune_kkt
         f.set_model(0, wl.gamma_start)
         f.forward(opts, want_data=False)
-        opts, table = tune_kkt(f, opts, (6, 8, 12), (1, 2), (30, 60))
+        opts, table = tune_kkt(f, opts, (4, 6, 8, 12, 16), (1, 2), (30,))
         tuned = [{"inner_iters": n, "wdepth": wd, "restart": rs, "s": round(t, 3), "outer": o, "ok": ok}
                  for n, wd, rs, t, o, ok in table]
     g0 = torch.from_numpy(wl.gamma_start).cuda()
