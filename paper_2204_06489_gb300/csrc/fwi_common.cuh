@@ -5,10 +5,13 @@
 //     rows z-major, x fastest, no row padding); one field per multigrid level;
 //   * a packed KKT vector is [du field | lambda field | ds control], all real
 //     scalars of precision T (complex entries interleaved re, im);
-//   * kernels over fields are launched on "row tiles": a tile is TILE_ROWS
-//     consecutive rows of one block and one warp handles one row, so every
-//     CTA belongs to exactly one block (per-block scalars, deterministic
-//     per-block reductions, ragged batches of different grid sizes).
+//   * kernels over fields are launched on "row tiles" (a tile is TILE_ROWS
+//     consecutive rows of one block, one warp per row: elementwise updates,
+//     dots, prolongation, small levels) or on "column strips" (a warp walks up
+//     to MARCH_ROWS rows of a band of columns of one block: the fine-level
+//     stencils).  Either way a CTA or warp belongs to exactly one block
+//     (per-block scalars, deterministic per-block reductions, ragged batches
+//     of different grid sizes without padding).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

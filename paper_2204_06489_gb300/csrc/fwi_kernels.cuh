@@ -1,10 +1,12 @@
 // fwi_kernels.cuh -- CUDA kernels of the full-space Gauss-Newton FWI path.
 //
-// Every kernel here is HBM-bound (5-point stencils, transfers, coupling
-// reductions, Krylov vector updates): nothing is a dense contraction, so no
-// tensor cores.  Field kernels run on row tiles (fwi_common.cuh): one warp per
-// grid row, lanes stride along x, so loads of a row are coalesced and the
-// x-neighbours and the rows above/below come from L1/L2.
+// The kernels are bandwidth- or issue-bound (5-point stencils with complex
+// PML coefficients, transfers, coupling reductions, Krylov vector updates):
+// nothing is a dense contraction, so no tensor cores.  The fine-level
+// stencils walk column strips down the grid with the rows they need in
+// registers (one lane per column, neighbours by shuffles); elementwise work
+// runs on row tiles (one warp per grid row, coalesced along x); the coarse
+// multigrid levels of a block run in one CTA's shared memory.
 #pragma once
 #include "fwi_common.cuh"
 

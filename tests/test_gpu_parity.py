@@ -305,9 +305,9 @@ def test_kkt_solve_odd_control_size(lib):
 
 @pytest.mark.parametrize("prec,tol", [(torch.complex128, 1e-12), (torch.complex64, 2e-6)])
 def test_wide_grid_operator_and_cycle(lib, prec, tol):
-    """A grid wider than two 128-column chunks of the staged stencil kernel
-    (313 padded columns: chunks of 128, 128 and a ragged 57) and taller than
-    several row tiles; operator, adjoint and one multigrid cycle against the
+    """A wide grid (313 padded columns: ten 30-column strips and a ragged 13 for
+    the operator, five 60-column strips and a ragged 13 for the smoother) taller
+    than one strip band; operator, adjoint and one multigrid cycle against the
     oracle."""
     import paper_2204_06489_gb300 as P
     wl = FI.micro_workload(seed=11, nx=301, nz=29, npml=6, n_src=2, n_rec=7, freq=6.0)
