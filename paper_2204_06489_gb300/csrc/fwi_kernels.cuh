@@ -99,91 +99,6 @@ __device__ __forceinline__ double2 cinv(double2 z) {
   return make_double2(z.x * r, -z.y * r);
 }
 
-// The 5-point operator along one grid row j.  Row constants (Z_j,
-// 1/Z_{j-1/2}, 1/Z_{j+1/2}) are loaded once; the diagonal cc and 1/cc come
-// from per-operator arrays computed at set-up (shared by all sources of a
-// frequency, L2-resident), so a node costs
-//   (Op u)_ij = cc u_ij - Z_j (u_i+1,j / X_{i+1/2} + u_i-1,j / X_{i-1/2})
-//                       - X_i (u_i,j+1 / Z_{j+1/2} + u_i,j-1 / Z_{j-1/2}),
-// every factor conjugated when CJ (A^H = conj A, A^T = A).
-template <typename T, bool CJ>
-struct RowOp {
-  typedef typename cplx<T>::t T2;
-  const T2 *X, *iXh, *dg, *dgi;
-  T2 Zj, iZn, iZs;
-  int nx, nz, j;
-  __device__ __forceinline__ RowOp(const OpDev &op, const T2 *__restrict__ st, const T2 *__restrict__ dgb,
-                                   const T2 *__restrict__ dgib, int j_) {
-    X = st + op.st;
-    iXh = X + op.nx;
-    const T2 *Z = iXh + op.nx + 1;
-    const T2 *iZh = Z + op.nz;
-    nx = op.nx; nz = op.nz; j = j_;
-    dg = dgb + op.dg + j * op.nx;
-    dgi = dgib + op.dg + j * op.nx;
-    Zj = cmaybe_conj(Z[j], CJ);
-    iZn = cmaybe_conj(iZh[j], CJ);
-    iZs = cmaybe_conj(iZh[j + 1], CJ);
-  }
-  __device__ __forceinline__ T2 diag(int i) const { return cmaybe_conj(ld_keep(dg + i), CJ); }
-  __device__ __forceinline__ T2 dinv(int i) const { return cmaybe_conj(ld_keep(dgi + i), CJ); }
-  // (Op u)_ij; urow points at row j of the block's grid
-  __device__ __forceinline__ T2 apply(const T2 *__restrict__ urow, int i) const {
-    T2 Xi = cmaybe_conj(ld_keep(X + i), CJ);
-    T2 iw = cmaybe_conj(ld_keep(iXh + i), CJ);
-    T2 ie = cmaybe_conj(ld_keep(iXh + i + 1), CJ);
-    T2 uc = urow[i];
-    T2 ue = i + 1 < nx ? urow[i + 1] : mk<T2>(0, 0);
-    T2 uw = i > 0 ? urow[i - 1] : mk<T2>(0, 0);
-    T2 us = j + 1 < nz ? urow[i + nx] : mk<T2>(0, 0);
-    T2 un = j > 0 ? urow[i - nx] : mk<T2>(0, 0);
-    T2 hx = cadd(cmul(ie, ue), cmul(iw, uw));
-    T2 hz = cadd(cmul(iZs, us), cmul(iZn, un));
-    return csub(csub(cmul(diag(i), uc), cmul(Zj, hx)), cmul(Xi, hz));
-  }
-};
-
-// y = Op x | b - Op x | x + w (b - Op x)/cc | w b / cc  on every block of a level.
-// One warp per row, two columns per lane in flight.
-template <typename T, bool CJ>
-__global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 6 : 3)
-k_field_op(LevelView<T> L, int mode, T w, const typename cplx<T>::t *__restrict__ x,
-           const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
-  typedef typename cplx<T>::t T2;
-  const TileDev t = L.tiles[blockIdx.x];
-  if (L.skip && L.skip[t.blk]) return;
-  const BlkDev bk = L.blks[t.blk];
-  const OpDev op = L.ops[bk.op];
-  const int j = t.row0 + (threadIdx.x >> 5);
-  if (j >= op.nz) return;
-  const RowOp<T, CJ> R(op, L.st, L.dg, L.dgi, j);
-  const long long row = bk.off + (long long)j * op.nx;
-  const T2 *xr = x ? x + row : nullptr;
-  const T2 *br = b ? b + row : nullptr;
-  T2 *yr = y + row;
-  const int lane = threadIdx.x & 31;
-  for (int i0 = lane; i0 < op.nx; i0 += 64) {
-    T2 out[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      int i = i0 + 32 * q;
-      if (i < op.nx) {
-        if (mode == FM_JACOBI0) {
-          out[q] = cscale(cmul(br[i], R.dinv(i)), w);
-        } else {
-          T2 ax = R.apply(xr, i);
-          if (mode == FM_APPLY) out[q] = ax;
-          else if (mode == FM_RESID) out[q] = csub(br[i], ax);
-          else out[q] = cadd(xr[i], cscale(cmul(csub(br[i], ax), R.dinv(i)), w));
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-      if (i0 + 32 * q < op.nx) yr[i0 + 32 * q] = out[q];
-  }
-}
-
 // L2-evict-last loads with a policy created once per thread.
 __device__ __forceinline__ float2 ld_keep_p(const float2 *p, unsigned long long pol) {
   float2 v;

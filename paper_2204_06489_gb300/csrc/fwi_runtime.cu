@@ -802,15 +802,12 @@ template <typename T>
 void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
                    typename cplx<T>::t *y, bool opA, int level) {
   LevelView<T> L = opA ? viewA<T>() : viewM<T>(level);
-  // the register-marching kernel on the fine levels, the direct one on small grids
-  if (L.n_strips > 0) {
-    const int grid = std::max(1, (L.n_strips + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
-    if (cj) launch_march_cj<T, true>(grid, st, L, mode, wj, x, b, y);
-    else launch_march_cj<T, false>(grid, st, L, mode, wj, x, b, y);
-  } else {
-    if (cj) k_field_op<T, true><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
-    else k_field_op<T, false><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, mode, wj, x, b, y);
-  }
+  // column strips exist on level 0 and on every other global level (< ls),
+  // the only levels this is called on
+  if (L.n_strips == 0) fail(FWI_E_INVAL, "internal: no column strips on a global multigrid level");
+  const int grid = (L.n_strips + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32);
+  if (cj) launch_march_cj<T, true>(grid, st, L, mode, wj, x, b, y);
+  else launch_march_cj<T, false>(grid, st, L, mode, wj, x, b, y);
   KCHECK();
 }
 
