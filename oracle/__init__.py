@@ -17,8 +17,9 @@ grid       padded grid, PML stretching functions, model embedding
 helmholtz  sparse operator assembly, sources, receivers
 fwi        forward modelling, data residual, misfit, adjoint gradient
 kkt        scaled KKT matvec / RHS, exact and inexact preconditioners, direct
-           references (real-form sparse KKT, dense normal equations)
-krylov     flexible GMRES in the real inner product, BiCGStab
+           references (real-form sparse KKT, dense normal equations), the
+           matrix-free normal operator of RSGN-CG (Sec. 3)
+krylov     flexible GMRES in the real inner product, BiCGStab, CG
 mg         geometric multigrid for the shifted operator (the inner block solver)
 newton     one Newton step and the frequency loop
 

@@ -184,6 +184,28 @@ class KKT:
             Js.append((Y[self.ci, :] * self.c[b][self.ci][:, None]).T)
         return Js
 
+    def normal_matvec(self, v: np.ndarray) -> np.ndarray:
+        """H v without forming J (Sec. 3, eq. normal_system_discrete_sum, the
+        form RSGN-CG uses): for every block one forward solve du = A'^{-1} P~ v
+        and one adjoint solve lm = A'^{-H} F du, then eps v + sum Re(P~^H lm)."""
+        out = self.eps * np.asarray(v, dtype=float).copy()
+        for b in range(self.B):
+            fi = self.prob.block_freq(b)
+            du = fwi.solve(self.prob, self.s_n, fi, self.P_apply(b, v), False)
+            lm = fwi.solve(self.prob, self.s_n, fi, self.Fd[b] * du, True)
+            out += self.PH_apply_re(b, lm)
+        return out
+
+    def normal_rhs(self) -> np.ndarray:
+        """g of the normal equations without forming J: one adjoint solve per
+        block, g = sum Re(P~^H A'^{-H} Q^T W^2 r) - eps s_n/gamma_ref."""
+        g = -self.eps * self.s_n / self.prob.gamma_ref if self.include_Ls_n else np.zeros(self.Nc)
+        b1 = fwi.scatter_weighted(self.prob, self.r)
+        for b in range(self.B):
+            lm = fwi.solve(self.prob, self.s_n, self.prob.block_freq(b), b1[b], True)
+            g = g + self.PH_apply_re(b, lm)
+        return g
+
     def normal_system(self):
         """(H, g) of the reduced Gauss-Newton system (Sec. 3, eq.
         normal_system_discrete2) in the scaled control: H = sum Re(J^H W^2 J) + eps I,

@@ -10,6 +10,10 @@ next, so the right-preconditioned *flexible* form (Saad 1993) is used; with a
 fixed linear preconditioner it reduces to right-preconditioned GMRES.  The
 inner product is the real one, <x, y> = x . y on the packed real vector.
 
+Conjugate gradients (Hestenes & Stiefel 1952) solve the reduced-space normal
+equations of Sec. 3 (RSGN-CG), whose matrix is symmetric positive definite for
+eps > 0.
+
 BiCGStab (van der Vorst 1992) with right preconditioning is the inner block
 solver of the inexact preconditioner; Sec. 7 mentions BiCGStab as a
 memory-lean alternative.  It works on complex vectors with the Hermitian inner
@@ -132,4 +136,30 @@ def bicgstab(apply_A, b: np.ndarray, precond=None, iters: int = 10, tol: float =
             break
         if om == 0.0:
             break
+    return x, hist
+
+
+def cg(apply_H, g: np.ndarray, tol: float = 1e-6, max_iter: int = 1000):
+    """Unpreconditioned conjugate gradients for H x = g, H symmetric positive
+    definite (real vectors), from x = 0, stopping when the recursively updated
+    residual satisfies ||r|| <= tol ||g||.  Returns (x, relres_history)."""
+    x = np.zeros_like(g)
+    r = g.copy()
+    p = r.copy()
+    gn = np.linalg.norm(g)
+    hist = []
+    if gn == 0.0:
+        return x, hist
+    rho = float(r @ r)
+    for _ in range(max_iter):
+        hp = apply_H(p)
+        alpha = rho / float(p @ hp)
+        x = x + alpha * p
+        r = r - alpha * hp
+        rho_new = float(r @ r)
+        hist.append(np.sqrt(rho_new) / gn)
+        if hist[-1] <= tol:
+            break
+        p = r + (rho_new / rho) * p
+        rho = rho_new
     return x, hist
