@@ -27,6 +27,6 @@ Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, a library routine, an invariant or brute force, except the
 multigrid V-cycle and the inner BiCGStab: the paper leaves the inner solver
 open (Sec. 5 names only "shifted Laplacian with multigrid"), so those two are
-the build's own design and their parity is "parity unpinned" beyond the
+a design of their own and their parity is "parity unpinned" beyond the
 convergence and linearity properties tested for them.
 """

@@ -11,7 +11,7 @@ sigma_max = 3 c ln(1/R) / (2L) (Collino & Tsogka 2001), time convention
 e^{-i omega t} so X = 1 + i sigma_x / omega.  The Dirichlet value sits on a
 ghost ring one node outside the padded grid.
 
-Multigrid levels (the build's inner solver, not in the paper) reuse the same
+Multigrid levels (of the inner solver chosen here; the paper has none) reuse the same
 continuous profile: level l has spacing h_l = 2^l h, first node at
 x0_l = (2^l - 1) h and n_l = floor(n_{l-1} / 2) nodes per direction, so coarse
 node I sits on fine node 2I+1 and the ghost nodes of every level coincide with

@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 The paper approximates A inside eq. precond_approx by an incomplete LU and
 names a shifted-Laplacian preconditioner with multigrid (Erlangga et al.) as
-the better choice (Sec. 5); it gives no multigrid details.  This is the
-build's design, stated here as plainly as possible so that the CUDA kernels can
+the better choice (Sec. 5); it gives no multigrid details.  The design below
+is this package's own choice, stated as plainly as possible so that the CUDA kernels can
 be compared with it element by element (parity unpinned beyond the linearity,
 fixed-point and convergence properties that the tests check):
 

@@ -1,5 +1,5 @@
-"""Properties of the oracle's multigrid preconditioner and inner solver (the
-build's own design of the shifted-Laplacian route named in Sec. 5; parity
+"""Properties of the oracle's multigrid preconditioner and inner solver (a
+design of its own for the shifted-Laplacian route named in Sec. 5; parity
 beyond these properties is unpinned).  CPU only."""
 import numpy as np
 
