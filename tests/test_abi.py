@@ -58,6 +58,18 @@ def test_create_rejects_bad_grids_and_survey(L):
     L.fwi_destroy(None)
 
 
+def test_solver_entry_points_reject_a_null_context(L):
+    """Host-side argument check of the stepping and solving calls: a NULL
+    context is FWI_E_INVAL before any device work."""
+    from paper_2204_06489_gb300 import api
+    st = api.Stats()
+    ds = np.zeros(4)
+    o = api.default_opts()
+    for name in ("fwi_newton_step", "fwi_rsgn_step", "fwi_kkt_solve"):
+        fn = getattr(L, name)
+        assert fn(None, C.byref(o), ds.ctypes.data_as(api.DP), 0, C.byref(st)) == api.FWI_E_INVAL, name
+
+
 def test_product_path_has_no_cpu_fallback():
     """The binding loads only the in-tree CUDA library and never imports the oracle."""
     import importlib
@@ -70,3 +82,4 @@ def test_product_path_has_no_cpu_fallback():
     assert after == before
     src = open(__import__("paper_2204_06489_gb300.api", fromlist=["x"]).__file__).read()
     assert "import oracle" not in src and "from oracle" not in src
+
