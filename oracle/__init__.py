@@ -25,8 +25,9 @@ newton     one Newton step and the frequency loop
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, a library routine, an invariant or brute force, except the
-multigrid V-cycle and the inner BiCGStab: the paper leaves the inner solver
-open (Sec. 5 names only "shifted Laplacian with multigrid"), so those two are
-a design of their own and their parity is "parity unpinned" beyond the
-convergence and linearity properties tested for them.
+multigrid cycle: the paper leaves the inner solver open (Sec. 5 names only
+"shifted Laplacian with multigrid"), so the cycle is a design of its own and
+its parity is "parity unpinned" beyond the convergence, linearity and
+fixed-point properties tested for it.  The inner BiCGStab is pinned iterate by
+iterate against scipy.sparse.linalg.bicgstab.
 """

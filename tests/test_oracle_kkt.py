@@ -199,3 +199,25 @@ def test_rsgn_cg_reaches_the_kkt_update():
     ds_kkt = K.unpack(K.solve_direct())[1]
     assert hist[-1] <= 1e-12
     assert np.linalg.norm(ds_cg - ds_kkt) <= 1e-8 * np.linalg.norm(ds_kkt)
+
+
+@pytest.mark.parametrize("with_precond", [False, True])
+def test_bicgstab_iterates_equal_scipy(with_precond):
+    """The inner solver's fixed-iteration form (k iterations from x = 0, shadow
+    residual b, right preconditioning) is van der Vorst's BiCGStab, iterate by
+    iterate: after k iterations it equals scipy.sparse.linalg.bicgstab stopped
+    at maxiter = k, on a complex non-Hermitian system, with and without a
+    (Jacobi) preconditioner."""
+    import scipy.sparse.linalg as spla
+    rng = np.random.default_rng(12)
+    n = 80
+    A = (np.eye(n) * (3 + 1j) + rng.standard_normal((n, n)) * 0.25
+         + 1j * rng.standard_normal((n, n)) * 0.15)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    Minv = np.diag(1 / np.diag(A))
+    pre = (lambda v: Minv @ v) if with_precond else None
+    Mop = spla.LinearOperator((n, n), matvec=lambda v: Minv @ v, dtype=complex) if with_precond else None
+    for k in (1, 2, 5, 9):
+        x, _ = krylov.bicgstab(lambda v: A @ v, b, pre, iters=k, tol=0.0)
+        xs, _ = spla.bicgstab(A, b, rtol=1e-300, atol=0.0, maxiter=k, M=Mop)
+        assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs), (k, np.linalg.norm(x - xs))
