@@ -112,7 +112,7 @@ def _peaks():
         return {}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of the level-0 stencil launches
+# dram__bytes_read.sum + dram__bytes_write.sum of the level-0 smoother launches
 # per algorithmic byte, from the ncu capture summarised under profiles/ (None
 # while the kernels have changed since the last capture).  The reported
 # traffic scales it by each timed launch's algorithmic bytes.
@@ -431,7 +431,7 @@ def main():
     for _ in range(args.warmup):
         step_device()
     torch.cuda.synchronize()
-    f.stencil_timer(1)          # live CUDA-event timing of the level-0 stencil kernel
+    f.stencil_timer(1)          # live CUDA-event timing of the level-0 smoother kernel
     launches0 = f._L.fwi_kernel_launches()
     clocks = Clocks(local)
     clocks.start()

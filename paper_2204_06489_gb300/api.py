@@ -304,7 +304,7 @@ class FWI:
         return ds, st.as_dict()
 
     def stencil_timer(self, enable: int):
-        """(ms, algorithmic bytes, launches) of the level-0 stencil kernel since
+        """(ms, algorithmic bytes, launches) of the level-0 two-sweep smoother kernel since
         the last reset; ``enable`` 1/0 resets and switches timing, -1 reads."""
         ms, by, n = C.c_double(), C.c_double(), C.c_longlong()
         self._check(self._L.fwi_stencil_timer(self._h, enable, C.byref(ms), C.byref(by), C.byref(n)))
