@@ -1373,24 +1373,14 @@ void Ctx::forward(const fwi_opts &o, fwi_stats *stats) {
   int nrec = (int)rec_node.size();
   q.alloc(std::max(1, nrec));
   r.alloc(std::max(1, nrec));
-  std::vector<double2> dh(std::max(1, nrec), make_double2(0, 0));
   bool have_d = true;
   for (auto &I : inst) have_d = have_d && I.has_data;
   DBuf<double2> dd;
   if (have_d && nrec) {
-    // gather observed data per entry on the device-side order (copy per instance)
-    std::vector<long long> src_idx(nrec);
+    // observed data in receiver-entry order (blocks in order; per block the
+    // source's receivers at the block's frequency): one copy per block
     dd.alloc(nrec);
     int e = 0;
-    for (int b = 0; b < B; ++b) {
-      Instance &I = inst[blk_inst[b]];
-      int k = blk_src[b], f = blk_freq[b];
-      for (int q2 = I.rec_off[k]; q2 < I.rec_off[k + 1]; ++q2, ++e) {
-        (void)f;
-      }
-    }
-    // device copy of each instance's data in entry order
-    e = 0;
     for (int b = 0; b < B; ++b) {
       Instance &I = inst[blk_inst[b]];
       int k = blk_src[b], f = blk_freq[b];
