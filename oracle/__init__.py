@@ -21,13 +21,16 @@ kkt        scaled KKT matvec / RHS, exact and inexact preconditioners, direct
            matrix-free normal operator of RSGN-CG (Sec. 3)
 krylov     flexible GMRES in the real inner product, BiCGStab, CG
 mg         geometric multigrid for the shifted operator (the inner block solver)
-newton     one Newton step and the frequency loop
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
-closed form, a library routine, an invariant or brute force, except the
-multigrid cycle: the paper leaves the inner solver open (Sec. 5 names only
-"shifted Laplacian with multigrid"), so the cycle is a design of its own and
-its parity is "parity unpinned" beyond the convergence, linearity and
-fixed-point properties tested for it.  The inner BiCGStab is pinned iterate by
-iterate against scipy.sparse.linalg.bicgstab.
+closed form, a library routine, an invariant or brute force.  The multigrid
+cycle (the paper leaves the inner solver open; Sec. 5 names only "shifted
+Laplacian with multigrid") is pinned by exact Fourier analysis: on grids
+without the layer, with constant gamma and 2^k - 1 nodes per side, the cycle
+applied to every sine mode equals its closed-form two-, three- and four-grid
+symbol (damped Jacobi, full weighting, bilinear interpolation, rediscretised
+coarse operators, V/W recursion); the coarse levels' layer profile is pinned
+by the positions of the coarse nodes on the fine profile.  The inner BiCGStab
+is pinned iterate by iterate against scipy.sparse.linalg.bicgstab, the
+coupling block P~ by finite differences of the forward data.
 """

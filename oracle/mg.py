@@ -6,8 +6,8 @@ The paper approximates A inside eq. precond_approx by an incomplete LU and
 names a shifted-Laplacian preconditioner with multigrid (Erlangga et al.) as
 the better choice (Sec. 5); it gives no multigrid details.  The design below
 is this package's own choice, stated as plainly as possible so that the CUDA kernels can
-be compared with it element by element (parity unpinned beyond the linearity,
-fixed-point and convergence properties that the tests check):
+be compared with it element by element; the tests pin it against the exact
+Fourier symbols of the cycle on constant-coefficient grids without the layer:
 
   * operator of level l: the h_l^2-scaled 5-point PML operator rediscretised
     on level l with omega^2 -> (1 + i beta) omega^2 (helmholtz.assemble with

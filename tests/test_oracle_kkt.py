@@ -7,6 +7,7 @@ from scipy.ndimage import gaussian_filter
 
 import fwi_inputs as FI
 from oracle import fwi, kkt, krylov
+from oracle import helmholtz as H
 
 
 def _micro(include=True, eps=1e-2, seed=0):
@@ -221,3 +222,92 @@ def test_bicgstab_iterates_equal_scipy(with_precond):
         x, _ = krylov.bicgstab(lambda v: A @ v, b, pre, iters=k, tol=0.0)
         xs, _ = spla.bicgstab(A, b, rtol=1e-300, atol=0.0, maxiter=k, M=Mop)
         assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs), (k, np.linalg.norm(x - xs))
+
+
+def _weighted_micro(seed=0, nx=21, nz=13, eps=1e-2, include=True):
+    """Micro workload whose data weights W are not all 1 (uniform in [0.5, 2])."""
+    wl = FI.micro_workload(seed=seed, nx=nx, nz=nz, n_rec=5)
+    wl.survey.rec_w = np.random.default_rng(100 + seed).uniform(0.5, 2.0, wl.survey.rec_w.shape)
+    prob = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    d = fwi.sample(prob, fwi.forward(prob, wl.gamma_true.ravel()))
+    return wl, prob, d, kkt.KKT(prob, wl.gamma_start.ravel(), d, eps, include_Ls_n=include)
+
+
+def test_coupling_block_by_finite_differences_of_the_data():
+    """The coupling P~_b = h^2 gamma_ref omega_b^2 diag(u_b) E of the scaled KKT
+    system (Sec. 3, eq. P; Sec. 4) is the derivative of the state equation with
+    respect to the scaled control: the linearised data J~_b ds~ = Q A'^{-1} P~_b ds~
+    must equal the central difference of the forward data,
+    (Q u(s + t gamma_ref ds~) - Q u(s - t gamma_ref ds~)) / 2t.  A wrong factor
+    (h^2, gamma_ref, omega^2), a conjugate or a sign in P~ fails this."""
+    wl, prob, d, K = _weighted_micro(nx=25, nz=15)
+    s0 = K.s_n
+    rng = np.random.default_rng(21)
+    dst = gaussian_filter(rng.standard_normal((wl.grid.nz, wl.grid.nx)), 2.0).ravel()
+    dst /= np.abs(dst).max()                       # ds~ = O(1): ds = gamma_ref ds~
+    t = 1e-4
+    qp = fwi.sample(prob, fwi.forward(prob, s0 + t * prob.gamma_ref * dst))
+    qm = fwi.sample(prob, fwi.forward(prob, s0 - t * prob.gamma_ref * dst))
+    Js = K.jacobian()
+    for b in range(K.B):
+        fd = (qp[b] - qm[b]) / (2 * t)
+        lin = Js[b] @ dst
+        du = fwi.solve(prob, s0, prob.block_freq(b), K.P_apply(b, dst))
+        q_lin = du[H.receiver_indices(wl.grid, wl.survey, prob.block_src(b))]
+        assert np.linalg.norm(lin - fd) <= 1e-6 * np.linalg.norm(fd), (b, np.linalg.norm(lin - fd) / np.linalg.norm(fd))
+        assert np.linalg.norm(q_lin - fd) <= 1e-6 * np.linalg.norm(fd)
+
+
+def test_weighted_gradient_matches_central_differences():
+    """W != 1 (Sec. 3: Phi = 1/2 ||W r||^2): the adjoint gradient, whose adjoint
+    source is Q^T W^T W r, against central differences of the weighted misfit."""
+    wl, prob, d, K = _weighted_micro(nx=25, nz=15)
+    s0 = K.s_n
+    phi, g = fwi.gradient(prob, s0, d)
+    for seed in range(3):
+        dirn = gaussian_filter(np.random.default_rng(seed).standard_normal((wl.grid.nz, wl.grid.nx)), 2.0).ravel()
+        dirn *= 0.01 * np.mean(s0) / np.abs(dirn).max()
+        fp = fwi.misfit(prob, fwi.residual(prob, fwi.forward(prob, s0 + dirn), d))
+        fm = fwi.misfit(prob, fwi.residual(prob, fwi.forward(prob, s0 - dirn), d))
+        an = float(np.dot(g, dirn))
+        assert abs((fp - fm) / 2 - an) <= 1e-3 * abs(an), (seed, (fp - fm) / 2, an)
+
+
+def test_weighted_misfit_and_gradient_scale_with_w_squared():
+    """Multiplying every weight by 3 multiplies the misfit and its gradient by 9
+    (W enters squared); a single W in place of W^T W would give 3."""
+    wl, prob, d, K = _weighted_micro()
+    s0 = K.s_n
+    phi1, g1 = fwi.gradient(prob, s0, d)
+    wl.survey.rec_w = 3.0 * wl.survey.rec_w
+    prob3 = fwi.Problem.create(wl.grid, wl.survey, wl.gamma_start)
+    phi3, g3 = fwi.gradient(prob3, s0, d)
+    assert abs(phi3 - 9 * phi1) <= 1e-12 * phi3
+    assert np.linalg.norm(g3 - 9 * g1) <= 1e-11 * np.linalg.norm(g3)
+    direct = 0.5 * sum(float(np.sum((w * np.abs(rb)) ** 2)) for w, rb in
+                       zip([wl.survey.rec_w[wl.survey.rec_offsets[prob.block_src(b)]:
+                                            wl.survey.rec_offsets[prob.block_src(b) + 1]]
+                            for b in range(prob.n_blocks)], K.r))
+    assert abs(phi3 - direct) <= 1e-12 * direct
+
+
+@pytest.mark.parametrize("include", [True, False])
+def test_weighted_kkt_update_is_the_weighted_least_squares_solution(include):
+    """With W != 1 the KKT update (Sec. 4) is the minimiser of the linearised
+    problem 1/2 ||W (r - J~ ds~)||^2 + eps/2 ||s_n/gamma_ref + ds~||^2 (Sec. 3),
+    computed here by numpy.linalg.lstsq on the stacked real system
+    [W J~; sqrt(eps) I] ds~ = [W r; -sqrt(eps) s_n/gamma_ref] (row scaling by W,
+    not the W^2 of the normal equations and of F = Q^T W^T W Q)."""
+    wl, prob, d, K = _weighted_micro(include=include)
+    rows, rhs = [], []
+    for b, J in enumerate(K.jacobian()):
+        w = H.receiver_weights(wl.survey, prob.block_src(b))
+        WJ, Wr = w[:, None] * J, w * K.r[b]
+        rows += [WJ.real, WJ.imag]
+        rhs += [Wr.real, Wr.imag]
+    se = np.sqrt(K.eps)
+    rows.append(se * np.eye(K.Nc))
+    rhs.append(-se * K.s_n / prob.gamma_ref if include else np.zeros(K.Nc))
+    ds_ls = np.linalg.lstsq(np.vstack(rows), np.concatenate(rhs), rcond=None)[0]
+    ds_kkt = K.unpack(K.solve_direct())[1]
+    assert np.linalg.norm(ds_kkt - ds_ls) <= 1e-8 * np.linalg.norm(ds_ls)

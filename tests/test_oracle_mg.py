@@ -1,7 +1,8 @@
 """Properties of the oracle's multigrid preconditioner and inner solver (a
-design of its own for the shifted-Laplacian route named in Sec. 5; the
-multigrid cycle's parity beyond these properties is unpinned, the BiCGStab
-iteration itself is pinned against scipy in test_oracle_kkt).  CPU only."""
+design of its own for the shifted-Laplacian route named in Sec. 5).  The
+cycle itself is pinned against its exact Fourier symbols in
+test_oracle_mg_fourier, the BiCGStab iteration against scipy in
+test_oracle_kkt.  CPU only."""
 import numpy as np
 
 import fwi_inputs as FI
