@@ -90,6 +90,11 @@ typedef struct {
                              doubled (up to 8x) after a sweep that gains < 20x [60]   */
   int max_fwd_refine;     /* cap on forward refinement sweeps                  [20]   */
   int use_graph;          /* replay the preconditioner from a CUDA graph       [1]    */
+  int arnoldi_fp64;       /* FGMRES inner products (orthogonalisation, norms) with
+                             FP64 products and sums; 0: FP32 runs of complex64
+                             products summed in FP64 (faster, less exact)       [1]    */
+  int check_orth;         /* measure max |I - V^T V| of every FGMRES basis into
+                             fwi_stats.orth_loss (diagnostics, costs extra dots) [0]   */
 } fwi_opts;
 
 typedef struct {
@@ -101,6 +106,7 @@ typedef struct {
   double misfit;          /* data misfit 1/2 sum |W r|^2 at the step's model (sum over instances) */
   double t_setup_ms, t_forward_ms, t_solve_ms;
   double fwd_rel_res;     /* final max_b ||f_b - A u_b|| / ||f_b|| of the forward / adjoint solve */
+  double orth_loss;       /* max |I - V^T V| over the FGMRES bases (with opts.check_orth), else 0 */
 } fwi_stats;
 
 /* Layout of the context's buffers (element counts). */
@@ -201,6 +207,20 @@ int fwi_newton_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_devic
 int fwi_rsgn_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device,
                   fwi_stats *stats);
 
+/* Largest eigenvalue of the Gauss-Newton matrix Re(J~^H W^T W J~) at the
+ * current models (Sec. 3, eq. normal_system_discrete2 without the eps I term,
+ * in the scaled control ds~ of fwi_kkt_solve; J~ = Q A'^{-1} P~), by `iters`
+ * power iterations from the constant vector: v_0 = 1/||1||,
+ * w = G v_{k-1}, lambda_k = v_{k-1}^T w, v_k = w / ||w||; *lambda =
+ * lambda_iters (a lower bound that rises towards the largest eigenvalue).
+ * Each iteration makes one forward and one adjoint refined solve of every
+ * block (opts->fwd_tol, opts->precision).  Needs fwi_forward.  With several
+ * instances the matrix is block diagonal over them.  Used for the rule
+ * eps = alpha * lambda_max that sets the regulariser from the data term.
+ * FWI_E_NOCONV if a block solve missed fwd_tol (lambda still written). */
+int fwi_normal_lambda_max(fwi_ctx *ctx, const fwi_opts *opts, int iters, double *lambda,
+                          fwi_stats *stats);
+
 /* ---- operator-level entry points (device buffers, for checks and tools) ----
  * x, y: device field buffers in the given precision (float2 or double2
  * elements, field layout).  The operators use the current models and, where
@@ -250,6 +270,9 @@ int fwi_mg_cycle(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, int
  *     get FWI_E_INVAL with the required size in fwi_last_error.
  *   - The first call on each device (with that device current) looks up the
  *     array's device address; make that first call before any stream capture.
+ *     The context's device (the device current at its first device use) must
+ *     be the current device; otherwise FWI_E_INVAL.
+ *   - Live stencil timing (fwi_stencil_timer) is suspended during the call.
  *   - Every call, on every context, shares the one array and leaves its
  *     contents behind; the cycle writes each buffer before reading it, so no
  *     clearing is needed.  Calls whose GPU work overlaps (different streams,
@@ -265,6 +288,11 @@ int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info);
  * (kernels replayed from a CUDA graph included).  Diagnostics only; the paper
  * has no counterpart. */
 unsigned long long fwi_kernel_launches(void);
+
+/* Number of cudaMalloc, cudaMallocHost, cudaFree and cudaFreeHost calls this
+ * library has made in this process so far.  Diagnostics (it lets a caller
+ * check that a call allocated nothing); the paper has no counterpart. */
+unsigned long long fwi_memory_calls(void);
 
 /* Live timing of the complex64 level-0 smoother kernel (two damped-Jacobi
  * sweeps of the shifted 5-point operator of Sec. 2 in one pass, every block):

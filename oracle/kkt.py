@@ -113,16 +113,22 @@ class KKT:
         b3 = np.zeros((self.B, self.N), dtype=np.complex128)
         return self.pack(b1, b2, b3)
 
-    def precond(self, v: np.ndarray, inner=None) -> np.ndarray:
+    def precond(self, v: np.ndarray, inner=None, inner_batch=None) -> np.ndarray:
         """z = P^{-1} v (eq. precond) or P~^{-1} v (eq. precond_approx) when
-        ``inner(b, rhs, adjoint)`` approximates A'^{-1} / A'^{-H}."""
+        ``inner(b, rhs, adjoint)`` approximates A'^{-1} / A'^{-H}.
+        ``inner_batch(rhs [B, N], adjoint) -> [B, N]`` may replace the loop of
+        per-block solves (the same solves, e.g. spread over processes)."""
         v1, v2, v3 = self.unpack(v)
-        if inner is None:
-            def inner(b, rhs, adjoint):
-                return fwi.solve(self.prob, self.s_n, self.prob.block_freq(b), rhs, adjoint)
-        zl = np.array([inner(b, v1[b], True) for b in range(self.B)])
+        if inner_batch is None:
+            if inner is None:
+                def inner(b, rhs, adjoint):
+                    return fwi.solve(self.prob, self.s_n, self.prob.block_freq(b), rhs, adjoint)
+
+            def inner_batch(rhs, adjoint):
+                return np.array([inner(b, rhs[b], adjoint) for b in range(self.B)])
+        zl = inner_batch(v1, True)
         zs = (v2 + sum(self.PH_apply_re(b, zl[b]) for b in range(self.B))) / self.eps
-        zu = np.array([inner(b, v3[b] + self.P_apply(b, zs), False) for b in range(self.B)])
+        zu = inner_batch(np.array([v3[b] + self.P_apply(b, zs) for b in range(self.B)]), False)
         return self.pack(zu, zs, zl)
 
     def relres(self, x: np.ndarray) -> float:
@@ -205,6 +211,20 @@ class KKT:
             lm = fwi.solve(self.prob, self.s_n, self.prob.block_freq(b), b1[b], True)
             g = g + self.PH_apply_re(b, lm)
         return g
+
+    def gn_lambda_max(self, iters: int):
+        """Largest eigenvalue of the Gauss-Newton matrix G = Re(J~^H W^T W J~)
+        (Sec. 3, eq. normal_system_discrete2 without eps I) by power iteration
+        from the constant vector: v_0 = 1/||1||; w = G v_{k-1} (matrix-free:
+        ``normal_matvec`` minus its eps v term); lambda_k = v_{k-1} . w;
+        v_k = w / ||w||.  Returns [lambda_1, ..., lambda_iters]."""
+        v = np.full(self.Nc, 1.0 / np.sqrt(self.Nc))
+        out = []
+        for _ in range(iters):
+            w = self.normal_matvec(v) - self.eps * v
+            out.append(float(v @ w))
+            v = w / np.linalg.norm(w)
+        return out
 
     def normal_system(self):
         """(H, g) of the reduced Gauss-Newton system (Sec. 3, eq.

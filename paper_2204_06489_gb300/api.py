@@ -47,14 +47,15 @@ class Opts(C.Structure):
                 ("inner_tol", C.c_double), ("mg_cycle", C.c_int), ("mg_wdepth", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("omega_jac", C.c_double), ("shift_beta", C.c_double), ("sigma_cap", C.c_double),
                 ("mg_levels", C.c_int), ("fwd_tol", C.c_double), ("fwd_iters", C.c_int),
-                ("max_fwd_refine", C.c_int), ("use_graph", C.c_int)]
+                ("max_fwd_refine", C.c_int), ("use_graph", C.c_int), ("arnoldi_fp64", C.c_int),
+                ("check_orth", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("refinements", C.c_int), ("fwd_sweeps", C.c_int),
                 ("inner_iters", C.c_longlong), ("rel_res", C.c_double), ("misfit", C.c_double),
                 ("t_setup_ms", C.c_double), ("t_forward_ms", C.c_double), ("t_solve_ms", C.c_double),
-                ("fwd_rel_res", C.c_double)]
+                ("fwd_rel_res", C.c_double), ("orth_loss", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -105,6 +106,7 @@ def load(build_if_missing: bool = False):
         "fwi_kkt_solve": (C.c_int, [P, C.POINTER(Opts), P, C.c_int, C.POINTER(Stats)]),
         "fwi_newton_step": (C.c_int, [P, C.POINTER(Opts), P, C.c_int, C.POINTER(Stats)]),
         "fwi_rsgn_step": (C.c_int, [P, C.POINTER(Opts), P, C.c_int, C.POINTER(Stats)]),
+        "fwi_normal_lambda_max": (C.c_int, [P, C.POINTER(Opts), C.c_int, DP, C.POINTER(Stats)]),
         "fwi_apply_helmholtz": (C.c_int, [P, P, P, C.c_int, C.c_int]),
         "fwi_apply_kkt": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
         "fwi_apply_precond": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
@@ -114,6 +116,7 @@ def load(build_if_missing: bool = False):
         "fwi_get_layout": (C.c_int, [P, C.POINTER(LayoutInfo)]),
         "fwi_last_error": (C.c_char_p, [P]),
         "fwi_kernel_launches": (C.c_ulonglong, []),
+        "fwi_memory_calls": (C.c_ulonglong, []),
         "fwi_stencil_timer": (C.c_int, [P, C.c_int, DP, DP, C.POINTER(C.c_longlong)]),
         "fwi_destroy": (None, [P]),
     }
@@ -302,6 +305,16 @@ class FWI:
                                    C.byref(st))
         self._check(rc, allow_noconv)
         return ds, st.as_dict()
+
+    def normal_lambda_max(self, opts: Optional[Opts] = None, iters: int = 10):
+        """Power-iteration estimate of the largest eigenvalue of the Gauss-Newton
+        matrix Re(J~^H W^T W J~) at the current models (needs ``forward``)."""
+        st = Stats()
+        lam = C.c_double()
+        rc = self._L.fwi_normal_lambda_max(self._h, C.byref(opts) if opts else None, int(iters), C.byref(lam),
+                                           C.byref(st))
+        self._check(rc)
+        return lam.value, st.as_dict()
 
     def stencil_timer(self, enable: int):
         """(ms, algorithmic bytes, launches) of the level-0 two-sweep smoother kernel since

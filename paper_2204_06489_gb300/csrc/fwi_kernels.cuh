@@ -1331,37 +1331,65 @@ __global__ void k_kkt_F(int n, const long long *node, const double *w2, const ty
 }
 
 // Coupling reduction over the blocks of each instance, at every core node c:
-//   acc_c = sum_b cf_b Re(conj(u_b) lm_b)   (FP64, fixed order)
+//   acc_c = sum_b cf_b Re(conj(u_b) lm_b)   (fixed order)
 // mode 0 (KKT row 2):      out_c = eps * ds_c - acc_c
 // mode 1 (preconditioner): out_c = (v_c + acc_c) / eps
 // mode 2 (gradient):       out_c = -acc_c   (cf_b = omega_b^2 h^2, lm = lambda')
 // mode 3 (normal matrix):  out_c = eps * v_c + acc_c
-// Block partitions: threadIdx.y takes blocks b = blk0 + ty, ty + 4, ...; the 4
-// partial sums are combined in a fixed order.
+// A thread owns one core node and the blocks b = blk0 + ty + 4 q (threadIdx.y
+// = ty, four partitions combined in a fixed order).  Every block of an
+// instance has the same padded grid, so the node's element in block b is
+// base + (b - blk0) Nx Nz: no per-block table reads, and four blocks' loads
+// are issued before their products are summed.  complex64 data accumulate
+// the products in FP32 runs of at most DOT_RUN blocks, each run added into an
+// FP64 total; complex128 accumulates in FP64.
+#define CPL_ROWS 4
 template <typename T, typename TO>
-__global__ void k_coupling_reduce(const InstDev *inst, int Nx_stride_unused, const long long *blk_off,
-                                  const int *blk_Nx, const double *cf, const typename cplx<T>::t *__restrict__ u,
-                                  const typename cplx<T>::t *__restrict__ lm, const TO *__restrict__ v,
-                                  double eps, int mode, TO *__restrict__ out) {
+__global__ void __launch_bounds__(128 * CPL_ROWS)
+k_coupling_reduce(const InstDev *inst, const long long *blk_off, const double *cf,
+                  const typename cplx<T>::t *__restrict__ u, const typename cplx<T>::t *__restrict__ lm,
+                  const TO *__restrict__ v, double eps, int mode, TO *__restrict__ out) {
+  typedef typename cplx<T>::t T2;
   const InstDev in = inst[blockIdx.y];
-  long long nc = (long long)in.nx * in.nz;
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  __shared__ double part[4][128];
-  double acc = 0.0;
+  const long long nc = (long long)in.nx * in.nz;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  __shared__ double part[CPL_ROWS][128];
+  double tot = 0.0;
   if (c < nc) {
-    int cz = (int)(c / in.nx), cx = (int)(c - (long long)cz * in.nx);
-    for (int b = in.blk0 + threadIdx.y; b < in.blk1; b += 4) {
-      int Nx = blk_Nx[b];
-      long long k = blk_off[b] + (long long)(cz + in.npml) * Nx + (cx + in.npml);
-      double2 uu = to_d2(u[k]), ll = to_d2(lm[k]);
-      acc += cf[b] * (uu.x * ll.x + uu.y * ll.y);
+    const int Nx = in.nx + 2 * in.npml, Nz = in.nz + 2 * in.npml;
+    const long long F = (long long)Nx * Nz;
+    const int cz = (int)(c / in.nx), cx = (int)(c - (long long)cz * in.nx);
+    const long long base = blk_off[in.blk0] + (long long)(cz + in.npml) * Nx + (cx + in.npml);
+    T run = 0;
+    int cnt = 0;
+    int b = in.blk0 + threadIdx.y;
+    for (; b + 3 * CPL_ROWS < in.blk1; b += 4 * CPL_ROWS) {
+      T2 uu[4], ll[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long k = base + (long long)(b + q * CPL_ROWS - in.blk0) * F;
+        uu[q] = u[k];
+        ll[q] = lm[k];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        run = tfma((T)cf[b + q * CPL_ROWS], tfma(uu[q].x, ll[q].x, uu[q].y * ll[q].y), run);
+      if (sizeof(T) == 4 && (cnt += 4) >= DOT_RUN) { tot += (double)run; run = 0; cnt = 0; }
     }
+    for (; b < in.blk1; b += CPL_ROWS) {
+      const long long k = base + (long long)(b - in.blk0) * F;
+      const T2 uu = u[k], ll = lm[k];
+      run = tfma((T)cf[b], tfma(uu.x, ll.x, uu.y * ll.y), run);
+    }
+    tot += (double)run;
   }
-  part[threadIdx.y][threadIdx.x] = acc;
+  part[threadIdx.y][threadIdx.x] = tot;
   __syncthreads();
   if (threadIdx.y == 0 && c < nc) {
-    double s = ((part[0][threadIdx.x] + part[1][threadIdx.x]) + part[2][threadIdx.x]) + part[3][threadIdx.x];
-    long long o = in.ctrl + c;
+    double s = part[0][threadIdx.x];
+#pragma unroll
+    for (int q = 1; q < CPL_ROWS; ++q) s += part[q][threadIdx.x];
+    const long long o = in.ctrl + c;
     double r;
     if (mode == 0) r = eps * (double)v[o] - s;
     else if (mode == 1) r = ((double)v[o] + s) / eps;
@@ -1477,12 +1505,15 @@ __global__ void k_update_model(const InstDev *inst, double *const *s_core, const
 #define FLAT_THREADS 256
 #define MD_CHUNK 8
 
-// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv.  complex64 data: each
-// thread accumulates FP32 runs of MD_RUN products per vector (two independent
-// chains of interleaved elements) and adds each run into an FP64 total; FP64
-// across threads.  complex128: FP64 throughout.  Fixed grid, deterministic.
+// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv, deterministic (fixed
+// grid and order).  EXACT = true (the Arnoldi inner products): every product
+// is formed and summed in FP64 (the product of two floats is exact in double),
+// so the orthogonalisation of complex64 vectors runs in FP64 arithmetic.
+// EXACT = false: complex64 data accumulate FP32 runs of MD_RUN products per
+// vector (two independent chains of interleaved elements) and add each run
+// into an FP64 total.  complex128 data are FP64 throughout either way.
 #define MD_RUN 64
-template <typename T>
+template <typename T, bool EXACT = false>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, double *partial) {
   double tot[MD_CHUNK];
@@ -1495,23 +1526,32 @@ k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, doub
   const long long stride = (long long)gridDim.x * FLAT_THREADS;
   int cnt = 0;
   long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x;
-  for (; i + stride < n; i += 2 * stride) {
-    const T wa = w[i], wb = w[i + stride];
-#pragma unroll
-    for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) { ra[v] = tfma(vp[v][i], wa, ra[v]); rb[v] = tfma(vp[v][i + stride], wb, rb[v]); }
-    if (sizeof(T) == 4 && (cnt += 2) >= MD_RUN) {
+  if (EXACT && sizeof(T) == 4) {
+    for (; i < n; i += stride) {
+      const double wa = (double)w[i];
 #pragma unroll
       for (int v = 0; v < MD_CHUNK; ++v)
-        if (v < nv) { tot[v] += (double)(ra[v] + rb[v]); ra[v] = 0; rb[v] = 0; }
-      cnt = 0;
+        if (v < nv) tot[v] = tfma((double)vp[v][i], wa, tot[v]);
     }
-  }
-  if (i < n) {
-    const T wa = w[i];
+  } else {
+    for (; i + stride < n; i += 2 * stride) {
+      const T wa = w[i], wb = w[i + stride];
 #pragma unroll
-    for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) ra[v] = tfma(vp[v][i], wa, ra[v]);
+      for (int v = 0; v < MD_CHUNK; ++v)
+        if (v < nv) { ra[v] = tfma(vp[v][i], wa, ra[v]); rb[v] = tfma(vp[v][i + stride], wb, rb[v]); }
+      if (sizeof(T) == 4 && (cnt += 2) >= MD_RUN) {
+#pragma unroll
+        for (int v = 0; v < MD_CHUNK; ++v)
+          if (v < nv) { tot[v] += (double)(ra[v] + rb[v]); ra[v] = 0; rb[v] = 0; }
+        cnt = 0;
+      }
+    }
+    if (i < n) {
+      const T wa = w[i];
+#pragma unroll
+      for (int v = 0; v < MD_CHUNK; ++v)
+        if (v < nv) ra[v] = tfma(vp[v][i], wa, ra[v]);
+    }
   }
   __shared__ double red[MD_CHUNK][FLAT_THREADS / 32];
 #pragma unroll
@@ -1558,17 +1598,21 @@ k_multi_axpy(long long n, int nv, const T *const *V, const double *coef, double 
   }
 }
 
-// partial[blockIdx.x] = sum x[i] y[i] (run accumulation per thread, FP64
-// across threads, fixed grid)
-template <typename T>
+// partial[blockIdx.x] = sum x[i] y[i], FP64 across threads, fixed grid.  EXACT:
+// products and sums in FP64; else FP32 runs of DOT_RUN for float data.
+template <typename T, bool EXACT = false>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_dot2(long long n, const T *__restrict__ x, const T *__restrict__ y, double *partial) {
   double tot = 0.0;
   T run = 0;
   int cnt = 0;
   for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
-    run = tfma(x[i], y[i], run);
-    if (sizeof(T) == 4 && ++cnt == DOT_RUN) { tot += run; run = 0; cnt = 0; }
+    if (EXACT) {
+      tot = tfma((double)x[i], (double)y[i], tot);
+    } else {
+      run = tfma(x[i], y[i], run);
+      if (sizeof(T) == 4 && ++cnt == DOT_RUN) { tot += run; run = 0; cnt = 0; }
+    }
   }
   double acc = tot + (double)run;
   __shared__ double red[FLAT_THREADS / 32];

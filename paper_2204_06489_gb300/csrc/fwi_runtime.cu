@@ -45,6 +45,10 @@ static std::atomic<unsigned long long> g_launches{0};
 
 static void fail(int code, const std::string &m) { throw Err{code, m}; }
 
+// Every cudaMalloc / cudaMallocHost / cudaFree / cudaFreeHost the library makes
+// (diagnostics: fwi_memory_calls).
+static std::atomic<unsigned long long> g_memcalls{0};
+
 template <typename T> struct DBuf {
   T *p = nullptr;
   size_t n = 0;
@@ -58,7 +62,7 @@ template <typename T> struct DBuf {
   }
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) { cudaFree(p); g_memcalls.fetch_add(1); }
     p = nullptr;
     n = 0;
   }
@@ -67,6 +71,7 @@ template <typename T> struct DBuf {
     release();
     if (count == 0) return;
     cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+    g_memcalls.fetch_add(1);
     if (e != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
@@ -221,6 +226,8 @@ struct Ctx {
   // live timing of the level-0 stencil kernel (k_field_op): event pairs around
   // direct launches on this context's stream, with the launch's algorithmic bytes
   int timer_on = 0;
+  bool timer_blocked = false;      // set by calls that must not allocate (no timed launches)
+  int dev = -1;                    // CUDA device of the context (recorded at first device use)
   std::vector<cudaEvent_t> ev_a, ev_b;
   std::vector<double> ev_bytes;    // bytes per processed node of each timed launch
   DBuf<unsigned long long> ev_work; // nodes processed by each timed launch (device counters)
@@ -248,8 +255,8 @@ struct Ctx {
   ~Ctx() {
     for (auto e : ev_a) cudaEventDestroy(e);
     for (auto e : ev_b) cudaEventDestroy(e);
-    if (pin) cudaFreeHost(pin);
-    if (pinflag) cudaFreeHost(pinflag);
+    if (pin) { cudaFreeHost(pin); g_memcalls.fetch_add(1); }
+    if (pinflag) { cudaFreeHost(pinflag); g_memcalls.fetch_add(1); }
     if (own_stream && st) cudaStreamDestroy(st);
   }
 
@@ -268,6 +275,7 @@ struct Ctx {
   int gradient(const fwi_opts &o, double *misfit_out, double *grad, int on_device, fwi_stats *stats);
   int newton_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats);
   int rsgn_solve(const fwi_opts &o, fwi_stats *stats);
+  int normal_lambda_max(const fwi_opts &o, int iters, double *lambda, fwi_stats *stats);
   int rsgn_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats);
   void apply_update(double *ds, int on_device);
   void write_ctrl(const double *src_ctrl_dev, double *dst, int on_device, const double *fac);
@@ -302,7 +310,9 @@ struct Ctx {
                                          const typename cplx<T>::t *u);
   template <typename T> int fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi_opts &o,
                                    int *iters, long long *inner, const typename cplx<T>::t *u);
-  template <typename T> void multidot(long long n, int nv, T *const *dV, const T *w, double *out, int acc);
+  template <typename T> void multidot(long long n, int nv, T *const *dV, const T *w, double *out, int acc,
+                                      bool exact);
+  double orth_loss = 0.0;   // max |I - V^T V| of the FGMRES bases of the last KKT solve (check_orth)
   void forward(const fwi_opts &o, fwi_stats *stats);
   template <typename T> int refined_solve(const double2 *rhs, double2 *x, int cj, const fwi_opts &o,
                                           fwi_stats *stats);
@@ -376,6 +386,7 @@ static int auto_levels(int Nx, int Nz, int max_nodes = 256, int min_dim = 3) {
 
 void Ctx::build_layout() {
   if (layout_ok) return;
+  if (dev < 0) CK(cudaGetDevice(&dev));
   if (!st) {
     // the legacy default stream cannot be captured into a CUDA graph: use a
     // private blocking stream (it still orders with the legacy default stream)
@@ -472,6 +483,7 @@ void Ctx::build_layout() {
   if (!pin) {
     CK(cudaMallocHost((void **)&pin, 64 * sizeof(double)));
     CK(cudaMallocHost((void **)&pinflag, 4 * sizeof(int)));
+    g_memcalls.fetch_add(2);
   }
   layout_ok = true;
   hier_key.clear();
@@ -816,7 +828,7 @@ void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const t
 // kernel counts the nodes it processed into L.work).
 template <typename T>
 bool Ctx::timer_begin(int level, LevelView<T> &L) {
-  if (!timer_on || level != 0 || sizeof(T) != 4) return false;
+  if (!timer_on || timer_blocked || level != 0 || sizeof(T) != 4) return false;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(st, &cs));
   if (cs != cudaStreamCaptureStatusNone) return false;
@@ -1100,7 +1112,7 @@ void Ctx::kkt_matvec(const T *xi, T *y, double eps, const typename cplx<T>::t *u
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
   dim3 g((unsigned)((mx + 127) / 128), (unsigned)inst.size());
-  k_coupling_reduce<T, T><<<g, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfK.p, u, lm, ds, eps, 0, ys);
+  k_coupling_reduce<T, T><<<g, dim3(128, CPL_ROWS), 0, st>>>(d_inst.p, d_blk_off.p, cfK.p, u, lm, ds, eps, 0, ys);
   KCHECK();
 }
 
@@ -1123,7 +1135,7 @@ void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count, const t
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
   dim3 g((unsigned)((mx + 127) / 128), (unsigned)inst.size());
-  k_coupling_reduce<T, T><<<g, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfK.p, u, zl, v2, o.eps, 1, zs);
+  k_coupling_reduce<T, T><<<g, dim3(128, CPL_ROWS), 0, st>>>(d_inst.p, d_blk_off.p, cfK.p, u, zl, v2, o.eps, 1, zs);
   KCHECK();
   // z_u = A'^{-1} (v3 + P~ z_s)
   LevelView<T> L = viewA<T>();
@@ -1169,11 +1181,12 @@ void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, con
 }
 
 template <typename T>
-void Ctx::multidot(long long n, int nv, T *const *dV, const T *wv, double *out, int acc) {
+void Ctx::multidot(long long n, int nv, T *const *dV, const T *wv, double *out, int acc, bool exact) {
   Work<T> &w = work<T>();
   for (int c0 = 0; c0 < nv; c0 += MD_CHUNK) {
     int c = std::min(MD_CHUNK, nv - c0);
-    k_multidot<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
+    if (exact) k_multidot<T, true><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
+    else k_multidot<T, false><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
     KCHECK();
     k_reduce_partials<<<c, 32, 0, st>>>(c, FLAT_BLOCKS, w.partial_flat.p, out + c0, acc);
     KCHECK();
@@ -1182,8 +1195,10 @@ void Ctx::multidot(long long n, int nv, T *const *dV, const T *wv, double *out, 
 
 // ||x||^2 or x.y over a flat array into *out (FP64, deterministic).
 template <typename T>
-static void flat_dot(cudaStream_t st, long long n, const T *x, const T *y, double *partial, double *out) {
-  k_dot2<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
+static void flat_dot(cudaStream_t st, long long n, const T *x, const T *y, double *partial, double *out,
+                     bool exact = false) {
+  if (exact) k_dot2<T, true><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
+  else k_dot2<T, false><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
   KCHECK();
   k_reduce_partials<<<1, 32, 0, st>>>(1, FLAT_BLOCKS, partial, out, 0);
   KCHECK();
@@ -1203,7 +1218,8 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
   T *const *dV = w.dptrV.p;
   T *const *dZ = w.dptrZ.p;
   CK(cudaMemsetAsync(x, 0, n * sizeof(T), st));
-  flat_dot<T>(st, n, rhs, rhs, w.partial_flat.p, w.scal.p);
+  const bool exact = o.arnoldi_fp64 != 0;
+  flat_dot<T>(st, n, rhs, rhs, w.partial_flat.p, w.scal.p, exact);
   CK(cudaMemcpyAsync(pin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
   sync();
   const double bnorm = std::sqrt(pin[0]);
@@ -1228,19 +1244,19 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
       precond_any<T>(vj, zj, o, inner, u);
       kkt_matvec<T>(zj, wv, eps, u);
       // classical Gram-Schmidt, twice
-      multidot<T>(n, j + 1, dV, wv, w.hcol.p, 0);
+      multidot<T>(n, j + 1, dV, wv, w.hcol.p, 0, exact);
       for (int c0 = 0; c0 < j + 1; c0 += MD_CHUNK)
         k_multi_axpy<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, std::min(MD_CHUNK, j + 1 - c0), dV + c0,
                                                               w.hcol.p + c0, -1.0, wv);
       KCHECK();
-      multidot<T>(n, j + 1, dV, wv, w.hsum.p, 0);
+      multidot<T>(n, j + 1, dV, wv, w.hsum.p, 0, exact);
       for (int c0 = 0; c0 < j + 1; c0 += MD_CHUNK)
         k_multi_axpy<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, std::min(MD_CHUNK, j + 1 - c0), dV + c0,
                                                               w.hsum.p + c0, -1.0, wv);
       KCHECK();
       k_dadd<<<1, 64, 0, st>>>(j + 1, w.hcol.p, w.hsum.p);
       KCHECK();
-      flat_dot<T>(st, n, wv, wv, w.partial_flat.p, w.scal.p + 2);
+      flat_dot<T>(st, n, wv, wv, w.partial_flat.p, w.scal.p + 2, exact);
       k_givens<<<1, 1, 0, st>>>(j, m, w.H.p, w.cs.p, w.sn.p, w.g.p, w.hcol.p, w.scal.p + 2, w.scal.p + 3,
                                 w.scal.p + 4);
       KCHECK();
@@ -1252,6 +1268,17 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
       k = j + 1;
       if (!std::isfinite(pin[0])) fail(FWI_E_NUMERIC, "non-finite residual in FGMRES");
       if (pin[0] / bnorm <= tol) { conv = true; break; }
+    }
+    if (o.check_orth && k > 0) {
+      // loss of orthogonality of this cycle's basis V_0 .. V_k: max |delta_ij - V_i . V_j|
+      // (FP64 products; diagnostics only, one multi-dot per basis vector)
+      std::vector<double> hh(k + 1);
+      for (int jj = 0; jj <= k; ++jj) {
+        multidot<T>(n, jj + 1, dV, w.V.p + (size_t)jj * w.ld, w.hsum.p, 0, true);
+        CK(cudaMemcpyAsync(hh.data(), w.hsum.p, (jj + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+        sync();
+        for (int ii = 0; ii <= jj; ++ii) orth_loss = std::max(orth_loss, std::fabs((ii == jj ? 1.0 : 0.0) - hh[ii]));
+      }
     }
     k_backsub<<<1, 1, 0, st>>>(k, m, w.H.p, w.g.p, w.y.p);
     KCHECK();
@@ -1265,7 +1292,7 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
     k_axpby<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, 1.0, rhs, -1.0, w.tmp.p);
     KCHECK();
     r = w.tmp.p;
-    flat_dot<T>(st, n, r, r, w.partial_flat.p, w.scal.p);
+    flat_dot<T>(st, n, r, r, w.partial_flat.p, w.scal.p, exact);
     CK(cudaMemcpyAsync(pin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
     sync();
     beta = std::sqrt(pin[0]);
@@ -1506,6 +1533,7 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
   long long inner = 0;
   double worst = 0.0;
   int status = FWI_E_NOCONV;
+  orth_loss = 0.0;
   for (;;) {
     inst_norms(rho_k64.p, rn);
     worst = 0.0;
@@ -1551,6 +1579,7 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
     stats->refinements += sweeps;
     stats->inner_iters += inner;
     stats->rel_res = worst;
+    stats->orth_loss = orth_loss;
     stats->t_solve_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return status;
@@ -1577,7 +1606,7 @@ int Ctx::gradient(const fwi_opts &o, double *misfit_out, double *grad, int on_de
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
   dim3 gr((unsigned)((mx + 127) / 128), (unsigned)inst.size());
-  k_coupling_reduce<double, double><<<gr, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfG.p, u64.p,
+  k_coupling_reduce<double, double><<<gr, dim3(128, CPL_ROWS), 0, st>>>(d_inst.p, d_blk_off.p, cfG.p, u64.p,
                                                                  lam.p, nullptr, 0.0, 2, target);
   KCHECK();
   if (!on_device) CK(cudaMemcpyAsync(grad, g.p, Nc * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1623,6 +1652,82 @@ void Ctx::apply_update(double *ds, int on_device) {
   have_fwd = false;
 }
 
+// The matrix-free Gauss-Newton normal operator of the scaled control (Sec. 3,
+// eq. normal_system_discrete_sum):
+//   H~ v = eps v + Re(P~^H A'^{-H} F A'^{-1} P~ v),  F = Q^T W^T W Q,
+// one forward and one adjoint FP64-refined block solve of every block per
+// product (complex64 or complex128 inner solves, opts.fwd_tol), and the
+// right-hand side of the normal equations.  Used by RSGN-CG and by the
+// power iteration for the largest eigenvalue of Re(J~^H W^T W J~).
+struct NormalOp {
+  Ctx &c;
+  const fwi_opts &o;
+  fwi_stats *stats;
+  long long nc;
+  dim3 gr;
+  DBuf<double2> fa, fb, zero, qv, rdummy;
+  DBuf<double> part;
+  int solve_rc = FWI_OK;
+  NormalOp(Ctx &cc, const fwi_opts &oo, fwi_stats *ss) : c(cc), o(oo), stats(ss), nc(cc.Nc) {
+    fa.alloc(c.F0); fb.alloc(c.F0); zero.alloc(c.F0);
+    zero.zero(c.st);
+    part.alloc(FLAT_BLOCKS);
+    const int nrec = (int)c.rec_node.size();
+    qv.alloc(std::max(nrec, 1)); rdummy.alloc(std::max(nrec, 1));
+    long long mx = 0;
+    for (auto &I : c.inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
+    gr = dim3((unsigned)((mx + 127) / 128), (unsigned)c.inst.size());
+  }
+  void solve(const double2 *rhs, double2 *sol, int cj) {
+    int rc = o.precision == FWI_C128 ? c.refined_solve<double>(rhs, sol, cj, o, stats)
+                                     : c.refined_solve<float>(rhs, sol, cj, o, stats);
+    if (rc != FWI_OK) solve_rc = rc;
+  }
+  // out = eps * v + Re(P~^H lambda)  (per core node, fixed block order)
+  void couple(const double2 *lam, const double *v, double eps, double *out) {
+    cudaStream_t st = c.st;
+    k_coupling_reduce<double, double><<<gr, dim3(128, CPL_ROWS), 0, st>>>(c.d_inst.p, c.d_blk_off.p, c.cfK.p,
+                                                                        c.u64.p, lam, v, eps, 3, out);
+    KCHECK();
+  }
+  // lambda = A'^{-H} Q^T W^T W (values at the receivers q)
+  void adjoint_of_receivers(const double2 *q, double2 *lam) {
+    cudaStream_t st = c.st;
+    CK(cudaMemsetAsync(fa.p, 0, c.F0 * sizeof(double2), st));
+    if (c.n_unique)
+      k_rec_scatter<<<grid_for(c.n_unique, 128, 1 << 20), 128, 0, st>>>(c.n_unique, c.d_unode.p, c.d_uoff.p,
+                                                                        c.d_uidx.p, c.d_rec_w.p, q, fa.p);
+    KCHECK();
+    solve(fa.p, lam, 1);
+  }
+  // out = H~ v (eps = o.eps) or the Gauss-Newton part alone (eps = 0)
+  void apply(const double *v, double eps, double *out) {
+    cudaStream_t st = c.st;
+    LevelView<double> L64 = c.viewA<double>();
+    k_coupling_scatter<double><<<L64.n_tiles, TILE_THREADS, 0, st>>>(L64, c.d_inst.p, c.cfK.p, c.u64.p, zero.p, v,
+                                                                     fb.p);
+    KCHECK();
+    solve(fb.p, fa.p, 0);                                  // du = A'^{-1} P~ v
+    const int nrec = (int)c.rec_node.size();
+    if (nrec)
+      k_rec_residual<<<grid_for(nrec, 128, 1 << 20), 128, 0, st>>>(nrec, c.d_rec_node.p, fa.p, nullptr, qv.p,
+                                                                   rdummy.p, 0);
+    KCHECK();
+    adjoint_of_receivers(qv.p, fb.p);                      // lambda = A'^{-H} F du
+    couple(fb.p, v, eps, out);
+  }
+  double dot(const double *a, const double *b) {
+    k_dot2<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, c.st>>>(nc, a, b, part.p);
+    KCHECK();
+    std::vector<double> h(FLAT_BLOCKS);
+    CK(cudaMemcpyAsync(h.data(), part.p, FLAT_BLOCKS * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    double acc = 0.0;
+    for (double v : h) acc += v;
+    return acc;
+  }
+};
+
 // Reduced-space Gauss-Newton (Sec. 3, eq. normal_system_discrete_sum) by
 // conjugate gradients, on the same scaled variables as the KKT solve:
 //   (eps I + Re(P~^H A'^{-H} F A'^{-1} P~)) ds~ = b_s + Re(P~^H A'^{-H} Q^T W^T W r),
@@ -1643,61 +1748,11 @@ int Ctx::rsgn_solve(const fwi_opts &o, fwi_stats *stats) {
   xi64.alloc(nkkt);
   CK(cudaMemsetAsync(xi64.p, 0, nkkt * sizeof(double), st));
   double *x = xi64.p + 4 * F0;             // ds~ (the KKT layout's control slot)
-  DBuf<double> g, rr, p, hp, bs, part;
-  g.alloc(nc); rr.alloc(nc); p.alloc(nc); hp.alloc(nc); bs.alloc(nc); part.alloc(FLAT_BLOCKS);
-  DBuf<double2> fa, fb, zero;
-  fa.alloc(F0); fb.alloc(F0); zero.alloc(F0);
-  zero.zero(st);
+  DBuf<double> g, rr, p, hp, bs;
+  g.alloc(nc); rr.alloc(nc); p.alloc(nc); hp.alloc(nc); bs.alloc(nc);
+  NormalOp N(*this, o, stats);
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
-  const dim3 gr((unsigned)((mx + 127) / 128), (unsigned)inst.size());
-  LevelView<double> L64 = viewA<double>();
-  int solve_rc = FWI_OK;
-  auto solve = [&](const double2 *rhs, double2 *sol, int cj) {
-    int rc = o.precision == FWI_C128 ? refined_solve<double>(rhs, sol, cj, o, stats)
-                                     : refined_solve<float>(rhs, sol, cj, o, stats);
-    if (rc != FWI_OK) solve_rc = rc;
-  };
-  // out = eps * v + Re(P~^H lambda)  (per core node, fixed block order)
-  auto couple = [&](const double2 *lam, const double *v, double eps, double *out) {
-    k_coupling_reduce<double, double><<<gr, dim3(128, 4), 0, st>>>(d_inst.p, 0, d_blk_off.p, d_blk_Nx.p, cfK.p, u64.p,
-                                                                   lam, v, eps, 3, out);
-    KCHECK();
-  };
-  // lambda = A'^{-H} Q^T W^T W (values at the receivers q)
-  auto adjoint_of_receivers = [&](const double2 *q, double2 *lam) {
-    CK(cudaMemsetAsync(fa.p, 0, F0 * sizeof(double2), st));
-    if (n_unique)
-      k_rec_scatter<<<grid_for(n_unique, 128, 1 << 20), 128, 0, st>>>(n_unique, d_unode.p, d_uoff.p, d_uidx.p,
-                                                                      d_rec_w.p, q, fa.p);
-    KCHECK();
-    solve(fa.p, lam, 1);
-  };
-  auto dot = [&](const double *a, const double *b) {
-    k_dot2<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, a, b, part.p);
-    KCHECK();
-    std::vector<double> h(FLAT_BLOCKS);
-    CK(cudaMemcpyAsync(h.data(), part.p, FLAT_BLOCKS * sizeof(double), cudaMemcpyDeviceToHost, st));
-    sync();
-    double acc = 0.0;
-    for (double v : h) acc += v;
-    return acc;
-  };
-  const int nrec = (int)rec_node.size();
-  DBuf<double2> qv, rdummy;
-  qv.alloc(std::max(nrec, 1)); rdummy.alloc(std::max(nrec, 1));
-  // H~ v
-  auto normal = [&](const double *v, double *out) {
-    k_coupling_scatter<double><<<L64.n_tiles, TILE_THREADS, 0, st>>>(L64, d_inst.p, cfK.p, u64.p, zero.p, v, fb.p);
-    KCHECK();
-    solve(fb.p, fa.p, 0);                                  // du = A'^{-1} P~ v
-    if (nrec)
-      k_rec_residual<<<grid_for(nrec, 128, 1 << 20), 128, 0, st>>>(nrec, d_rec_node.p, fa.p, nullptr, qv.p,
-                                                                   rdummy.p, 0);
-    KCHECK();
-    adjoint_of_receivers(qv.p, fb.p);                      // lambda = A'^{-H} F du
-    couple(fb.p, v, o.eps, out);
-  };
   // right-hand side g = b_s + Re(P~^H A'^{-H} Q^T W^T W r)
   {
     std::vector<const double *> sp;
@@ -1712,28 +1767,28 @@ int Ctx::rsgn_solve(const fwi_opts &o, fwi_stats *stats) {
                                                                               o.include_Ls_n, bsfull.p + 4 * F0);
     KCHECK();
     CK(cudaMemcpyAsync(bs.p, bsfull.p + 4 * F0, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    adjoint_of_receivers(r.p, fb.p);
-    couple(fb.p, bs.p, 1.0, g.p);
+    N.adjoint_of_receivers(r.p, N.fb.p);
+    N.couple(N.fb.p, bs.p, 1.0, g.p);
     sync();
   }
   // CG from ds~ = 0
   CK(cudaMemcpyAsync(rr.p, g.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(p.p, g.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  const double gn = std::sqrt(dot(g.p, g.p));
+  const double gn = std::sqrt(N.dot(g.p, g.p));
   double rho = gn * gn;
   int it = 0;
   int status = FWI_E_NOCONV;
   double rel = gn > 0.0 ? 1.0 : 0.0;
   if (!(gn > 0.0)) status = FWI_OK;
   while (status != FWI_OK && it < o.max_outer) {
-    normal(p.p, hp.p);
-    const double php = dot(p.p, hp.p);
+    N.apply(p.p, o.eps, hp.p);
+    const double php = N.dot(p.p, hp.p);
     if (!std::isfinite(php) || !(php > 0.0)) fail(FWI_E_NUMERIC, "reduced-space CG: p^T H p is not positive");
     const double alpha = rho / php;
     k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, alpha, p.p, 1.0, x);
     k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, -alpha, hp.p, 1.0, rr.p);
     KCHECK();
-    const double rho_new = dot(rr.p, rr.p);
+    const double rho_new = N.dot(rr.p, rr.p);
     ++it;
     rel = std::sqrt(rho_new) / gn;
     if (rel <= o.tol) { status = FWI_OK; break; }
@@ -1747,8 +1802,37 @@ int Ctx::rsgn_solve(const fwi_opts &o, fwi_stats *stats) {
     stats->rel_res = rel;
     stats->t_solve_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
-  if (solve_rc != FWI_OK && status == FWI_OK) status = solve_rc;
+  if (N.solve_rc != FWI_OK && status == FWI_OK) status = N.solve_rc;
   return status;
+}
+
+// Largest eigenvalue of the Gauss-Newton matrix Re(J~^H W^T W J~) (Sec. 3, eq.
+// normal_system_discrete2 without eps I, scaled control) by power iteration
+// from the constant vector: v_0 = 1/||1||; w = G v_{k-1}; lambda_k = v_{k-1} . w;
+// v_k = w / ||w||.  Returns lambda_iters.  With several instances this is the
+// block-diagonal matrix of all of them (the largest over instances).
+int Ctx::normal_lambda_max(const fwi_opts &o, int iters, double *lambda, fwi_stats *stats) {
+  if (!have_fwd) fail(FWI_E_INVAL, "fwi_normal_lambda_max needs fwi_forward at the current model");
+  if (iters < 1) fail(FWI_E_INVAL, "iters must be >= 1");
+  const long long nc = Nc;
+  NormalOp N(*this, o, stats);
+  DBuf<double> v, w;
+  v.alloc(nc); w.alloc(nc);
+  std::vector<double> one((size_t)nc, 1.0 / std::sqrt((double)nc));
+  CK(cudaMemcpyAsync(v.p, one.data(), nc * sizeof(double), cudaMemcpyHostToDevice, st));
+  double lam = 0.0;
+  for (int k = 0; k < iters; ++k) {
+    N.apply(v.p, 0.0, w.p);
+    lam = N.dot(v.p, w.p);
+    const double wn = std::sqrt(N.dot(w.p, w.p));
+    if (!std::isfinite(wn)) fail(FWI_E_NUMERIC, "non-finite power iterate");
+    if (!(wn > 0.0)) { lam = 0.0; break; }
+    k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, 1.0 / wn, w.p, 0.0, v.p);
+    KCHECK();
+  }
+  sync();
+  *lambda = lam;
+  return N.solve_rc;
 }
 
 int Ctx::rsgn_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats) {
@@ -1825,6 +1909,8 @@ void fwi_default_opts(fwi_opts *o) {
   o->fwd_iters = 60;
   o->max_fwd_refine = 20;
   o->use_graph = 1;
+  o->arnoldi_fp64 = 1;
+  o->check_orth = 0;
 }
 
 int fwi_create(fwi_ctx **out, int n_instances, const fwi_grid *grids, void *cuda_stream) {
@@ -2077,6 +2163,21 @@ int fwi_rsgn_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device,
   API_END(ctx)
 }
 
+int fwi_normal_lambda_max(fwi_ctx *ctx, const fwi_opts *opts, int iters, double *lambda, fwi_stats *stats) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!check_opts(&o) || !lambda) fwi::fail(FWI_E_INVAL, "invalid arguments");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  c.build_hierarchy(o);
+  int rc = c.normal_lambda_max(o, iters, lambda, stats);
+  if (rc != FWI_OK) c.err = "a block solve of the power iteration missed fwd_tol";
+  return rc;
+  API_END(ctx)
+}
+
 int fwi_apply_helmholtz(fwi_ctx *ctx, const void *x, void *y, int adjoint, int precision) {
   API_BEGIN(ctx)
   Ctx &c = ctx->c;
@@ -2203,6 +2304,9 @@ static int mg_cycle_noalloc_impl(fwi::Ctx &c, const fwi_opts &o, const void *b, 
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) fwi::fail(FWI_E_INVAL, "device index out of range");
+  if (dev != c.dev)
+    fwi::fail(FWI_E_INVAL, "fwi_mg_cycle_noalloc: the context's device (" + std::to_string(c.dev) +
+                               ") is not the current device (" + std::to_string(dev) + ")");
   if (!g_noalloc_ready[dev]) {
     void *ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -2227,6 +2331,14 @@ static int mg_cycle_noalloc_impl(fwi::Ctx &c, const fwi_opts &o, const void *b, 
     CK(cudaFuncSetAttribute(fwi::k_coarse_cycle<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CK(cudaFuncSetAttribute(fwi::k_coarse_cycle<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
+  // no live stencil timing inside this call: its event buffers are allocated
+  // on first use, and this call allocates nothing
+  struct TimerBlock {
+    fwi::Ctx &c;
+    bool prev;
+    explicit TimerBlock(fwi::Ctx &cc) : c(cc), prev(cc.timer_blocked) { c.timer_blocked = true; }
+    ~TimerBlock() { c.timer_blocked = prev; }
+  } block(c);
   c.mg_cycle_into<T>((const T2 *)b, (T2 *)x, 0, o, lx, lb, lt, t0);
   c.sync();
   return FWI_OK;
@@ -2268,6 +2380,8 @@ int fwi_get_layout(fwi_ctx *ctx, fwi_layout_info *info) {
 }
 
 unsigned long long fwi_kernel_launches(void) { return fwi::g_launches.load(); }
+
+unsigned long long fwi_memory_calls(void) { return fwi::g_memcalls.load(); }
 
 int fwi_stencil_timer(fwi_ctx *ctx, int enable, double *ms, double *bytes, long long *launches) {
   API_BEGIN(ctx)

@@ -311,3 +311,19 @@ def test_weighted_kkt_update_is_the_weighted_least_squares_solution(include):
     ds_ls = np.linalg.lstsq(np.vstack(rows), np.concatenate(rhs), rcond=None)[0]
     ds_kkt = K.unpack(K.solve_direct())[1]
     assert np.linalg.norm(ds_kkt - ds_ls) <= 1e-8 * np.linalg.norm(ds_ls)
+
+
+def test_gauss_newton_lambda_max_by_power_iteration():
+    """The regulariser rule eps = alpha * lambda_max(Re J~^H W^2 J~) needs the
+    largest eigenvalue of the Gauss-Newton matrix (Sec. 3).  The power
+    iteration's Rayleigh quotients never exceed it, never decrease (G is
+    symmetric positive semidefinite) and converge to numpy.linalg.eigvalsh of
+    the dense matrix built column by column."""
+    _, _, _, K = _weighted_micro()
+    Hm, _ = K.normal_system()
+    G = Hm - K.eps * np.eye(K.Nc)
+    lmax = np.linalg.eigvalsh(G).max()
+    lam = K.gn_lambda_max(60)
+    assert all(l <= lmax * (1 + 1e-12) for l in lam)
+    assert all(b >= a * (1 - 1e-12) for a, b in zip(lam, lam[1:]))
+    assert abs(lam[-1] - lmax) <= 1e-6 * lmax, (lam[-1], lmax)

@@ -2,7 +2,10 @@
 device memory during the call (their memory belongs to another pool, or they
 run next to busy streams where cudaMalloc/cudaFree would block).  Its level
 buffers live in a static device array of the library, so it must give the
-same result as fwi_mg_cycle, call after call.  Collected last on purpose."""
+same result as fwi_mg_cycle, call after call, and make no cudaMalloc /
+cudaFree (the library's own count of memory calls and the device's free
+memory stay unchanged, with the live stencil timer switched on).  Collected
+last on purpose."""
 import ctypes as C
 
 import numpy as np
@@ -40,10 +43,36 @@ def test_noalloc_cycle_matches_allocating_cycle(lib, dtype, tol):
     g = np.random.default_rng(21)
     b = torch.from_numpy(g.standard_normal(n) + 1j * g.standard_normal(n)).to(dtype).cuda()
     ref = _run(f, lib.fwi_mg_cycle, opts, b)            # builds the hierarchy (allocating call)
-    for _ in range(2):                                  # two calls in a row share the static array
-        got = _run(f, lib.fwi_mg_cycle_noalloc, opts, b)
-        rel = (torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref)).item()
+    x = torch.empty_like(b)
+    prec = f._prec_of(b)
+
+    def call():
+        f._check(lib.fwi_mg_cycle_noalloc(f._h, C.byref(opts), C.c_void_p(b.data_ptr()),
+                                          C.c_void_p(x.data_ptr()), prec))
+        torch.cuda.synchronize()
+
+    call()                                              # first call: loads the kernels, looks up the array
+    # the live stencil timer allocates its event buffers on first use; inside
+    # this call it must stay off, so the call still allocates nothing
+    f.stencil_timer(1)
+    outs = [torch.empty_like(b) for _ in range(2)]
+    torch.linalg.vector_norm(outs[0] - ref)             # torch reserves its own memory before the check
+    torch.cuda.synchronize()
+    # only the two library calls (and device-to-device copies into buffers
+    # that already exist) run between the two readings of free device memory
+    free0, _ = torch.cuda.mem_get_info()
+    calls0 = lib.fwi_memory_calls()
+    for k in range(2):                                  # two calls in a row share the static array
+        call()
+        outs[k].copy_(x)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert lib.fwi_memory_calls() == calls0
+    assert free1 == free0, (free0, free1)
+    for out in outs:
+        rel = (torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref)).item()
         assert rel < tol, rel
+    f.stencil_timer(0)
     f.close()
 
 
