@@ -6,13 +6,15 @@ layer, 40 surface sources x 3/5/7 Hz = 120 Helmholtz blocks, 401 receivers).
 A step = set-up of the multigrid hierarchy, forward modelling of all blocks
 (FP64-refined), data residual, the KKT solve to 1e-6 relative residual with the
 inexact block-triangular preconditioner (complex64 bulk, FP64 refinement), and
-the model update.  Every step starts from the same starting model, so steps
-are identical work.  Observed data come from the library's own forward
-modelling at the true model (untimed set-up).
+the model update.  Timed steps walk the workload's 5-step Gauss-Newton
+trajectory from the starting model (reset after every 5 steps).  Observed data
+come from the library's own forward modelling at the true model (untimed
+set-up).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle (exact
-block solves by sparse LU, i.e. the paper's GMRes-full) on a bounded sample.
+block solves by sparse LU, i.e. the paper's GMRes-full) on whole steps of the
+same workload.
 """
 from __future__ import annotations
 
@@ -32,6 +34,9 @@ METRIC = "Newton-step KKT solve time to 1e-6 residual; Krylov iters/s; stencil H
 EPS = 1e-1            # regulariser weight on the relative model: the oracle's exact-preconditioner
                       # GMRES(30) needs 13 iterations here (the paper's Table 1: 16)
 WORKLOAD = "marmousi_shaped_401x141_h20_pml20_40src_3-5-7Hz_120blocks"
+INCLUDE_LS_N = 0      # regulariser on the update only (Levenberg-Marquardt damping), as in the paper's
+                      # multi-frequency experiment: with the -L s_n term, eps = 0.1 on the absolute model
+                      # pulls the model towards zero and a 5-step trajectory diverges after step 1
 
 
 def _dist():
@@ -113,13 +118,19 @@ def _peaks():
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the level-0 smoother launches
-# per algorithmic byte, from the ncu capture summarised under profiles/ (None
-# while the kernels have changed since the last capture).  The reported
-# traffic scales it by each timed launch's algorithmic bytes.
-TRAFFIC_PER_ALG_BYTE = (207.3 + 116.2) / (229.9 + 153.3)
+# per byte of its fused pass (b and the result, plus x unless it starts from
+# zero), from the ncu capture summarised under profiles/ (None while the
+# kernel has changed since the last capture).
+TRAFFIC_PER_FUSED_BYTE = (207.3 + 116.2) / (229.9 + 153.3)
 
 
-def _roofline(ms, nbytes, n, peaks):
+def _roofline(ms, nbytes, n, peaks, fused_bytes=None):
+    """Roofline of the level-0 two-sweep smoother from the library's live
+    timing of its direct launches: achieved = algorithmic bytes per launch
+    (the scope table's 24 B per node and damped-Jacobi sweep for complex64:
+    x, b and the result, two sweeps per launch, 40 B per node when the first
+    sweep starts from zero) over the average launch duration (CUDA events on
+    the launching stream)."""
     peak = peaks.get("hbm_gbs")
     src = "MEASURED_PEAKS.json hbm_gbs (measured)"
     if not peak:
@@ -128,12 +139,20 @@ def _roofline(ms, nbytes, n, peaks):
         return None
     ach = nbytes / (ms / 1e3) / 1e9
     per_launch = nbytes / n
-    return {"kernel": "k_jacobi2_march<float> at level 0 (two fused damped-Jacobi sweeps of the "
-                      "shifted 5-point PML stencil, all blocks)",
-            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "peak_source": src, "launches_timed": n, "avg_launch_us": ms / n * 1e3,
-            "algorithmic_bytes_per_launch": per_launch,
-            "traffic": (TRAFFIC_PER_ALG_BYTE * per_launch) if TRAFFIC_PER_ALG_BYTE else None}
+    out = {"kernel": "k_jacobi2_march<float> at level 0 (two fused damped-Jacobi sweeps of the "
+                     "shifted 5-point PML stencil, all blocks)",
+           "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "peak_source": src, "launches_timed": n, "avg_launch_us": ms / n * 1e3,
+           "algorithmic_bytes_per_launch": per_launch,
+           "accounting": "24 B per node and sweep (x, b, result), 2 sweeps per launch; 40 B per node from zero"}
+    if fused_bytes:
+        fpl = fused_bytes / n
+        out["fused_pass_bytes_per_launch"] = fpl
+        out["fused_pass_gbs"] = fused_bytes / (ms / 1e3) / 1e9
+        out["traffic"] = TRAFFIC_PER_FUSED_BYTE * fpl if TRAFFIC_PER_FUSED_BYTE else None
+    else:
+        out["traffic"] = None
+    return out
 
 
 def run_inner_case(args):
@@ -162,9 +181,9 @@ def run_inner_case(args):
         f.inner_solve(b, opts)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / args.steps
-    ms, nbytes, cnt = f.stencil_timer(0)
+    ms, nbytes, cnt, pb = f.stencil_timer(0, with_pass=True)
     print(json.dumps({"case": "inner", "inner_iters": 4, "s_per_solve": dt,
-                      "roofline": _roofline(ms, nbytes, cnt, _peaks())}))
+                      "roofline": _roofline(ms, nbytes, cnt, _peaks(), pb)}))
 
 
 def _setup_ctx(P, wls, opts, stream):
@@ -285,12 +304,78 @@ def run_extra_case(args):
         ds, st = f.newton_step(o, allow_noconv=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        ms, nbytes, cnt = f.stencil_timer(0)
-        out.update(newton_step_s=dt, outer_iters=st["outer_iters"], rel_res=st["rel_res"],
-                   forward_ms=st["t_forward_ms"], kkt_ms=st["t_solve_ms"],
-                   krylov_iters_per_s=st["outer_iters"] / (st["t_solve_ms"] / 1e3),
-                   inner_block_iters_per_s=st["inner_iters"] / (dt),
-                   roofline=_roofline(ms, nbytes, cnt, _peaks()))
+        ms, nbytes, cnt, pb = f.stencil_timer(0, with_pass=True)
+        converged = st["rel_res"] <= o.tol and st["fwd_rel_res"] <= o.fwd_tol
+        out.update(converged=converged, newton_step_s=dt, outer_iters=st["outer_iters"], rel_res=st["rel_res"],
+                   fwd_rel_res=st["fwd_rel_res"], forward_ms=st["t_forward_ms"], kkt_ms=st["t_solve_ms"],
+                   roofline=_roofline(ms, nbytes, cnt, _peaks(), pb))
+        if converged:
+            out.update(krylov_iters_per_s=st["outer_iters"] / (st["t_solve_ms"] / 1e3),
+                       inner_block_iters_per_s=st["inner_iters"] / dt)
+        else:
+            out["note"] = "not converged: no throughput is reported for an unconverged solve"
+    print(json.dumps(out))
+    f.close()
+
+
+def run_kkt_case(args):
+    """Profiling case: the KKT-side kernels (KKT product, coupling reductions,
+    FGMRES multi-dots and updates) on the benchmark workload: set-up, forward
+    modelling, and one KKT solve stopped after ``--max-outer`` FGMRES
+    iterations (a truncated solve: not a benchmark value)."""
+    import torch
+    import paper_2204_06489_gb300 as P
+    P.load(build_if_missing=True)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    wl = _workload()
+    opts = P.default_opts(eps=EPS, inner_iters=args.inner_iters or 12, include_Ls_n=INCLUDE_LS_N,
+                          max_outer=args.max_outer)
+    f = _setup_ctx(P, [wl], opts, stream)
+    f.forward(opts, want_data=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st = f.kkt_solve(opts, allow_noconv=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "kkt", "outer_iters": st["outer_iters"], "rel_res": st["rel_res"],
+                      "s": time.perf_counter() - t0}))
+    f.close()
+
+
+def run_epsrule_case(args):
+    """The regulariser rule eps = alpha * lambda_max(Re J~^H W^T W J~), alpha =
+    1e-2, lambda_max from 10 power iterations on the matrix-free Gauss-Newton
+    operator (fwi_normal_lambda_max) at the starting model of the benchmark
+    workload; then one Newton step at that eps and one at the headline eps,
+    with their FGMRES iterations and times (one JSON line)."""
+    import torch
+    import paper_2204_06489_gb300 as P
+    P.load(build_if_missing=True)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    wl = _workload()
+    opts = P.default_opts(eps=EPS, inner_iters=args.inner_iters or 12, max_outer=args.max_outer,
+                          include_Ls_n=INCLUDE_LS_N)
+    f = _setup_ctx(P, [wl], opts, stream)
+    f.forward(opts, want_data=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, _ = f.normal_lambda_max(opts, iters=10)
+    t_lam = time.perf_counter() - t0
+    eps_rule = 1e-2 * lam
+    out = {"case": "epsrule", "lambda_max": lam, "power_iters": 10, "lambda_s": round(t_lam, 2),
+           "alpha": 1e-2, "eps_rule": eps_rule, "steps": []}
+    for eps in (eps_rule, EPS):
+        o = P.Opts.from_buffer_copy(opts)
+        o.eps = eps
+        f.set_model(0, wl.gamma_start)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ds, st = f.newton_step(o, allow_noconv=True)
+        torch.cuda.synchronize()
+        out["steps"].append({"eps": eps, "step_s": round(time.perf_counter() - t1, 3), "outer_iters": st["outer_iters"],
+                             "rel_res": st["rel_res"], "converged": st["rel_res"] <= o.tol,
+                             "kkt_ms": st["t_solve_ms"]})
     print(json.dumps(out))
     f.close()
 
@@ -341,10 +426,10 @@ def oracle_step(workers: int = 0, n_src: int = 40, freqs=(3.0, 5.0, 7.0)):
     t0 = time.perf_counter()
     if pool is not None:
         u = pool.solve(src, False)
-        K = kkt.KKT(prob, s0, d, EPS, include_Ls_n=True, u_n=u)
+        K = kkt.KKT(prob, s0, d, EPS, include_Ls_n=bool(INCLUDE_LS_N), u_n=u)
         pre = lambda v: K.precond(v, inner_batch=pool.solve)   # noqa: E731
     else:
-        K = kkt.KKT(prob, s0, d, EPS, include_Ls_n=True)
+        K = kkt.KKT(prob, s0, d, EPS, include_Ls_n=bool(INCLUDE_LS_N))
         pre = K.precond
     x, info = krylov.fgmres(K.matvec, K.rhs(), pre, restart=30, tol=1e-6, max_iter=300)
     s1 = s0 + K.delta_s(x)
@@ -401,32 +486,35 @@ def cpu_baseline_fields(r):
     return {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="native")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--case", default="newton",
-                    choices=["newton", "inner", "batch3a", "batch3b", "large", "autograd", "rsgn", "tradeoff"])
-    ap.add_argument("--max-outer", type=int, default=60)
-    ap.add_argument("--fd-dirs", type=int, default=4)
-    ap.add_argument("--inner-iters", type=int, default=None)
-    ap.add_argument("--restart", type=int, default=None)
-    ap.add_argument("--eps", type=float, default=None)
-    ap.add_argument("--profile-outer", type=int, default=None,
-                    help="profiling runs only: cap the FGMRES iterations of the Newton step "
-                         "(the step is then truncated and its number is not a benchmark value)")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.case == "inner":
-        return run_inner_case(args)
-    if args.case != "newton":
-        return run_extra_case(args)
+NEWTON_STEPS = 5       # Gauss-Newton steps of the workload's trajectory (the model is reset after them)
 
+
+def _kernel_table(prof, peak, wall_ms):
+    """Rows of the library's kernel profile of one step, largest total time
+    first: launches, total and average device time, algorithmic bytes per
+    launch, achieved GB/s and its fraction of the measured HBM bandwidth."""
+    rows = []
+    tot = sum(r["ms"] for r in prof["rows"])
+    for r in sorted(prof["rows"], key=lambda r: -r["ms"]):
+        name = r["kernel"] + (f"[L{r['level']}]" if r["level"] >= 0 and r["kernel"] != "k_coupling_reduce" else
+                              (f"[mode {r['level']}]" if r["kernel"] == "k_coupling_reduce" else ""))
+        gbs = r["bytes"] / (r["ms"] / 1e3) / 1e9 if r["ms"] > 0 and r["bytes"] > 0 else None
+        rows.append({"kernel": name, "launches": r["launches"], "ms": round(r["ms"], 3),
+                     "share": round(r["ms"] / tot, 4) if tot else None,
+                     "avg_us": round(r["ms"] / r["launches"] * 1e3, 2),
+                     "bytes_per_launch": round(r["bytes"] / r["launches"]) if r["bytes"] else 0,
+                     "gbs": round(gbs, 1) if gbs else None, "frac": round(gbs / peak, 3) if gbs else None})
+    return {"kernel_ms": round(tot, 3), "gap_ms": round(prof["gap_ms"], 3), "wall_ms": round(wall_ms, 3),
+            "rows": rows}
+
+
+def run_newton(args):
+    """The headline line: Gauss-Newton steps of the 120-block workload.  Each
+    timed step is one step of the workload's 5-step trajectory (steps 1-5 from
+    the starting model, then the model is reset), so K = 5, 10, ... times whole
+    trajectories; inputs are resident in HBM; CUDA events on the context's
+    stream give per-step device times."""
+    import ctypes as C
     import numpy as np
     import torch
     ws, rank = _dist()
@@ -442,7 +530,7 @@ def main():
     torch.cuda.set_stream(stream)
     f = P.FWI([wl.grid], stream=stream.cuda_stream)
     f.set_survey(0, wl.survey)
-    opts = P.default_opts(eps=args.eps or EPS, precision=args.precision)
+    opts = P.default_opts(eps=args.eps or EPS, precision=args.precision, include_Ls_n=INCLUDE_LS_N)
     if args.inner_iters:
         opts.inner_iters = args.inner_iters
     if args.restart:
@@ -463,20 +551,18 @@ def main():
         tuned = [{"inner_iters": n, "wdepth": wd, "restart": rs, "s": round(t, 3), "outer": o, "ok": ok}
                  for n, wd, rs, t, o, ok in table]
     g0 = torch.from_numpy(wl.gamma_start).cuda()
-    d_dev = torch.from_numpy(d_true[0]).cuda()
     ds_dev = torch.zeros(wl.grid.nx * wl.grid.nz, dtype=torch.float64, device="cuda")
 
-    import ctypes as C
-
-    def step_device():
+    def step_device(k, o=None):
         st = P.api.Stats()
-        f.set_model(0, g0)
-        rc = f._L.fwi_newton_step(f._h, C.byref(opts), C.c_void_p(ds_dev.data_ptr()), 1, C.byref(st))
+        if k % NEWTON_STEPS == 0:
+            f.set_model(0, g0)
+        rc = f._L.fwi_newton_step(f._h, C.byref(o or opts), C.c_void_p(ds_dev.data_ptr()), 1, C.byref(st))
         f._check(rc, allow_noconv=bool(args.profile_outer))
         return st
 
-    for _ in range(args.warmup):
-        step_device()
+    for k in range(args.warmup):
+        step_device(k)
     torch.cuda.synchronize()
     f.stencil_timer(1)          # live CUDA-event timing of the level-0 smoother kernel
     launches0 = f._L.fwi_kernel_launches()
@@ -485,62 +571,129 @@ def main():
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
     stats = []
-    for _ in range(args.steps):
-        stats.append(step_device())
-    e1.record(stream)
+    for k in range(args.steps):
+        stats.append(step_device(k))
+        ev[k + 1].record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     ck = clocks.stop()
-    dev_s = e0.elapsed_time(e1) / 1e3
+    dev_s = ev[0].elapsed_time(ev[-1]) / 1e3
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     launches = f._L.fwi_kernel_launches() - launches0
-    st_ms, st_bytes, st_n = f.stencil_timer(0)
+    st_ms, st_bytes, st_n, st_pass = f.stencil_timer(0, with_pass=True)
     value, per_step = replica_throughput(dev_s, args.steps)
-    outer = sum(s.outer_iters for s in stats) / len(stats)
-    inner = sum(s.inner_iters for s in stats) / len(stats)
-    relres = max(s.rel_res for s in stats)
-    t_fwd = sum(s.t_forward_ms for s in stats) / len(stats)
-    fwd_sweeps = sum(s.fwd_sweeps for s in stats) / len(stats)
-    t_kkt = sum(s.t_solve_ms for s in stats) / len(stats)
+    traj = []
+    for q in range(min(NEWTON_STEPS, args.steps)):
+        sel = [k for k in range(args.steps) if k % NEWTON_STEPS == q]
+        traj.append({"newton_step": q + 1, "ms": round(sum(step_ms[k] for k in sel) / len(sel), 1),
+                     "outer_iters": sum(stats[k].outer_iters for k in sel) / len(sel),
+                     "rel_res": max(stats[k].rel_res for k in sel),
+                     "misfit": stats[sel[0]].misfit})
 
-    # end to end through the C ABI with host buffers (h2d model + data, d2h update)
-    g_host = np.ascontiguousarray(wl.gamma_start)
+    # end to end through the C ABI with host buffers (h2d model + data, d2h
+    # update), walking the same trajectory: the host keeps the model
+    g_start = np.ascontiguousarray(wl.gamma_start)
     d_host = np.ascontiguousarray(d_true[0])
     ds_host = np.zeros(wl.grid.nx * wl.grid.nz)
+    g_host = g_start.copy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for k in range(args.steps):
+        if k % NEWTON_STEPS == 0:
+            g_host = g_start.copy()
         f.set_model(0, g_host)
         f.set_observed(0, d_host)
         st = P.api.Stats()
         f._check(f._L.fwi_newton_step(f._h, C.byref(opts), ds_host.ctypes.data_as(C.c_void_p), 0, C.byref(st)),
                  allow_noconv=bool(args.profile_outer))
+        g_host = g_host + ds_host.reshape(g_host.shape)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
 
     peaks = _peaks()
+    peak = peaks.get("hbm_gbs") or 6800.0
+    extras = {}
+    if not args.no_extras and ws == 1:
+        step1 = [step_ms[k] for k in range(args.steps) if k % NEWTON_STEPS == 0]
+        # (a) the plain complex128 GPU form of the same method, same tolerance,
+        # step 1 of the trajectory (one untimed warm-up step first)
+        o128 = P.Opts.from_buffer_copy(opts)
+        o128.precision = 0
+        step_device(0, o128)
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        st128 = step_device(0, o128)
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        ms128 = e_a.elapsed_time(e_b)
+        extras["c128"] = {"ms_step1": round(ms128, 1), "outer_iters": st128.outer_iters,
+                          "rel_res": st128.rel_res, "mixed_ms_step1": round(sum(step1) / len(step1), 1),
+                          "mixed_speedup": round(ms128 / (sum(step1) / len(step1)), 2)}
+        # (b) per-kernel table of step 1 with direct launches (no graph replay),
+        # CUDA events around every launch
+        op = P.Opts.from_buffer_copy(opts)
+        op.use_graph = 0
+        step_device(0, op)
+        f.kernel_profile(1)
+        e_a.record(stream)
+        stp = step_device(0, op)
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        prof = f.kernel_profile(0)
+        kt = _kernel_table(prof, peak, e_a.elapsed_time(e_b))
+        kt["outer_iters"] = stp.outer_iters
+        kt["note"] = ("step 1 of the trajectory with direct launches; kernel_ms = sum of per-launch event times; "
+                      "gap_share_of_graph_step = 1 - kernel_ms / the timed (graph-replayed) step-1 time")
+        kt["gap_share_of_graph_step"] = round(1.0 - kt["kernel_ms"] / (sum(step1) / len(step1)), 4)
+        extras["kernel_table"] = kt
+        # (c) the two forms of the Arnoldi inner products, with the measured loss
+        # of orthogonality of the complex64 basis (max |I - V^T V|)
+        arn = []
+        for fp64 in (1, 0):
+            oa = P.Opts.from_buffer_copy(opts)
+            oa.arnoldi_fp64 = fp64
+            oa.check_orth = 1
+            f.set_model(0, g0)
+            f.forward(oa, want_data=False)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, sa = f.kkt_solve(oa, allow_noconv=True)
+            torch.cuda.synchronize()
+            arn.append({"arnoldi_fp64": fp64, "outer_iters": sa["outer_iters"], "rel_res": sa["rel_res"],
+                        "orth_loss": sa["orth_loss"], "kkt_s_with_check": round(time.perf_counter() - t1, 3)})
+        extras["arnoldi"] = arn
+    outer = sum(s.outer_iters for s in stats) / len(stats)
+    inner = sum(s.inner_iters for s in stats) / len(stats)
     out = {"metric": METRIC, "value": value, "unit": "Newton-step KKT solves/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "c64+f64-refine" if args.precision == 1 else "c128",
            "data": "synthetic (seeded layered-faulted model; data from the library's forward modelling)",
            "config": {"workload": WORKLOAD, "blocks": 120, "grid_padded": "441x181", "eps": opts.eps,
-                      "tol": 1e-6, "restart": opts.restart, "inner_iters": opts.inner_iters, "mg": f"W(2,2) to level {opts.mg_wdepth}, V below",
+                      "tol": 1e-6, "restart": opts.restart, "inner_iters": opts.inner_iters,
+                      "include_Ls_n": INCLUDE_LS_N,
+                      "mg": f"W(2,2) to level {opts.mg_wdepth}, V below",
+                      "steps": f"each timed step is one of the {NEWTON_STEPS} Gauss-Newton steps of the "
+                               f"trajectory from the starting model (reset after {NEWTON_STEPS})",
                       "l2": "working set > L2 (packed KKT vector 153 MB, Krylov basis 9.4 GB)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
-           "kkt_solve_s": per_step, "outer_iters_per_step": outer, "krylov_iters_per_s": outer / per_step,
-           "inner_block_iters_per_s": inner / per_step, "rel_res_max": relres,
-           "phase_ms": {"forward": t_fwd, "kkt_solve": t_kkt}, "forward_sweeps": fwd_sweeps, "autotune": tuned,
+           "outer_iters_per_step": outer, "krylov_iters_per_s": outer / per_step,
+           "inner_block_iters_per_s": inner / per_step, "rel_res_max": max(s.rel_res for s in stats),
+           "trajectory": traj,
+           "phase_ms": {"forward": sum(s.t_forward_ms for s in stats) / len(stats),
+                        "kkt_solve": sum(s.t_solve_ms for s in stats) / len(stats)},
+           "forward_sweeps": sum(s.fwd_sweeps for s in stats) / len(stats), "autotune": tuned,
            "gpu_launches": int(launches),
-           "roofline": _roofline(st_ms, st_bytes, st_n, peaks),
+           "roofline": _roofline(st_ms, st_bytes, st_n, peaks, st_pass),
            "clocks": ck,
            "e2e": {"value": ws / e2e_s, "unit": "Newton-step KKT solves/s",
-                   "h2d_bytes_per_step": int(g_host.nbytes + d_host.nbytes),
+                   "h2d_bytes_per_step": int(g_start.nbytes + d_host.nbytes),
                    "d2h_bytes_per_step": int(ds_host.nbytes)}}
+    out.update(extras)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_fields(cpu_baseline())
     if rank == 0:
@@ -548,6 +701,43 @@ def main():
     f.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the untimed extras of the headline line (complex128 form, kernel table, "
+                         "Arnoldi precision comparison)")
+    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--case", default="newton",
+                    choices=["newton", "inner", "batch3a", "batch3b", "large", "autograd", "rsgn", "tradeoff",
+                             "epsrule", "kkt"])
+    ap.add_argument("--max-outer", type=int, default=60)
+    ap.add_argument("--fd-dirs", type=int, default=4)
+    ap.add_argument("--inner-iters", type=int, default=None)
+    ap.add_argument("--restart", type=int, default=None)
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--profile-outer", type=int, default=None,
+                    help="profiling runs only: cap the FGMRES iterations of the Newton step "
+                         "(the step is then truncated and its number is not a benchmark value)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.case == "inner":
+        return run_inner_case(args)
+    if args.case == "epsrule":
+        return run_epsrule_case(args)
+    if args.case == "kkt":
+        return run_kkt_case(args)
+    if args.case != "newton":
+        return run_extra_case(args)
+    return run_newton(args)
 
 
 if __name__ == "__main__":

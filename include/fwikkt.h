@@ -299,12 +299,34 @@ unsigned long long fwi_memory_calls(void);
  * while enabled, every launch of it that is not inside a CUDA graph is
  * bracketed by CUDA events on the context's stream, and the kernel counts the
  * grid nodes it processed (blocks whose inner solve has finished are
- * skipped).  Writes (nullable) the accumulated time (ms), algorithmic bytes
- * (per processed node: b and the result, plus x unless the sweeps start from
- * zero, one complex element each) and launch count since the last reset;
- * then enable = 1 resets and turns timing on, 0 resets and turns it off, -1
- * only reads.  Diagnostics; the paper has no counterpart. */
-int fwi_stencil_timer(fwi_ctx *ctx, int enable, double *ms, double *bytes, long long *launches);
+ * skipped).  Writes (nullable) the accumulated time (ms), the algorithmic
+ * bytes (per processed node and sweep: x, b and the result, one complex
+ * element each, so six elements per node for the two sweeps and five when the
+ * first starts from zero), the launch count, and pass_bytes (per processed
+ * node what the fused pass itself must move: b and the result, plus x unless
+ * it starts from zero) since the last reset; then enable = 1 resets and turns
+ * timing on, 0 resets and turns it off, -1 only reads.  Diagnostics; the
+ * paper has no counterpart. */
+int fwi_stencil_timer(fwi_ctx *ctx, int enable, double *ms, double *bytes, long long *launches,
+                      double *pass_bytes);
+
+/* Kernel profile (diagnostics; the paper has no counterpart).  While it is
+ * enabled, every kernel this library launches directly (not inside a stream
+ * capture or a CUDA graph) is bracketed by two CUDA events on its stream.
+ * Per kernel and multigrid level (-1 where none applies) the profile sums the
+ * launches, the event time and the algorithmic bytes each launch site states
+ * (every operand read and result written once; a damped-Jacobi sweep counts
+ * x, b and the result, so the two-sweep smoother counts six complex elements
+ * per node, five when it starts from zero); it also sums the time between one
+ * launch's end and the next launch's start ("gap": launch and host latency).
+ * The call synchronises the context's stream, then, if buf is not NULL,
+ * writes the profile as a NUL-terminated JSON object
+ *   {"gap_ms": g, "gaps": n, "rows": [{"kernel": s, "level": l, "launches": n,
+ *    "ms": t, "bytes": b}, ...]}
+ * into buf (FWI_E_INVAL if buflen is too small; the message gives the size).
+ * Then enable = 1 clears the profile and turns it on, 0 clears it and turns
+ * it off, -1 changes nothing.  The profile is process-wide. */
+int fwi_kernel_profile(fwi_ctx *ctx, int enable, char *buf, long long buflen);
 
 /* Message of the last failure on this context ("" if none). NULL ctx: the
  * message of the last failed fwi_create. */

@@ -117,7 +117,8 @@ def load(build_if_missing: bool = False):
         "fwi_last_error": (C.c_char_p, [P]),
         "fwi_kernel_launches": (C.c_ulonglong, []),
         "fwi_memory_calls": (C.c_ulonglong, []),
-        "fwi_stencil_timer": (C.c_int, [P, C.c_int, DP, DP, C.POINTER(C.c_longlong)]),
+        "fwi_kernel_profile": (C.c_int, [P, C.c_int, C.c_char_p, C.c_longlong]),
+        "fwi_stencil_timer": (C.c_int, [P, C.c_int, DP, DP, C.POINTER(C.c_longlong), DP]),
         "fwi_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -316,11 +317,31 @@ class FWI:
         self._check(rc)
         return lam.value, st.as_dict()
 
-    def stencil_timer(self, enable: int):
-        """(ms, algorithmic bytes, launches) of the level-0 two-sweep smoother kernel since
-        the last reset; ``enable`` 1/0 resets and switches timing, -1 reads."""
-        ms, by, n = C.c_double(), C.c_double(), C.c_longlong()
-        self._check(self._L.fwi_stencil_timer(self._h, enable, C.byref(ms), C.byref(by), C.byref(n)))
+    def kernel_profile(self, enable: int):
+        """The library's kernel profile since the last reset (a dict with
+        gap_ms, gaps and rows of kernel, level, launches, ms, bytes); ``enable``
+        1/0 then clears it and switches it on/off, -1 only reads."""
+        import json
+        n = 1 << 16
+        while True:
+            buf = C.create_string_buffer(n)
+            rc = self._L.fwi_kernel_profile(self._h, -1, buf, n)
+            if rc == FWI_OK:
+                break
+            if n > (1 << 26):
+                self._check(rc)
+            n *= 4
+        self._check(self._L.fwi_kernel_profile(self._h, enable, None, 0))
+        return json.loads(buf.value.decode())
+
+    def stencil_timer(self, enable: int, with_pass: bool = False):
+        """(ms, algorithmic bytes, launches[, fused-pass bytes]) of the level-0
+        two-sweep smoother kernel since the last reset; ``enable`` 1/0 resets
+        and switches timing, -1 reads."""
+        ms, by, n, pb = C.c_double(), C.c_double(), C.c_longlong(), C.c_double()
+        self._check(self._L.fwi_stencil_timer(self._h, enable, C.byref(ms), C.byref(by), C.byref(n), C.byref(pb)))
+        if with_pass:
+            return ms.value, by.value, n.value, pb.value
         return ms.value, by.value, n.value
 
     # ------------------------------------------------------------------ operators (torch CUDA tensors)

@@ -576,104 +576,112 @@ struct CoarseArgs {
 #define SC_UNROLL 4
 // The levels of one block held in shared memory: x, b and a scratch vector
 // per level, plus the level's operator data (stretch factors X, 1/X_{i-1/2},
-// Z, 1/Z_{j-1/2} and gamma), so that a sweep reads nothing from global
-// memory; the diagonal is formed at each node from them,
-//   cc = Z_j (1/X_{i+1/2} + 1/X_{i-1/2}) + X_i (1/Z_{j+1/2} + 1/Z_{j-1/2} - m gamma Z_j),
-// m = (1 + i beta)(omega h_l)^2 (the same expression the set-up kernel
-// evaluates in FP64), conjugated when CJ.
+// Z, 1/Z_{j-1/2} and the inverse diagonal d = 1/cc, which the set-up formed in
+// FP64 for every operator), so that a sweep reads nothing from global memory.
+// A damped-Jacobi sweep needs only d:
+//   x + w d (b - (cc x - Z_j h_x - X_i h_z)) = (1 - w) x + w d (b + Z_j h_x + X_i h_z),
+// with h_x = x_e / X_{i+1/2} + x_w / X_{i-1/2}, h_z = x_s / Z_{j+1/2} + x_n / Z_{j-1/2};
+// the residual forms cc = 1/d.
 template <typename T> struct SmemLevel {
   typedef typename cplx<T>::t T2;
   T2 *x, *b, *t;           // level vectors (t: scratch, ping-pong with x)
   const T2 *X, *iXh, *Z, *iZh;
-  const T *g;
+  const T2 *di;            // inverse diagonal 1/cc of the level's operator (conjugated when CJ)
   int nx, nz;
-  T2 mass;
 };
 
 // Shared memory of the coarse levels of one block (bytes): what
 // k_coarse_cycle lays out per level, rounded as it rounds.
 __host__ __device__ __forceinline__ size_t smem_level_bytes(int nx, int nz, size_t elem) {
   const size_t n = (size_t)nx * nz;
-  return 3 * n * elem + (size_t)(2 * nx + 2 * nz + 2) * elem + ((n + 3) / 4 * 4) * (elem / 2);
+  return 4 * n * elem + (size_t)(2 * nx + 2 * nz + 2) * elem;
 }
 
+// The cycle state lives in shared memory (one copy per CTA): the level
+// descriptors (vector pointers, operator data, sizes) and the operators.
+// Threads keep only scalars in registers: which of a level's two vectors
+// holds x (one parity bit per level) and the remaining coarse-grid
+// corrections of each level (two bits per level), so no per-thread array is
+// indexed dynamically and nothing goes to local memory.
 template <typename T, bool CJ>
 struct SmemCycle {
   typedef typename cplx<T>::t T2;
-  const CoarseArgs &a;
-  SmemLevel<T> lvl[MAX_LEVELS];
-  OpDev op[MAX_LEVELS];
-  int blk, nlev;
-  __device__ SmemCycle(const CoarseArgs &a_) : a(a_) {}
+  SmemLevel<T> *lvl;       // [MAX_LEVELS] in shared memory
+  const OpDev *op;         // [MAX_LEVELS] in shared memory
+  const double2 *inv;      // this block's coarsest inverse (global)
+  int nlev, nu1, nu2, cyc, wdepth;
+  T w;
+  unsigned par = 0;        // bit l: level l's current x is in t (ping-pong)
+  __device__ __forceinline__ T2 *X_(int l) const { return (par >> l) & 1u ? lvl[l].t : lvl[l].x; }
+  __device__ __forceinline__ T2 *T_(int l) const { return (par >> l) & 1u ? lvl[l].x : lvl[l].t; }
 
-  // (Op u) at node (j, i) of level L and its diagonal; urow points at row j.
-  struct Node { T2 au, cc; };
-  __device__ __forceinline__ static Node node(const SmemLevel<T> &L, const T2 *urow, int j, int i, T2 Zj,
-                                              T2 iZn, T2 iZs, T2 szm) {
+  // Off-diagonal part of the operator at node (j, i) of level L, negated:
+  // Z_j h_x + X_i h_z; urow points at row j.
+  __device__ __forceinline__ static T2 offdiag(const SmemLevel<T> &L, const T2 *urow, int j, int i, T2 Zj,
+                                               T2 iZn, T2 iZs) {
     const T2 Xi = cmaybe_conj(L.X[i], CJ);
     const T2 iw = cmaybe_conj(L.iXh[i], CJ);
     const T2 ie = cmaybe_conj(L.iXh[i + 1], CJ);
-    const T g = L.g[j * L.nx + i];
-    Node r;
-    // cc = Zj (ie + iw) + Xi (iZs + iZn - g m Zj); szm = (iZs + iZn, m Zj)
-    r.cc = cadd(cmul(Zj, cadd(ie, iw)), cmul(Xi, csub(szm, cscale(cmul(L.mass, Zj), g))));
     const T2 zero = mk<T2>(0, 0);
-    const T2 uc = urow[i];
     const T2 ue = i + 1 < L.nx ? urow[i + 1] : zero;
     const T2 uw = i > 0 ? urow[i - 1] : zero;
     const T2 us = j + 1 < L.nz ? urow[i + L.nx] : zero;
     const T2 un = j > 0 ? urow[i - L.nx] : zero;
     const T2 hx = cadd(cmul(ie, ue), cmul(iw, uw));
     const T2 hz = cadd(cmul(iZs, us), cmul(iZn, un));
-    r.au = csub(csub(cmul(r.cc, uc), cmul(Zj, hx)), cmul(Xi, hz));
-    return r;
+    return cadd(cmul(Zj, hx), cmul(Xi, hz));
   }
-  // A warp takes a row, a lane the columns lane + 32 q (q < SC_UNROLL) at a
-  // time; results are stored after all of them are formed.
+  // One damped-Jacobi sweep on level l (from x = 0 when from_zero): a warp
+  // takes a row, a lane the columns lane + 32 q (q < SC_UNROLL) at a time;
+  // results go to the other vector, which then becomes x.
   __device__ void jacobi(int l, bool from_zero) {
-    const SmemLevel<T> L = lvl[l];     // a copy: kept in registers across the shared-memory stores
+    const SmemLevel<T> L = lvl[l];
+    const T2 *xs = X_(l);
+    T2 *ts = T_(l);
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const T w = (T)a.w;
     for (int j = threadIdx.x >> 5; j < L.nz; j += nw) {
       const T2 Zj = cmaybe_conj(L.Z[j], CJ), iZn = cmaybe_conj(L.iZh[j], CJ), iZs = cmaybe_conj(L.iZh[j + 1], CJ);
-      const T2 szm = cadd(iZn, iZs);
-      const T2 *xr = L.x + j * L.nx;
+      const T2 *xr = xs + j * L.nx;
       const T2 *br = L.b + j * L.nx;
+      const T2 *dr = L.di + j * L.nx;
       for (int i0 = lane; i0 < L.nx; i0 += 32 * SC_UNROLL) {
         T2 out[SC_UNROLL];
 #pragma unroll
         for (int q = 0; q < SC_UNROLL; ++q) {
           const int i = i0 + 32 * q;
           if (i < L.nx) {
-            const Node nd = node(L, xr, j, i, Zj, iZn, iZs, szm);
-            const T2 d = cinv(nd.cc);
+            const T2 d = dr[i];
             if (from_zero) out[q] = cscale(cmul(br[i], d), w);
-            else out[q] = cadd(xr[i], cscale(cmul(csub(br[i], nd.au), d), w));
+            else out[q] = cadd(cscale(xr[i], (T)1 - w),
+                               cscale(cmul(cadd(br[i], offdiag(L, xr, j, i, Zj, iZn, iZs)), d), w));
           }
         }
 #pragma unroll
         for (int q = 0; q < SC_UNROLL; ++q)
-          if (i0 + 32 * q < L.nx) L.t[j * L.nx + i0 + 32 * q] = out[q];
+          if (i0 + 32 * q < L.nx) ts[j * L.nx + i0 + 32 * q] = out[q];
       }
     }
     __syncthreads();
-    lvl[l].x = L.t; lvl[l].t = L.x;   // ping-pong
+    par ^= 1u << l;        // every thread flips its own copy: ping-pong
   }
   __device__ void restrict_to(int l) {  // b_{l+1} = P^T (b_l - M_l x_l)
     const SmemLevel<T> L = lvl[l];
+    const T2 *xs = X_(l);
+    T2 *ts = T_(l);
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = threadIdx.x >> 5; j < L.nz; j += nw) {
       const T2 Zj = cmaybe_conj(L.Z[j], CJ), iZn = cmaybe_conj(L.iZh[j], CJ), iZs = cmaybe_conj(L.iZh[j + 1], CJ);
-      const T2 szm = cadd(iZn, iZs);
-      const T2 *xr = L.x + j * L.nx;
+      const T2 *xr = xs + j * L.nx;
       const T2 *br = L.b + j * L.nx;
-      T2 *tr = L.t + j * L.nx;
+      const T2 *dr = L.di + j * L.nx;
+      T2 *tr = ts + j * L.nx;
       for (int i0 = lane; i0 < L.nx; i0 += 32 * SC_UNROLL) {
         T2 out[SC_UNROLL];
 #pragma unroll
         for (int q = 0; q < SC_UNROLL; ++q) {
           const int i = i0 + 32 * q;
-          if (i < L.nx) out[q] = csub(br[i], node(L, xr, j, i, Zj, iZn, iZs, szm).au);
+          if (i < L.nx)   // b - (cc x - Z_j h_x - X_i h_z), cc = 1/d
+            out[q] = cadd(csub(br[i], cmul(cinv(dr[i]), xr[i])), offdiag(L, xr, j, i, Zj, iZn, iZs));
         }
 #pragma unroll
         for (int q = 0; q < SC_UNROLL; ++q)
@@ -681,63 +689,66 @@ struct SmemCycle {
       }
     }
     __syncthreads();
-    const OpDev &o = op[l];
-    const OpDev &c = op[l + 1];
-    int nc = c.nx * c.nz;
+    const int onx = L.nx, onz = L.nz;
+    const int cnx = lvl[l + 1].nx, cnz = lvl[l + 1].nz;
+    T2 *bc = lvl[l + 1].b;
+    const int nc = cnx * cnz;
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-      int J = k / c.nx, I = k - J * c.nx;
+      const int J = k / cnx, I = k - J * cnx;
       T2 acc = mk<T2>(0, 0);
       for (int db = -1; db <= 1; ++db) {
-        int j = 2 * J + 1 + db;
-        if (j < 0 || j >= o.nz) continue;
-        T wz = db == 0 ? T(1) : T(0.5);
+        const int j = 2 * J + 1 + db;
+        if (j < 0 || j >= onz) continue;
+        const T wz = db == 0 ? T(1) : T(0.5);
         for (int da = -1; da <= 1; ++da) {
-          int i = 2 * I + 1 + da;
-          if (i < 0 || i >= o.nx) continue;
-          T wx = da == 0 ? T(1) : T(0.5);
-          acc = cadd(acc, cscale(lvl[l].t[j * o.nx + i], wz * wx));
+          const int i = 2 * I + 1 + da;
+          if (i < 0 || i >= onx) continue;
+          const T wx = da == 0 ? T(1) : T(0.5);
+          acc = cadd(acc, cscale(ts[j * onx + i], wz * wx));
         }
       }
-      lvl[l + 1].b[k] = acc;
+      bc[k] = acc;
     }
     __syncthreads();
   }
   __device__ void prolong_from(int l) {  // x_l += P x_{l+1}
-    const OpDev &o = op[l];
-    const OpDev &c = op[l + 1];
-    int n = o.nx * o.nz;
+    const int fnx = lvl[l].nx, fnz = lvl[l].nz;
+    const int cnx = lvl[l + 1].nx, cnz = lvl[l + 1].nz;
+    T2 *xf = X_(l);
+    const T2 *xc = X_(l + 1);
+    const int n = fnx * fnz;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      int j = k / o.nx, i = k - j * o.nx;
+      const int j = k / fnx, i = k - j * fnx;
       T2 acc = mk<T2>(0, 0);
       for (int q = 0; q < 2; ++q) {
         int J; T wz;
         if (j & 1) { if (q) continue; J = (j - 1) >> 1; wz = 1; }
         else { J = (j >> 1) - 1 + q; wz = 0.5; }
-        if (J < 0 || J >= c.nz) continue;
+        if (J < 0 || J >= cnz) continue;
         for (int p = 0; p < 2; ++p) {
           int I; T wx;
           if (i & 1) { if (p) continue; I = (i - 1) >> 1; wx = 1; }
           else { I = (i >> 1) - 1 + p; wx = 0.5; }
-          if (I < 0 || I >= c.nx) continue;
-          acc = cadd(acc, cscale(lvl[l + 1].x[J * c.nx + I], wz * wx));
+          if (I < 0 || I >= cnx) continue;
+          acc = cadd(acc, cscale(xc[J * cnx + I], wz * wx));
         }
       }
-      lvl[l].x[k] = cadd(lvl[l].x[k], acc);
+      xf[k] = cadd(xf[k], acc);
     }
     __syncthreads();
   }
   // x = M^{-1} b with the FP64 inverse: one warp per row, lanes over columns.
   __device__ void coarsest(int l) {
-    const OpDev &o = op[l];
-    int n = o.nx * o.nz;
-    const double2 *M = a.inv + a.inv_off[a.blks[l][blk].op];
+    const int n = lvl[l].nx * lvl[l].nz;
+    const T2 *bl = lvl[l].b;
+    T2 *xl = X_(l);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = warp; r < n; r += nw) {
       double ax = 0.0, ay = 0.0;
       for (int c = lane; c < n; c += 32) {
-        double2 m = M[(long long)r * n + c];
+        double2 m = inv[(long long)r * n + c];
         if (CJ) m.y = -m.y;
-        double2 v = to_d2(lvl[l].b[c]);
+        const double2 v = to_d2(bl[c]);
         ax += m.x * v.x - m.y * v.y;
         ay += m.x * v.y + m.y * v.x;
       }
@@ -745,43 +756,48 @@ struct SmemCycle {
         ax += __shfl_down_sync(0xffffffffu, ax, q);
         ay += __shfl_down_sync(0xffffffffu, ay, q);
       }
-      if (lane == 0) lvl[l].x[r] = mk<T2>(ax, ay);
+      if (lane == 0) xl[r] = mk<T2>(ax, ay);
     }
     __syncthreads();
   }
   __device__ void presmooth(int l) {
-    for (int s = 0; s < a.nu1; ++s) jacobi(l, s == 0);
-    if (a.nu1 == 0) {
-      int n = op[l].nx * op[l].nz;
-      for (int k = threadIdx.x; k < n; k += blockDim.x) lvl[l].x[k] = mk<T2>(0, 0);
+    for (int s = 0; s < nu1; ++s) jacobi(l, s == 0);
+    if (nu1 == 0) {
+      const int n = lvl[l].nx * lvl[l].nz;
+      T2 *xl = X_(l);
+      for (int k = threadIdx.x; k < n; k += blockDim.x) xl[k] = mk<T2>(0, 0);
       __syncthreads();
     }
   }
   // The multigrid cycle from level `top` written as a loop (no device
   // recursion): going down, a level pre-smooths and restricts; the coarsest
   // level solves; going up, a level adds the prolonged correction and either
-  // repeats its coarse-grid correction (cycle index) or post-smooths.
+  // repeats its coarse-grid correction (cycle index) or post-smooths.  The
+  // corrections still to do are kept two bits per level in one register.
   __device__ void run(int top) {
-    int reps[MAX_LEVELS];
+    unsigned reps = 0;
     int l = top;
     bool down = true;
     for (int guard = 0; guard < (1 << 20); ++guard) {
       if (down) {
         if (l == nlev - 1) { coarsest(l); down = false; continue; }
         presmooth(l);
-        reps[l] = (l > 0 && l <= a.wdepth) ? a.cyc : 1;
+        const unsigned r = (l > 0 && l <= wdepth) ? (unsigned)cyc : 1u;
+        reps = (reps & ~(3u << (2 * l))) | (r << (2 * l));
         restrict_to(l);
         ++l;
       } else {
         if (l == top) break;
-        int p = l - 1;
+        const int p = l - 1;
         prolong_from(p);
-        if (--reps[p] > 0) {
+        const unsigned r = ((reps >> (2 * p)) & 3u) - 1u;
+        reps = (reps & ~(3u << (2 * p))) | (r << (2 * p));
+        if (r > 0) {
           restrict_to(p);
           l = p + 1;
           down = true;
         } else {
-          for (int s = 0; s < a.nu2; ++s) jacobi(p, false);
+          for (int s = 0; s < nu2; ++s) jacobi(p, false);
           l = p;
         }
       }
@@ -792,44 +808,58 @@ struct SmemCycle {
 #define COARSE_THREADS 512
 template <typename T, bool CJ>
 __global__ void __launch_bounds__(COARSE_THREADS, 1)
-k_coarse_cycle(CoarseArgs a, const typename cplx<T>::t *__restrict__ st, const T *__restrict__ gam,
-               const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ x) {
+k_coarse_cycle(const __grid_constant__ CoarseArgs a, const typename cplx<T>::t *__restrict__ st,
+               const typename cplx<T>::t *__restrict__ dgi, const typename cplx<T>::t *__restrict__ b,
+               typename cplx<T>::t *__restrict__ x) {
   typedef typename cplx<T>::t T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SmemLevel<T> s_lvl[MAX_LEVELS];
+  __shared__ OpDev s_op[MAX_LEVELS];
   T2 *sm = reinterpret_cast<T2 *>(smem_raw);
-  if (a.skip && a.skip[blockIdx.x]) return;
-  SmemCycle<T, CJ> c(a);
-  c.blk = blockIdx.x;
-  c.nlev = a.inst_nlev[a.blks[a.ls][c.blk].inst];
+  const int blk = blockIdx.x;
+  if (a.skip && a.skip[blk]) return;
+  const int nlev = a.inst_nlev[a.blks[a.ls][blk].inst];
   // per level (layout of smem_level_bytes): x, b, t [n]; X [nx]; 1/Xh [nx+1];
-  // Z [nz]; 1/Zh [nz+1]; gamma [n rounded up to 4]
+  // Z [nz]; 1/Zh [nz+1]; 1/cc [n]
   size_t off = 0;
-  for (int l = a.ls; l < c.nlev; ++l) {
-    const OpDev o = a.ops[a.blks[l][c.blk].op];
-    c.op[l] = o;
-    SmemLevel<T> &L = c.lvl[l];
+  for (int l = a.ls; l < nlev; ++l) {
+    const OpDev o = a.ops[a.blks[l][blk].op];
     const int n = o.nx * o.nz;
-    L.nx = o.nx; L.nz = o.nz;
-    L.mass = cmaybe_conj(mk<T2>(o.mass_re, o.mass_im), CJ);
-    L.x = sm + off; off += n;
-    L.b = sm + off; off += n;
-    L.t = sm + off; off += n;
+    T2 *lx = sm + off; off += n;
+    T2 *lb = sm + off; off += n;
+    T2 *lt = sm + off; off += n;
     T2 *stc = sm + off;
     const int nst = 2 * o.nx + 2 * o.nz + 2;
     off += nst;
     for (int k = threadIdx.x; k < nst; k += blockDim.x) stc[k] = st[o.st + k];
-    L.X = stc; L.iXh = stc + o.nx; L.Z = stc + 2 * o.nx + 1; L.iZh = L.Z + o.nz;
-    T *gs = reinterpret_cast<T *>(sm + off);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) gs[k] = gam[o.gam + k];
-    L.g = gs;
-    off += (n + 3) / 4 * 2;   // gamma: (n rounded up to 4) reals = half as many complex slots
+    T2 *ds = sm + off;
+    off += n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) ds[k] = cmaybe_conj(dgi[o.dg + k], CJ);
+    if (threadIdx.x == 0) {
+      SmemLevel<T> L;
+      L.x = lx; L.b = lb; L.t = lt;
+      L.X = stc; L.iXh = stc + o.nx; L.Z = stc + 2 * o.nx + 1; L.iZh = L.Z + o.nz;
+      L.di = ds;
+      L.nx = o.nx; L.nz = o.nz;
+      s_lvl[l] = L;
+      s_op[l] = o;
+    }
   }
-  const BlkDev bk = a.blks[a.ls][c.blk];
-  int n = c.op[a.ls].nx * c.op[a.ls].nz;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) c.lvl[a.ls].b[k] = b[bk.off + k];
+  __syncthreads();
+  SmemCycle<T, CJ> c;
+  c.lvl = s_lvl;
+  c.op = s_op;
+  c.inv = a.inv + a.inv_off[a.blks[nlev - 1][blk].op];
+  c.nlev = nlev; c.nu1 = a.nu1; c.nu2 = a.nu2; c.cyc = a.cyc; c.wdepth = a.wdepth;
+  c.w = (T)a.w;
+  const BlkDev bk = a.blks[a.ls][blk];
+  const int n = s_lvl[a.ls].nx * s_lvl[a.ls].nz;
+  T2 *bl = s_lvl[a.ls].b;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) bl[k] = b[bk.off + k];
   __syncthreads();
   c.run(a.ls);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) x[bk.off + k] = c.lvl[a.ls].x[k];
+  const T2 *xr = c.X_(a.ls);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) x[bk.off + k] = xr[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -1683,6 +1713,196 @@ __global__ void k_backsub(int k, int m, const double *H, const double *g, double
     double s = g[i];
     for (int c = i + 1; c < k; ++c) s -= H[(long long)c * (m + 1) + i] * y[c];
     double d = H[(long long)i * (m + 1) + i];
+    y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device-controlled FGMRES cycle (one CUDA graph per restart cycle whose WHILE
+// node runs the Arnoldi steps).  The step index j and the counters live in a
+// device control block; kernels that depend on j read it there.
+// ---------------------------------------------------------------------------
+struct FgCtl {
+  int j;          // Arnoldi step of this cycle (0-based)
+  int k;          // steps completed in this cycle
+  int total;      // iterations over all cycles (including this one)
+  int state;      // 0 running, 1 converged, 2 non-finite residual, 3 basis full / cap reached
+  int m, maxit;
+  double thr;     // convergence threshold tol * ||rhs||
+};
+
+// y = V[j + shift] (from = 1) or V[j + shift] = y (from = 0), j from the control block.
+template <typename T>
+__global__ void k_copy_indexed(long long n, const FgCtl *c, T *const *V, int shift, T *y, int from) {
+  T *v = V[c->j + shift];
+  const T *src = from ? v : y;
+  T *dst = from ? y : v;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// V[j + 1] = w / *s (s = h_{j+1,j}; 0 if s == 0), j from the control block.
+template <typename T>
+__global__ void k_scale_to_indexed(long long n, const FgCtl *c, T *const *V, const double *s, const T *w) {
+  T *v = V[c->j + 1];
+  const double sv = *s;
+  const T f = (T)(sv != 0.0 ? 1.0 / sv : 0.0);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[i] = w[i] * f;
+}
+
+// Number of vectors of chunk c0 for the current step: min(MD_CHUNK, cnt - c0)
+// with cnt = j + 1 (which = 0) or k (which = 1); <= 0 means nothing to do.
+__device__ __forceinline__ int chunk_count(const FgCtl *c, int which, int c0) {
+  const int cnt = which ? c->k : c->j + 1;
+  return min(MD_CHUNK, cnt - c0);
+}
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(FLAT_THREADS)
+k_multidot_dev(long long n, const FgCtl *c, int which, int c0, const T *const *V, const T *__restrict__ w,
+               double *partial) {
+  const int nv = chunk_count(c, which, c0);
+  if (nv <= 0) return;
+  // the body of k_multidot for nv vectors starting at V[c0]
+  double tot[MD_CHUNK];
+  T ra[MD_CHUNK], rb[MD_CHUNK];
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v) { tot[v] = 0.0; ra[v] = 0; rb[v] = 0; }
+  const T *vp[MD_CHUNK];
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v) vp[v] = v < nv ? V[c0 + v] : nullptr;
+  const long long stride = (long long)gridDim.x * FLAT_THREADS;
+  int cnt = 0;
+  long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x;
+  if (EXACT && sizeof(T) == 4) {
+    for (; i < n; i += stride) {
+      const double wa = (double)w[i];
+#pragma unroll
+      for (int v = 0; v < MD_CHUNK; ++v)
+        if (v < nv) tot[v] = tfma((double)vp[v][i], wa, tot[v]);
+    }
+  } else {
+    for (; i + stride < n; i += 2 * stride) {
+      const T wa = w[i], wb = w[i + stride];
+#pragma unroll
+      for (int v = 0; v < MD_CHUNK; ++v)
+        if (v < nv) { ra[v] = tfma(vp[v][i], wa, ra[v]); rb[v] = tfma(vp[v][i + stride], wb, rb[v]); }
+      if (sizeof(T) == 4 && (cnt += 2) >= MD_RUN) {
+#pragma unroll
+        for (int v = 0; v < MD_CHUNK; ++v)
+          if (v < nv) { tot[v] += (double)(ra[v] + rb[v]); ra[v] = 0; rb[v] = 0; }
+        cnt = 0;
+      }
+    }
+    if (i < n) {
+      const T wa = w[i];
+#pragma unroll
+      for (int v = 0; v < MD_CHUNK; ++v)
+        if (v < nv) ra[v] = tfma(vp[v][i], wa, ra[v]);
+    }
+  }
+  __shared__ double red[MD_CHUNK][FLAT_THREADS / 32];
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v) {
+    if (v < nv) {
+      double x = tot[v] + (double)(ra[v] + rb[v]);
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = x;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double s = 0.0;
+    for (int q = 0; q < FLAT_THREADS / 32; ++q) s += red[threadIdx.x][q];
+    partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// out[c0 + v] = sum_b partial[v][b] for v < the chunk's count (one warp per v)
+__global__ void k_reduce_partials_dev(const FgCtl *c, int which, int c0, int nb, const double *partial, double *out) {
+  const int v = blockIdx.x;
+  if (v >= chunk_count(c, which, c0)) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) s += partial[(long long)v * nb + b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) out[c0 + v] = s;
+}
+
+// w += sign * sum_v coef[c0 + v] V[c0 + v] for the chunk's vectors
+template <typename T>
+__global__ void __launch_bounds__(FLAT_THREADS)
+k_multi_axpy_dev(long long n, const FgCtl *c, int which, int c0, const T *const *V, const double *coef, double sign,
+                 T *w) {
+  const int nv = chunk_count(c, which, c0);
+  if (nv <= 0) return;
+  T cf[MD_CHUNK];
+  const T *vp[MD_CHUNK];
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v) { cf[v] = v < nv ? (T)(sign * coef[c0 + v]) : (T)0; vp[v] = v < nv ? V[c0 + v] : nullptr; }
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
+    T acc = w[i];
+#pragma unroll
+    for (int v = 0; v < MD_CHUNK; ++v)
+      if (v < nv) acc = tfma(cf[v], vp[v][i], acc);
+    w[i] = acc;
+  }
+}
+
+// a[i] += b[i] for i <= j
+__global__ void k_dadd_dev(const FgCtl *c, double *a, const double *b) {
+  for (int i = threadIdx.x; i <= c->j; i += blockDim.x) a[i] += b[i];
+}
+
+// Givens step of column j (k_givens with j from the control block).
+__global__ void k_givens_dev(const FgCtl *c, double *H, double *cs, double *sn, double *g, const double *hcol,
+                             const double *norm2, double *hnext, double *res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = c->j, m = c->m;
+  double *col = H + (long long)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = hcol[i];
+  const double hn = sqrt(fmax(norm2[0], 0.0));
+  col[j + 1] = hn;
+  *hnext = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rr = hypot(col[j], col[j + 1]);
+  const double cc = rr > 0.0 ? col[j] / rr : 1.0;
+  const double ss = rr > 0.0 ? col[j + 1] / rr : 0.0;
+  cs[j] = cc; sn[j] = ss;
+  col[j] = rr; col[j + 1] = 0.0;
+  g[j + 1] = -ss * g[j];
+  g[j] = cc * g[j];
+  res[0] = fabs(g[j + 1]);
+}
+
+// End of an Arnoldi step: advance the counters, test convergence and decide
+// whether the WHILE node runs another step.  The loop always ends: j grows by
+// one per step and the node stops at j = m or total = maxit.
+__global__ void k_fgmres_ctl(FgCtl *c, const double *res, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double r = res[0];
+  c->j += 1;
+  c->k = c->j;
+  c->total += 1;
+  int more = 1;
+  if (!isfinite(r)) { c->state = 2; more = 0; }
+  else if (r <= c->thr) { c->state = 1; more = 0; }
+  else if (c->j >= c->m || c->total >= c->maxit) { c->state = 3; more = 0; }
+  cudaGraphSetConditional(h, more);
+}
+
+// Back substitution with k from the control block.
+__global__ void k_backsub_dev(const FgCtl *c, const double *H, const double *g, double *y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = c->k, m = c->m;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int q = i + 1; q < k; ++q) s -= H[(long long)q * (m + 1) + i] * y[q];
+    const double d = H[(long long)i * (m + 1) + i];
     y[i] = d != 0.0 ? s / d : 0.0;
   }
 }

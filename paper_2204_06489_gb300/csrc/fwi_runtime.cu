@@ -34,13 +34,95 @@ struct Err {
     if (e_ != cudaSuccess)                                                                 \
       throw Err{FWI_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};           \
   } while (0)
+// Kernel profile (diagnostics, fwi_kernel_profile): while enabled, every
+// kernel launched directly (not inside a stream capture) is preceded by
+// KPROF(name, level, bytes, stream), which records a CUDA event on the stream,
+// and followed by KCHECK(), which records a second one.  Per (kernel, level)
+// the profile sums launches, event time and the algorithmic bytes the launch
+// site states (each operand and result counted once); the time between one
+// launch's end event and the next launch's start event is summed as gap time.
+struct ProfRow {
+  long long n = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+struct Prof {
+  bool on = false;
+  bool pending = false;
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> ev;                         // 2 per recorded launch
+  std::vector<std::pair<std::string, int>> key;        // per recorded launch
+  std::vector<double> bytes;
+  size_t used = 0;
+  std::map<std::pair<std::string, int>, ProfRow> rows;
+  double gap_ms = 0.0;
+  long long gaps = 0;
+  void harvest() {
+    for (size_t k = 0; k < used; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) {
+        ProfRow &r = rows[key[k]];
+        r.n += 1;
+        r.ms += ms;
+        r.bytes += bytes[k];
+      }
+      if (k > 0 && cudaEventElapsedTime(&ms, ev[2 * k - 1], ev[2 * k]) == cudaSuccess) {
+        gap_ms += ms;
+        ++gaps;
+      }
+    }
+    used = 0;
+  }
+  void clear() {
+    rows.clear();
+    gap_ms = 0.0;
+    gaps = 0;
+    used = 0;
+    pending = false;
+  }
+};
+static Prof g_prof;
+
+static void prof_begin(const char *name, int level, double nbytes, cudaStream_t s) {
+  Prof &P = g_prof;
+  P.pending = false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  if (P.used >= 8192) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return;
+    P.harvest();
+  }
+  while (P.ev.size() < 2 * (P.used + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    P.ev.push_back(e);
+  }
+  if (P.key.size() <= P.used) { P.key.resize(P.used + 1); P.bytes.resize(P.used + 1); }
+  P.key[P.used] = {name, level};
+  P.bytes[P.used] = nbytes;
+  P.st = s;
+  if (cudaEventRecord(P.ev[2 * P.used], s) != cudaSuccess) return;
+  P.pending = true;
+}
+static void prof_end() {
+  Prof &P = g_prof;
+  if (!P.pending) return;
+  P.pending = false;
+  if (cudaEventRecord(P.ev[2 * P.used + 1], P.st) == cudaSuccess) ++P.used;
+}
+#define KPROF(name, level, nbytes, stream)                                      \
+  do {                                                                          \
+    if (::fwi::g_prof.on) ::fwi::prof_begin(name, level, (double)(nbytes), stream); \
+  } while (0)
+
 // Every kernel launch of the library is followed by KCHECK(), which also
-// counts it (graph replays add the number of kernels captured in the graph).
+// counts it (graph replays add the number of kernels captured in the graph)
+// and closes its profile record.
 static std::atomic<unsigned long long> g_launches{0};
-#define KCHECK()                 \
-  do {                           \
-    ::fwi::g_launches.fetch_add(1); \
-    CK(cudaGetLastError());      \
+#define KCHECK()                     \
+  do {                               \
+    ::fwi::g_launches.fetch_add(1);  \
+    CK(cudaGetLastError());          \
+    if (::fwi::g_prof.pending) ::fwi::prof_end(); \
   } while (0)
 
 static void fail(int code, const std::string &m) { throw Err{code, m}; }
@@ -153,8 +235,15 @@ template <typename T> struct Work {
   cudaGraphExec_t graph = nullptr;
   std::string graph_key;
   unsigned long long graph_kernels = 0;
+  // device-controlled FGMRES restart cycle: WHILE node over Arnoldi steps
+  cudaGraphExec_t cyc = nullptr;
+  std::string cyc_key;
+  unsigned long long cyc_body_kernels = 0, cyc_tail_kernels = 0;
+  DBuf<FgCtl> ctl;
+  DBuf<T> wst;                                         // staging of the new Arnoldi vector
   ~Work() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (cyc) cudaGraphExecDestroy(cyc);
   }
 };
 
@@ -229,10 +318,11 @@ struct Ctx {
   bool timer_blocked = false;      // set by calls that must not allocate (no timed launches)
   int dev = -1;                    // CUDA device of the context (recorded at first device use)
   std::vector<cudaEvent_t> ev_a, ev_b;
-  std::vector<double> ev_bytes;    // bytes per processed node of each timed launch
+  std::vector<double> ev_bytes;    // algorithmic bytes per processed node of each timed launch
+  std::vector<double> ev_pbytes;   // bytes per processed node of the fused pass itself
   DBuf<unsigned long long> ev_work; // nodes processed by each timed launch (device counters)
   size_t ev_used = 0;
-  double timer_ms = 0.0, timer_bytes = 0.0;
+  double timer_ms = 0.0, timer_bytes = 0.0, timer_pbytes = 0.0;
   long long timer_n = 0;
   void harvest() {
     std::vector<unsigned long long> work(ev_used, 0);
@@ -245,6 +335,7 @@ struct Ctx {
       if (cudaEventElapsedTime(&ms, ev_a[q], ev_b[q]) == cudaSuccess) {
         timer_ms += ms;
         timer_bytes += ev_bytes[q] * (double)work[q];
+        timer_pbytes += ev_pbytes[q] * (double)work[q];
         ++timer_n;
       }
     }
@@ -260,6 +351,13 @@ struct Ctx {
     if (own_stream && st) cudaStreamDestroy(st);
   }
 
+  // core nodes x blocks summed over the instances (the coupling reduction's work)
+  long long cpl_nodes() const {
+    long long t = 0;
+    for (size_t i = 0; i < inst.size() && i < h_inst.size(); ++i)
+      t += (long long)inst[i].g.nx * inst[i].g.nz * (h_inst[i].blk1 - h_inst[i].blk0);
+    return t;
+  }
   template <typename T> Work<T> &work();
   template <typename T> LevelView<T> viewA();
   template <typename T> LevelView<T> viewM(int l);
@@ -292,7 +390,7 @@ struct Ctx {
                                     typename cplx<T>::t *&cur, typename cplx<T>::t *&oth, int l);
   template <typename T> void resid_restrict(int cj, int l, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
                                             typename cplx<T>::t *bc);
-  void timer_end(int streams, size_t elem_bytes);
+  void timer_end(int streams, int pass_streams, size_t elem_bytes);
   template <typename T> void apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *y,
                                         const typename cplx<T>::t *a, int nd);
   template <typename T> void jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
@@ -312,6 +410,8 @@ struct Ctx {
                                    int *iters, long long *inner, const typename cplx<T>::t *u);
   template <typename T> void multidot(long long n, int nv, T *const *dV, const T *w, double *out, int acc,
                                       bool exact);
+  template <typename T> void multi_axpy(long long n, int nv, T *const *dV, const double *coef, double sign, T *w);
+  template <typename T> void fgmres_cycle_graph(const fwi_opts &o, double eps, T *x, const typename cplx<T>::t *u);
   double orth_loss = 0.0;   // max |I - V^T V| of the FGMRES bases of the last KKT solve (check_orth)
   void forward(const fwi_opts &o, fwi_stats *stats);
   template <typename T> int refined_solve(const double2 *rhs, double2 *x, int cj, const fwi_opts &o,
@@ -321,6 +421,7 @@ struct Ctx {
   void sync() {
     CK(cudaStreamSynchronize(st));
     if (ev_used) harvest();
+    if (g_prof.used) g_prof.harvest();
   }
 };
 
@@ -343,8 +444,9 @@ template <> const double *gam_ptr<double>(Ctx &c) { return c.gam64.p; }
 template <typename T>
 void Ctx::launch_coarse(const CoarseArgs &ca, size_t smem, const typename cplx<T>::t *b, typename cplx<T>::t *x,
                         int cj) {
-  if (cj) k_coarse_cycle<T, true><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
-  else k_coarse_cycle<T, false><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), gam_ptr<T>(*this), b, x);
+  KPROF("k_coarse_cycle", ca.ls, 2.0 * sizeof(typename cplx<T>::t) * lv[ca.ls].field, st);
+  if (cj) k_coarse_cycle<T, true><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+  else k_coarse_cycle<T, false><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
   KCHECK();
 }
 
@@ -519,7 +621,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   // remaining levels (3 vectors and the operator data each) fit in the per-CTA
   // budget (c64);
   // complex128 may need a coarser start.
-  const size_t budget = 200 * 1024;
+  const size_t budget = 220 * 1024;
   auto smem_from = [&](int l0, size_t elem) {
     size_t mx = 0;
     for (auto &I : inst) {
@@ -605,6 +707,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   dax.upload(hax, st);
   st64.alloc(st_tot);
   st32.alloc(st_tot);
+  KPROF("k_stretch_setup", -1, 0, st);
   k_stretch_setup<<<(int)axes.size(), 128, 0, st>>>(dax.p, (int)axes.size(), st64.p, st32.p);
   KCHECK();
   // gamma on every level
@@ -613,12 +716,14 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   for (int i = 0; i < n_inst; ++i) {
     Instance &I = inst[i];
     long long n0 = (long long)I.Nx * I.Nz;
+    KPROF("k_gamma_fill", -1, 0, st);
     k_gamma_fill<<<grid_for(n0, 256), 256, 0, st>>>(I.layer.p, I.s.p, I.Nx, I.Nz, I.g.npml, I.g.nx, I.g.nz,
                                                      gam64.p + gam_off[i * MAX_LEVELS], gam32.p + gam_off[i * MAX_LEVELS]);
     KCHECK();
     for (int l = 1; l < I.nlev; ++l) {
       int nxf, nzf, nxc, nzc;
       dims(I, l - 1, nxf, nzf); dims(I, l, nxc, nzc);
+      KPROF("k_gamma_restrict", -1, 0, st);
       k_gamma_restrict<<<grid_for((long long)nxc * nzc, 256), 256, 0, st>>>(
           gam64.p + gam_off[i * MAX_LEVELS + l - 1], nxf, nzf, nxc, nzc, gam64.p + gam_off[i * MAX_LEVELS + l],
           gam32.p + gam_off[i * MAX_LEVELS + l]);
@@ -627,6 +732,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   }
   // diagonal of every operator and its inverse
   dg64.alloc(dg_tot); dgi64.alloc(dg_tot); dg32.alloc(dg_tot); dgi32.alloc(dg_tot);
+  KPROF("k_diag_setup", -1, 0, st);
   k_diag_setup<<<(int)h_ops.size(), 256, 0, st>>>(d_ops.p, st64.p, gam64.p, dg64.p, dgi64.p, dg32.p, dgi32.p);
   KCHECK();
   // coarsest inverses
@@ -655,8 +761,10 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
     dioff.upload(inv_off_l, st);
     dstat.alloc(1);
     dstat.zero(st);
+    KPROF("k_coarse_assemble", -1, 0, st);
     k_coarse_assemble<<<(int)coarse_ops.size(), 256, 0, st>>>(d_ops.p, dids.p, daoff.p, st64.p, gam64.p, aug.p);
     KCHECK();
+    KPROF("k_gauss_jordan", -1, 0, st);
     k_gauss_jordan<<<(int)coarse_ops.size(), 256, 0, st>>>(ddims.p, daoff.p, dioff.p, aug.p, inv.p, dstat.p);
     KCHECK();
     int hs = 0;
@@ -769,6 +877,8 @@ template <typename T> void Ctx::ensure_work(const fwi_opts &o) {
   }
   if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
   w.graph_key.clear();
+  if (w.cyc) { cudaGraphExecDestroy(w.cyc); w.cyc = nullptr; }
+  w.cyc_key.clear();
   sync();
   w.ready = 1;
   (void)o;
@@ -793,6 +903,10 @@ template <typename T> void Ctx::ensure_krylov(const fwi_opts &o) {
   w.H.alloc((size_t)(m + 1) * m); w.cs.alloc(m); w.sn.alloc(m); w.g.alloc(m + 1);
   w.hcol.alloc(m + 1); w.hsum.alloc(m + 1); w.y.alloc(m);
   w.rhs.alloc(nkkt); w.sol.alloc(nkkt);
+  w.wst.alloc(nkkt);
+  w.ctl.alloc(1);
+  if (w.cyc) { cudaGraphExecDestroy(w.cyc); w.cyc = nullptr; }
+  w.cyc_key.clear();
   sync();
 }
 
@@ -818,6 +932,7 @@ void Ctx::field_op(int mode, int cj, T wj, const typename cplx<T>::t *x, const t
   // the only levels this is called on
   if (L.n_strips == 0) fail(FWI_E_INVAL, "internal: no column strips on a global multigrid level");
   const int grid = (L.n_strips + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32);
+  KPROF(mode == FM_APPLY ? "k_field_op_march:apply" : mode == FM_RESID ? "k_field_op_march:resid" : mode == FM_JACOBI ? "k_field_op_march:jacobi" : "k_field_op_march:jacobi0", opA ? 0 : level, (mode == FM_APPLY || mode == FM_JACOBI0 ? 2.0 : 3.0) * sizeof(typename cplx<T>::t) * lv[opA ? 0 : level].field, st);
   if (cj) launch_march_cj<T, true>(grid, st, L, mode, wj, x, b, y);
   else launch_march_cj<T, false>(grid, st, L, mode, wj, x, b, y);
   KCHECK();
@@ -840,16 +955,17 @@ bool Ctx::timer_begin(int level, LevelView<T> &L) {
     cudaEvent_t a, b2;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b2));
-    ev_a.push_back(a); ev_b.push_back(b2); ev_bytes.push_back(0.0);
+    ev_a.push_back(a); ev_b.push_back(b2); ev_bytes.push_back(0.0); ev_pbytes.push_back(0.0);
   }
   L.work = ev_work.p + ev_used;
   CK(cudaEventRecord(ev_a[ev_used], st));
   return true;
 }
 
-void Ctx::timer_end(int streams, size_t elem_bytes) {
+void Ctx::timer_end(int streams, int pass_streams, size_t elem_bytes) {
   CK(cudaEventRecord(ev_b[ev_used], st));
   ev_bytes[ev_used] = (double)streams * (double)elem_bytes;
+  ev_pbytes[ev_used] = (double)pass_streams * (double)elem_bytes;
   ++ev_used;
   if (ev_used >= 4096) sync();
 }
@@ -862,6 +978,7 @@ void Ctx::apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *
   LevelView<T> L = viewA<T>();
   const int grid = std::max(1, (L.n_strips + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
   const T w = 0;
+  KPROF("k_field_op_march:apply+dots", 0, 3.0 * sizeof(typename cplx<T>::t) * F0, st);
   if (nd == 1) {
     if (cj) k_field_op_march<T, true, FM_APPLY, 1><<<grid, MARCH_THREADS, 0, st>>>(L, w, x, a, y, partial_s.p);
     else k_field_op_march<T, false, FM_APPLY, 1><<<grid, MARCH_THREADS, 0, st>>>(L, w, x, a, y, partial_s.p);
@@ -880,6 +997,7 @@ void Ctx::jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cpl
   LevelView<T> L = viewM<T>(level);
   const bool timed = timer_begin<T>(level, L);
   const int grid = std::max(1, (L.n_strips2 + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
+  KPROF("k_jacobi2_march", level, (x == nullptr ? 5.0 : 6.0) * sizeof(typename cplx<T>::t) * lv[level].field, st);
   if (x == nullptr) {
     if (cj) k_jacobi2_march<T, true, true><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
     else k_jacobi2_march<T, false, true><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
@@ -888,8 +1006,10 @@ void Ctx::jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cpl
     else k_jacobi2_march<T, false, false><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
   }
   KCHECK();
-  // algorithmic bytes per node: b, y (and x)
-  if (timed) timer_end(x == nullptr ? 2 : 3, sizeof(typename cplx<T>::t));
+  // algorithmic bytes per node: x, b and the result of each of the two sweeps
+  // (the first sweep from zero reads no x); the fused pass itself reads b
+  // (and x) and writes y once
+  if (timed) timer_end(x == nullptr ? 5 : 6, x == nullptr ? 2 : 3, sizeof(typename cplx<T>::t));
 }
 
 // b_{l+1} = P^T (b_l - M_l x_l) on every block.
@@ -900,6 +1020,7 @@ void Ctx::resid_restrict(int cj, int l, const typename cplx<T>::t *x, const type
   const int n = lv[l].n_rstrips;   // built for every global level l < ls, the only levels that restrict
   if (n == 0) fail(FWI_E_INVAL, "internal: no restriction strips on a global multigrid level");
   const int grid = (n + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32);
+  KPROF("k_resid_restrict_march", l, sizeof(typename cplx<T>::t) * (2.0 * lv[l].field + lv[l + 1].field), st);
   if (cj) k_resid_restrict_march<T, true><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
   else k_resid_restrict_march<T, false><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
   KCHECK();
@@ -910,6 +1031,7 @@ void Ctx::block_dots(int nd, const typename cplx<T>::t *a0, const typename cplx<
                      const typename cplx<T>::t *a1, const typename cplx<T>::t *b1,
                      const typename cplx<T>::t *a2, const typename cplx<T>::t *b2) {
   LevelView<T> L = viewA<T>();
+  KPROF("k_block_dots", 0, 2.0 * nd * sizeof(typename cplx<T>::t) * F0, st);
   k_block_dots<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, nd, a0, b0, a1, b1, a2, b2, partial.p);
   KCHECK();
 }
@@ -976,6 +1098,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
       resid_restrict<T>(cj, l, cur, bl, w.lb[l + 1].p);
       T2 *xc = cyc(l + 1, w.lb[l + 1].p, w.lx[l + 1].p, w.lt[l + 1].p);
+      KPROF("k_prolong_add", l, sizeof(T2) * (2.0 * lv[l].field + lv[l + 1].field), st);
       k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
       KCHECK();
     }
@@ -1020,6 +1143,7 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
       resid_restrict<T>(cj, l, cur, bl, lb[l + 1]);
       T2 *xc = cyc(l + 1, lb[l + 1], lx[l + 1], lt[l + 1]);
+      KPROF("k_prolong_add", l, sizeof(T2) * (2.0 * lv[l].field + lv[l + 1].field), st);
       k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
       KCHECK();
     }
@@ -1041,15 +1165,18 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   const int nt = L.n_tiles;
   const int sb = (B + BICG_WARPS - 1) / BICG_WARPS;
   auto upd = [&](int opk, T2 *y, const T2 *a, const T2 *c) {
+    KPROF("k_bicg_update", opk, (opk == 0 ? 4.0 : opk == 1 ? 3.0 : opk == 3 ? 2.0 : 1.0) * sizeof(typename cplx<T>::t) * F0, st);
     k_bicg_update<T><<<nt, TILE_THREADS, 0, st>>>(L, opk, w.bst.p, y, a, c);
     KCHECK();
   };
   auto scal = [&](int stage) {
+    KPROF("k_bicg_scalars", -1, 0, st);
     k_bicg_scalars<<<sb, BICG_WARPS * 32, 0, st>>>(B, lv[0].t0.p, lv[0].t1.p, partial.p, w.bst.p, stage, tol, w.done.p);
     KCHECK();
   };
   // stages whose dots come from the strip kernels (operator apply fused with dots)
   auto scal_s = [&](int stage) {
+    KPROF("k_bicg_scalars", -1, 0, st);
     k_bicg_scalars<<<sb, BICG_WARPS * 32, 0, st>>>(B, lv[0].s0.p, lv[0].s1.p, partial_s.p, w.bst.p, stage, tol, w.done.p);
     KCHECK();
   };
@@ -1082,6 +1209,7 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
     apply_dots<T>(cj, w.sh.p, w.t.p, w.s.p, 2);                        // t = A sh, <t, s>, <t, t>
     scal_s(3);
     // x += alpha ph + omega sh; r = s - omega t; <r, r>, <rh, r>
+    KPROF("k_bicg_xr", 0, 8.0 * sizeof(typename cplx<T>::t) * F0, st);
     k_bicg_xr<T><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, x, w.ph.p, w.sh.p, w.s.p, w.r.p, w.t.p, w.rh.p,
                                               partial.p);
     KCHECK();
@@ -1103,15 +1231,18 @@ void Ctx::kkt_matvec(const T *xi, T *y, double eps, const typename cplx<T>::t *u
   T2 *ylm = (T2 *)(y + 2 * F0);
   T *ys = y + 4 * F0;
   LevelView<T> L = viewA<T>();
+  KPROF("k_kkt_rows", 0, 5.0 * sizeof(typename cplx<T>::t) * F0, st);
   k_kkt_rows<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, d_inst.p, cfK.p, u, du, lm, ds, yu, ylm);
   KCHECK();
   if (n_F) {
+    KPROF("k_kkt_F", 0, 3.0 * sizeof(typename cplx<T>::t) * n_F, st);
     k_kkt_F<T><<<grid_for(n_F, 128, 1 << 20), 128, 0, st>>>(n_F, d_F_node.p, d_F_w2.p, du, yu);
     KCHECK();
   }
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
   dim3 g((unsigned)((mx + 127) / 128), (unsigned)inst.size());
+  KPROF("k_coupling_reduce", 0, 2.0 * sizeof(typename cplx<T>::t) * cpl_nodes() + 2.0 * sizeof(T) * Nc, st);
   k_coupling_reduce<T, T><<<g, dim3(128, CPL_ROWS), 0, st>>>(d_inst.p, d_blk_off.p, cfK.p, u, lm, ds, eps, 0, ys);
   KCHECK();
 }
@@ -1135,10 +1266,12 @@ void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count, const t
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
   dim3 g((unsigned)((mx + 127) / 128), (unsigned)inst.size());
+  KPROF("k_coupling_reduce", 1, 2.0 * sizeof(typename cplx<T>::t) * cpl_nodes() + 2.0 * sizeof(T) * Nc, st);
   k_coupling_reduce<T, T><<<g, dim3(128, CPL_ROWS), 0, st>>>(d_inst.p, d_blk_off.p, cfK.p, u, zl, v2, o.eps, 1, zs);
   KCHECK();
   // z_u = A'^{-1} (v3 + P~ z_s)
   LevelView<T> L = viewA<T>();
+  KPROF("k_coupling_scatter", 0, 3.0 * sizeof(typename cplx<T>::t) * F0, st);
   k_coupling_scatter<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, d_inst.p, cfK.p, u, v3, zs, w.t0b.p);
   KCHECK();
   inner_solve<T>(w.t0b.p, zu, 0, iters, tol, o, count);
@@ -1185,10 +1318,23 @@ void Ctx::multidot(long long n, int nv, T *const *dV, const T *wv, double *out, 
   Work<T> &w = work<T>();
   for (int c0 = 0; c0 < nv; c0 += MD_CHUNK) {
     int c = std::min(MD_CHUNK, nv - c0);
+    KPROF(exact ? "k_multidot:fp64" : "k_multidot:runs", -1, (double)(c + 1) * n * sizeof(T), st);
     if (exact) k_multidot<T, true><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
     else k_multidot<T, false><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
     KCHECK();
+    KPROF("k_reduce_partials", -1, 0, st);
     k_reduce_partials<<<c, 32, 0, st>>>(c, FLAT_BLOCKS, w.partial_flat.p, out + c0, acc);
+    KCHECK();
+  }
+}
+
+// w += sign * sum_v coef[v] V_v over nv vectors, MD_CHUNK per launch.
+template <typename T>
+void Ctx::multi_axpy(long long n, int nv, T *const *dV, const double *coef, double sign, T *w) {
+  for (int c0 = 0; c0 < nv; c0 += MD_CHUNK) {
+    const int c = std::min(MD_CHUNK, nv - c0);
+    KPROF("k_multi_axpy", -1, (double)(c + 2) * n * sizeof(T), st);
+    k_multi_axpy<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, coef + c0, sign, w);
     KCHECK();
   }
 }
@@ -1197,11 +1343,120 @@ void Ctx::multidot(long long n, int nv, T *const *dV, const T *wv, double *out, 
 template <typename T>
 static void flat_dot(cudaStream_t st, long long n, const T *x, const T *y, double *partial, double *out,
                      bool exact = false) {
+  KPROF(exact ? "k_dot2:fp64" : "k_dot2:runs", -1, 2.0 * n * sizeof(T), st);
   if (exact) k_dot2<T, true><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
   else k_dot2<T, false><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
   KCHECK();
+  KPROF("k_reduce_partials", -1, 0, st);
   k_reduce_partials<<<1, 32, 0, st>>>(1, FLAT_BLOCKS, partial, out, 0);
   KCHECK();
+}
+
+// One restart cycle of FGMRES as a CUDA graph under device control: a WHILE
+// node whose body is one Arnoldi step (V[j] to the preconditioner's input,
+// the preconditioner, Z[j], the KKT product, classical Gram-Schmidt twice,
+// the norm, the Givens update, V[j+1], and k_fgmres_ctl, which advances j and
+// sets the node's condition), followed by the back substitution and
+// x += Z y.  The step index and the convergence test live in the device
+// control block w.ctl; the host reads it once per cycle.  The graph is
+// captured once per (hierarchy, options, wavefields) and replayed.
+template <typename T>
+void Ctx::fgmres_cycle_graph(const fwi_opts &o, double eps, T *x, const typename cplx<T>::t *u) {
+  Work<T> &w = work<T>();
+  char key[320];
+  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d|%d|%p", hier_key.c_str(), o.inner_iters,
+           o.mg_cycle, o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, eps, o.shift_beta, (const void *)u, w.m,
+           o.arnoldi_fp64, (void *)x);
+  if (w.cyc && w.cyc_key == key) return;
+  if (w.cyc) { cudaGraphExecDestroy(w.cyc); w.cyc = nullptr; }
+  const long long n = nkkt;
+  const int m = w.m;
+  const bool exact = o.arnoldi_fp64 != 0;
+  T *const *dV = w.dptrV.p;
+  T *const *dZ = w.dptrZ.p;
+  FgCtl *c = w.ctl.p;
+  const int nchunk = (m + 1 + MD_CHUNK - 1) / MD_CHUNK;
+  cudaGraph_t g;
+  CK(cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() { cudaGraphDestroy(g); }
+  } gguard{g};
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CK(cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  auto dots = [&](double *out) {          // out[0..j] = V[0..j] . wst, chunk by chunk
+    for (int q = 0; q < nchunk; ++q) {
+      if (exact) k_multidot_dev<T, true><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, 0, q * MD_CHUNK, dV, w.wst.p,
+                                                                              w.partial_flat.p);
+      else k_multidot_dev<T, false><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, 0, q * MD_CHUNK, dV, w.wst.p,
+                                                                          w.partial_flat.p);
+      KCHECK();
+      k_reduce_partials_dev<<<MD_CHUNK, 32, 0, st>>>(c, 0, q * MD_CHUNK, FLAT_BLOCKS, w.partial_flat.p, out);
+      KCHECK();
+    }
+  };
+  auto axpys = [&](T *const *VV, int which, const double *coef, double sign, T *y) {
+    for (int q = 0; q < nchunk; ++q) {
+      k_multi_axpy_dev<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, which, q * MD_CHUNK, VV, coef, sign, y);
+      KCHECK();
+    }
+  };
+  unsigned long long before = g_launches.load();
+  CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  try {
+    k_copy_indexed<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV, 0, w.vin.p, 1);      // vin = V[j]
+    KCHECK();
+    long long dummy = 0;
+    precond<T>(w.vin.p, w.zout.p, o, &dummy, u);
+    k_copy_indexed<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dZ, 0, w.zout.p, 0);     // Z[j] = zout
+    KCHECK();
+    kkt_matvec<T>(w.zout.p, w.wst.p, eps, u);
+    dots(w.hcol.p);
+    axpys(dV, 0, w.hcol.p, -1.0, w.wst.p);
+    dots(w.hsum.p);
+    axpys(dV, 0, w.hsum.p, -1.0, w.wst.p);
+    k_dadd_dev<<<1, 64, 0, st>>>(c, w.hcol.p, w.hsum.p);
+    KCHECK();
+    flat_dot<T>(st, n, w.wst.p, w.wst.p, w.partial_flat.p, w.scal.p + 2, exact);
+    k_givens_dev<<<1, 1, 0, st>>>(c, w.H.p, w.cs.p, w.sn.p, w.g.p, w.hcol.p, w.scal.p + 2, w.scal.p + 3,
+                                  w.scal.p + 4);
+    KCHECK();
+    k_scale_to_indexed<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV, w.scal.p + 3, w.wst.p);  // V[j+1]
+    KCHECK();
+    k_fgmres_ctl<<<1, 1, 0, st>>>(c, w.scal.p + 4, h);
+    KCHECK();
+  } catch (...) {
+    cudaGraph_t tmp;
+    cudaStreamEndCapture(st, &tmp);
+    throw;
+  }
+  CK(cudaStreamEndCapture(st, &body));
+  w.cyc_body_kernels = g_launches.load() - before;
+  before = g_launches.load();
+  // after the loop: back substitution and x += Z y (k vectors)
+  CK(cudaStreamBeginCaptureToGraph(st, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  try {
+    k_backsub_dev<<<1, 1, 0, st>>>(c, w.H.p, w.g.p, w.y.p);
+    KCHECK();
+    axpys(dZ, 1, w.y.p, 1.0, x);
+  } catch (...) {
+    cudaGraph_t tmp;
+    cudaStreamEndCapture(st, &tmp);
+    throw;
+  }
+  CK(cudaStreamEndCapture(st, &g));
+  w.cyc_tail_kernels = g_launches.load() - before;
+  g_launches.fetch_sub(w.cyc_body_kernels + w.cyc_tail_kernels);   // captured, not launched
+  CK(cudaGraphInstantiate(&w.cyc, g, 0));
+  w.cyc_key = key;
 }
 
 // Right-preconditioned flexible GMRES(m) (Saad 1993) on the KKT matrix, CGS2
@@ -1219,6 +1474,10 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
   T *const *dZ = w.dptrZ.p;
   CK(cudaMemsetAsync(x, 0, n * sizeof(T), st));
   const bool exact = o.arnoldi_fp64 != 0;
+  // device control of each restart cycle whenever the preconditioner is
+  // graph-replayable (fixed inner iterations); otherwise the host loop below
+  const bool devctl = o.use_graph && !(o.inner_tol > 0.0);
+  if (devctl) fgmres_cycle_graph<T>(o, eps, x, u);
   flat_dot<T>(st, n, rhs, rhs, w.partial_flat.p, w.scal.p, exact);
   CK(cudaMemcpyAsync(pin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
   sync();
@@ -1229,13 +1488,45 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
   double beta = bnorm;
   int total = 0;
   bool conv = false;
+  // loss of orthogonality of a cycle's basis V_0 .. V_k: max |delta_ij - V_i . V_j|
+  // (FP64 products; diagnostics only, one multi-dot per basis vector)
+  auto orth_check = [&](int k) {
+    if (k <= 0) return;
+    std::vector<double> hh(k + 1);
+    for (int jj = 0; jj <= k; ++jj) {
+      multidot<T>(n, jj + 1, dV, w.V.p + (size_t)jj * w.ld, w.hsum.p, 0, true);
+      CK(cudaMemcpyAsync(hh.data(), w.hsum.p, (jj + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      sync();
+      for (int ii = 0; ii <= jj; ++ii) orth_loss = std::max(orth_loss, std::fabs((ii == jj ? 1.0 : 0.0) - hh[ii]));
+    }
+  };
   while (total < maxit && !conv) {
     CK(cudaMemcpyAsync(w.scal.p + 1, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
+    KPROF("k_scale_inv", -1, 2.0 * n * sizeof(T), st);
     k_scale_inv<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, w.scal.p + 1, r, w.V.p);
     KCHECK();
     std::vector<double> g0(m + 1, 0.0);
     g0[0] = beta;
     CK(cudaMemcpyAsync(w.g.p, g0.data(), (m + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (devctl) {
+      // the whole cycle on the device; the host reads the control block once
+      FgCtl *hc = reinterpret_cast<FgCtl *>(pin);
+      hc->j = 0; hc->k = 0; hc->total = total; hc->state = 0; hc->m = m; hc->maxit = maxit;
+      hc->thr = tol * bnorm;
+      CK(cudaMemcpyAsync(w.ctl.p, hc, sizeof(FgCtl), cudaMemcpyHostToDevice, st));
+      CK(cudaGraphLaunch(w.cyc, st));
+      CK(cudaMemcpyAsync(hc, w.ctl.p, sizeof(FgCtl), cudaMemcpyDeviceToHost, st));
+      sync();
+      const int kk = hc->k;
+      g_launches.fetch_add(w.cyc_body_kernels * (unsigned long long)kk + w.cyc_tail_kernels);
+      if (inner) *inner += 2LL * o.inner_iters * B * kk;
+      total = hc->total;
+      const int state = hc->state;
+      if (state == 2) fail(FWI_E_NUMERIC, "non-finite residual in FGMRES");
+      if (state == 1) conv = true;
+      if (o.check_orth) orth_check(kk);
+      if (conv || total >= maxit) break;
+    } else {
     int k = 0;
     for (int j = 0; j < m && total < maxit; ++j) {
       T *vj = w.V.p + (size_t)j * w.ld;
@@ -1245,21 +1536,18 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
       kkt_matvec<T>(zj, wv, eps, u);
       // classical Gram-Schmidt, twice
       multidot<T>(n, j + 1, dV, wv, w.hcol.p, 0, exact);
-      for (int c0 = 0; c0 < j + 1; c0 += MD_CHUNK)
-        k_multi_axpy<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, std::min(MD_CHUNK, j + 1 - c0), dV + c0,
-                                                              w.hcol.p + c0, -1.0, wv);
-      KCHECK();
+      multi_axpy<T>(n, j + 1, dV, w.hcol.p, -1.0, wv);
       multidot<T>(n, j + 1, dV, wv, w.hsum.p, 0, exact);
-      for (int c0 = 0; c0 < j + 1; c0 += MD_CHUNK)
-        k_multi_axpy<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, std::min(MD_CHUNK, j + 1 - c0), dV + c0,
-                                                              w.hsum.p + c0, -1.0, wv);
-      KCHECK();
+      multi_axpy<T>(n, j + 1, dV, w.hsum.p, -1.0, wv);
+      KPROF("k_dadd", -1, 0, st);
       k_dadd<<<1, 64, 0, st>>>(j + 1, w.hcol.p, w.hsum.p);
       KCHECK();
       flat_dot<T>(st, n, wv, wv, w.partial_flat.p, w.scal.p + 2, exact);
+      KPROF("k_givens", -1, 0, st);
       k_givens<<<1, 1, 0, st>>>(j, m, w.H.p, w.cs.p, w.sn.p, w.g.p, w.hcol.p, w.scal.p + 2, w.scal.p + 3,
                                 w.scal.p + 4);
       KCHECK();
+      KPROF("k_scale_inv", -1, 2.0 * n * sizeof(T), st);
       k_scale_inv<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, w.scal.p + 3, wv, wv);
       KCHECK();
       CK(cudaMemcpyAsync(pin, w.scal.p + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1269,26 +1557,16 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
       if (!std::isfinite(pin[0])) fail(FWI_E_NUMERIC, "non-finite residual in FGMRES");
       if (pin[0] / bnorm <= tol) { conv = true; break; }
     }
-    if (o.check_orth && k > 0) {
-      // loss of orthogonality of this cycle's basis V_0 .. V_k: max |delta_ij - V_i . V_j|
-      // (FP64 products; diagnostics only, one multi-dot per basis vector)
-      std::vector<double> hh(k + 1);
-      for (int jj = 0; jj <= k; ++jj) {
-        multidot<T>(n, jj + 1, dV, w.V.p + (size_t)jj * w.ld, w.hsum.p, 0, true);
-        CK(cudaMemcpyAsync(hh.data(), w.hsum.p, (jj + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-        sync();
-        for (int ii = 0; ii <= jj; ++ii) orth_loss = std::max(orth_loss, std::fabs((ii == jj ? 1.0 : 0.0) - hh[ii]));
-      }
-    }
+    if (o.check_orth) orth_check(k);
+    KPROF("k_backsub", -1, 0, st);
     k_backsub<<<1, 1, 0, st>>>(k, m, w.H.p, w.g.p, w.y.p);
     KCHECK();
-    for (int c0 = 0; c0 < k; c0 += MD_CHUNK)
-      k_multi_axpy<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, std::min(MD_CHUNK, k - c0), dZ + c0, w.y.p + c0,
-                                                            1.0, x);
-    KCHECK();
+    multi_axpy<T>(n, k, dZ, w.y.p, 1.0, x);
     if (conv || total >= maxit) break;
+    }
     // restart from r = rhs - M x
     kkt_matvec<T>(x, w.tmp.p, eps, u);
+    KPROF("k_axpby", -1, 3.0 * n * sizeof(T), st);
     k_axpby<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, 1.0, rhs, -1.0, w.tmp.p);
     KCHECK();
     r = w.tmp.p;
@@ -1305,6 +1583,7 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
 
 template <> const float2 *Ctx::u_T<float>() {
   if (u_version32 != fwd_version) {
+    KPROF("k_convert", 0, 12.0 * 2 * F0, st);
     k_convert<double, float><<<grid_for(2 * F0, 256), 256, 0, st>>>(2 * F0, (const double *)u64.p, (float *)w32.u.p);
     KCHECK();
     u_version32 = fwd_version;
@@ -1369,12 +1648,14 @@ int Ctx::refined_solve(const double2 *rhs, double2 *x, int cj, const fwi_opts &o
     prev = nb;
     for (int b = 0; b < B; ++b) fac[b] = nb[b] > 0.0 ? 1.0 / nb[b] : 0.0;
     CK(cudaMemcpyAsync(blkfac.p, fac.data(), B * sizeof(double), cudaMemcpyHostToDevice, st));
+    KPROF("k_blk_scale", 0, (16.0 + sizeof(typename cplx<T>::t)) * F0, st);
     k_blk_scale<double, T, T><<<nt, TILE_THREADS, 0, st>>>(LT, (const double *)rho64.p, blkfac.p, (T *)rT, 0);
     KCHECK();
     long long cnt = 0;
     inner_solve<T>(rT, eT, cj, iters, inner_tol, o, &cnt);
     if (stats) stats->inner_iters += cnt;
     CK(cudaMemcpyAsync(blkfac.p, nb.data(), B * sizeof(double), cudaMemcpyHostToDevice, st));
+    KPROF("k_blk_scale", 0, (sizeof(typename cplx<T>::t) + 32.0) * F0, st);
     k_blk_scale<T, double, T><<<nt, TILE_THREADS, 0, st>>>(LT, (const T *)eT, blkfac.p, (double *)x, 1);
     KCHECK();
     field_op<double>(FM_RESID, cj, 0.0, x, rhs, rho64.p, true, 0);
@@ -1391,6 +1672,7 @@ void Ctx::forward(const fwi_opts &o, fwi_stats *stats) {
   u64.alloc(F0);
   f64.alloc(F0);
   f64.zero(st);
+  KPROF("k_set_sources", -1, 0, st);
   k_set_sources<<<grid_for(B, 128), 128, 0, st>>>(B, d_src_node.p, d_src_amp.p, f64.p);
   KCHECK();
   int rc = o.precision == FWI_C128 ? refined_solve<double>(f64.p, u64.p, 0, o, stats)
@@ -1419,6 +1701,7 @@ void Ctx::forward(const fwi_opts &o, fwi_stats *stats) {
     }
   }
   if (nrec) {
+    KPROF("k_rec_residual", -1, 0, st);
     k_rec_residual<<<grid_for(nrec, 128, 1 << 20), 128, 0, st>>>(nrec, d_rec_node.p, u64.p, have_d ? dd.p : nullptr,
                                                                  q.p, r.p, have_d ? 1 : 0);
     KCHECK();
@@ -1440,6 +1723,7 @@ void Ctx::forward(const fwi_opts &o, fwi_stats *stats) {
   de0.upload(e0, st);
   de1.upload(e1, st);
   misfit_d.alloc(inst.size());
+  KPROF("k_misfit", -1, 0, st);
   k_misfit<<<(int)inst.size(), 256, 0, st>>>(de0.p, de1.p, d_rec_w.p, r.p, misfit_d.p);
   KCHECK();
   misfit.assign(inst.size(), 0.0);
@@ -1459,6 +1743,7 @@ void Ctx::forward(const fwi_opts &o, fwi_stats *stats) {
 void Ctx::seg_norms(const double *x) {
   const int nb = 64;
   dim3 g(nb, (unsigned)h_segs.size());
+  KPROF("k_seg_norm2", -1, 8.0 * nkkt, st);
   k_seg_norm2<double><<<g, FLAT_THREADS, 0, st>>>(d_segs.p, x, seg_partial.p, nb);
   KCHECK();
 }
@@ -1475,6 +1760,7 @@ void Ctx::write_ctrl(const double *src_ctrl_dev, double *dst, int on_device, con
   f.upload(hf, st);
   double *target = dst;
   if (!on_device) { out.alloc(Nc); target = out.p; }
+  KPROF("k_seg_scale", -1, 16.0 * Nc, st);
   k_seg_scale<double, double><<<dim3(64, (unsigned)cs.size()), 256, 0, st>>>(dcs.p, src_ctrl_dev, f.p, target);
   KCHECK();
   if (!on_device) CK(cudaMemcpyAsync(dst, out.p, Nc * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1493,9 +1779,11 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
   b64.zero(st);
   // b_u = Q^T W^T W r (FP64 field in the du slot)
   int nrec = (int)rec_node.size();
-  if (n_unique)
+  if (n_unique) {
+    KPROF("k_rec_scatter", -1, 0, st);
     k_rec_scatter<<<grid_for(n_unique, 128, 1 << 20), 128, 0, st>>>(n_unique, d_unode.p, d_uoff.p, d_uidx.p, d_rec_w.p,
                                                                     r.p, (double2 *)b64.p);
+  }
   KCHECK();
   (void)nrec;
   {
@@ -1507,6 +1795,7 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
     inst_gref.upload(gr, st);
     long long mx = 0;
     for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
+    KPROF("k_ctrl_rhs", -1, 0, st);
     k_ctrl_rhs<<<dim3(grid_for(mx, 256), (unsigned)inst.size()), 256, 0, st>>>(d_inst.p, dsp.p, inst_gref.p, o.eps,
                                                                               o.include_Ls_n, b64.p + 4 * F0);
     KCHECK();
@@ -1553,23 +1842,28 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
     int left = o.max_outer - outer;
     if (c128) {
       Work<double> &w = w64;
+      KPROF("k_seg_scale", -1, 16.0 * nkkt, st);
       k_seg_scale<double, double><<<g, 256, 0, st>>>(d_segs.p, rho_k64.p, inst_fac.p, w.rhs.p);
       KCHECK();
       fgmres<double>(w.rhs.p, w.sol.p, std::max(o.tol * 0.5, 1e-14), left, o.eps, o, &outer, &inner, u_T<double>());
       inst_fac.upload(back, st);
+      KPROF("k_seg_axpy", -1, 24.0 * nkkt, st);
       k_seg_axpy<double><<<g, 256, 0, st>>>(d_segs.p, w.sol.p, inst_fac.p, xi64.p);
       KCHECK();
     } else {
       Work<float> &w = w32;
+      KPROF("k_seg_scale", -1, 12.0 * nkkt, st);
       k_seg_scale<double, float><<<g, 256, 0, st>>>(d_segs.p, rho_k64.p, inst_fac.p, w.rhs.p);
       KCHECK();
       fgmres<float>(w.rhs.p, w.sol.p, o.sweep_tol, left, o.eps, o, &outer, &inner, u_T<float>());
       inst_fac.upload(back, st);
+      KPROF("k_seg_axpy", -1, 20.0 * nkkt, st);
       k_seg_axpy<float><<<g, 256, 0, st>>>(d_segs.p, w.sol.p, inst_fac.p, xi64.p);
       KCHECK();
     }
     // rho = b - M xi in FP64 (c128 matvec with the FP64 wavefields)
     kkt_matvec<double>(xi64.p, rho_k64.p, o.eps, u64.p);
+    KPROF("k_axpby", -1, 24.0 * nkkt, st);
     k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nkkt, 1.0, b64.p, -1.0, rho_k64.p);
     KCHECK();
     ++sweeps;
@@ -1594,9 +1888,11 @@ int Ctx::gradient(const fwi_opts &o, double *misfit_out, double *grad, int on_de
   DBuf<double2> rhs, lam;
   rhs.alloc(F0); lam.alloc(F0);
   rhs.zero(st);
-  if (n_unique)
+  if (n_unique) {
+    KPROF("k_rec_scatter", -1, 0, st);
     k_rec_scatter<<<grid_for(n_unique, 128, 1 << 20), 128, 0, st>>>(n_unique, d_unode.p, d_uoff.p, d_uidx.p, d_rec_w.p,
                                                                     r.p, rhs.p);
+  }
   KCHECK();
   int rc = o.precision == FWI_C128 ? refined_solve<double>(rhs.p, lam.p, 1, o, stats)
                                    : refined_solve<float>(rhs.p, lam.p, 1, o, stats);
@@ -1606,6 +1902,7 @@ int Ctx::gradient(const fwi_opts &o, double *misfit_out, double *grad, int on_de
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
   dim3 gr((unsigned)((mx + 127) / 128), (unsigned)inst.size());
+  KPROF("k_coupling_reduce", 2, 32.0 * cpl_nodes() + 8.0 * Nc, st);
   k_coupling_reduce<double, double><<<gr, dim3(128, CPL_ROWS), 0, st>>>(d_inst.p, d_blk_off.p, cfG.p, u64.p,
                                                                  lam.p, nullptr, 0.0, 2, target);
   KCHECK();
@@ -1641,6 +1938,7 @@ void Ctx::apply_update(double *ds, int on_device) {
   dsp.upload(sp, st);
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
+  KPROF("k_update_model", -1, 0, st);
   k_update_model<<<dim3(grid_for(mx, 256), (unsigned)inst.size()), 256, 0, st>>>(d_inst.p, dsp.p, dsd.p);
   KCHECK();
   if (ds) {
@@ -1686,6 +1984,7 @@ struct NormalOp {
   // out = eps * v + Re(P~^H lambda)  (per core node, fixed block order)
   void couple(const double2 *lam, const double *v, double eps, double *out) {
     cudaStream_t st = c.st;
+    KPROF("k_coupling_reduce", 3, 32.0 * c.cpl_nodes() + 16.0 * c.Nc, st);
     k_coupling_reduce<double, double><<<gr, dim3(128, CPL_ROWS), 0, st>>>(c.d_inst.p, c.d_blk_off.p, c.cfK.p,
                                                                         c.u64.p, lam, v, eps, 3, out);
     KCHECK();
@@ -1694,9 +1993,11 @@ struct NormalOp {
   void adjoint_of_receivers(const double2 *q, double2 *lam) {
     cudaStream_t st = c.st;
     CK(cudaMemsetAsync(fa.p, 0, c.F0 * sizeof(double2), st));
-    if (c.n_unique)
+    if (c.n_unique) {
+      KPROF("k_rec_scatter", -1, 0, st);
       k_rec_scatter<<<grid_for(c.n_unique, 128, 1 << 20), 128, 0, st>>>(c.n_unique, c.d_unode.p, c.d_uoff.p,
                                                                         c.d_uidx.p, c.d_rec_w.p, q, fa.p);
+    }
     KCHECK();
     solve(fa.p, lam, 1);
   }
@@ -1704,19 +2005,23 @@ struct NormalOp {
   void apply(const double *v, double eps, double *out) {
     cudaStream_t st = c.st;
     LevelView<double> L64 = c.viewA<double>();
+    KPROF("k_coupling_scatter", 0, 48.0 * c.F0, st);
     k_coupling_scatter<double><<<L64.n_tiles, TILE_THREADS, 0, st>>>(L64, c.d_inst.p, c.cfK.p, c.u64.p, zero.p, v,
                                                                      fb.p);
     KCHECK();
     solve(fb.p, fa.p, 0);                                  // du = A'^{-1} P~ v
     const int nrec = (int)c.rec_node.size();
-    if (nrec)
+    if (nrec) {
+      KPROF("k_rec_residual", -1, 0, st);
       k_rec_residual<<<grid_for(nrec, 128, 1 << 20), 128, 0, st>>>(nrec, c.d_rec_node.p, fa.p, nullptr, qv.p,
                                                                    rdummy.p, 0);
+    }
     KCHECK();
     adjoint_of_receivers(qv.p, fb.p);                      // lambda = A'^{-H} F du
     couple(fb.p, v, eps, out);
   }
   double dot(const double *a, const double *b) {
+    KPROF("k_dot2", -1, 16.0 * nc, c.st);
     k_dot2<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, c.st>>>(nc, a, b, part.p);
     KCHECK();
     std::vector<double> h(FLAT_BLOCKS);
@@ -1763,6 +2068,7 @@ int Ctx::rsgn_solve(const fwi_opts &o, fwi_stats *stats) {
     inst_gref.upload(gref, st);
     DBuf<double> bsfull;
     bsfull.alloc(nkkt);
+    KPROF("k_ctrl_rhs", -1, 0, st);
     k_ctrl_rhs<<<dim3(grid_for(mx, 256), (unsigned)inst.size()), 256, 0, st>>>(d_inst.p, dsp.p, inst_gref.p, o.eps,
                                                                               o.include_Ls_n, bsfull.p + 4 * F0);
     KCHECK();
@@ -1785,13 +2091,17 @@ int Ctx::rsgn_solve(const fwi_opts &o, fwi_stats *stats) {
     const double php = N.dot(p.p, hp.p);
     if (!std::isfinite(php) || !(php > 0.0)) fail(FWI_E_NUMERIC, "reduced-space CG: p^T H p is not positive");
     const double alpha = rho / php;
+    KPROF("k_axpby", -1, 24.0 * nc, st);
     k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, alpha, p.p, 1.0, x);
+    KCHECK();
+    KPROF("k_axpby", -1, 24.0 * nc, st);
     k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, -alpha, hp.p, 1.0, rr.p);
     KCHECK();
     const double rho_new = N.dot(rr.p, rr.p);
     ++it;
     rel = std::sqrt(rho_new) / gn;
     if (rel <= o.tol) { status = FWI_OK; break; }
+    KPROF("k_axpby", -1, 24.0 * nc, st);
     k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, 1.0, rr.p, rho_new / rho, p.p);
     KCHECK();
     rho = rho_new;
@@ -1827,6 +2137,7 @@ int Ctx::normal_lambda_max(const fwi_opts &o, int iters, double *lambda, fwi_sta
     const double wn = std::sqrt(N.dot(w.p, w.p));
     if (!std::isfinite(wn)) fail(FWI_E_NUMERIC, "non-finite power iterate");
     if (!(wn > 0.0)) { lam = 0.0; break; }
+    KPROF("k_axpby", -1, 24.0 * nc, st);
     k_axpby<double><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(nc, 1.0 / wn, w.p, 0.0, v.p);
     KCHECK();
   }
@@ -1996,8 +2307,10 @@ int fwi_set_model(fwi_ctx *ctx, int inst, const double *gamma_core, double gamma
     fwi::DBuf<int> flag;
     flag.alloc(1);
     flag.zero(c.st);
+    KPROF("k_model_stats", -1, 8.0 * n, c.st);
     fwi::k_model_stats<<<FLAT_BLOCKS, FLAT_THREADS, 0, c.st>>>((long long)n, I.s.p, part.p, flag.p);
     KCHECK();
+    KPROF("k_reduce_partials", -1, 0, c.st);
     fwi::k_reduce_partials<<<1, 32, 0, c.st>>>(1, FLAT_BLOCKS, part.p, part.p + FLAT_BLOCKS, 0);
     KCHECK();
     int hf = 0;
@@ -2016,6 +2329,7 @@ int fwi_set_model(fwi_ctx *ctx, int inst, const double *gamma_core, double gamma
   if (!I.has_model) {
     I.gamma_ref = gamma_ref > 0.0 ? gamma_ref : sum / (double)n;
     I.layer.alloc((size_t)I.Nx * I.Nz);
+    KPROF("k_gamma_pad", -1, 0, c.st);
     fwi::k_gamma_pad<<<fwi::grid_for((long long)I.Nx * I.Nz, 256), 256, 0, c.st>>>(I.s.p, I.Nx, I.Nz, I.g.npml,
                                                                                    I.g.nx, I.g.nz, I.layer.p);
     KCHECK();
@@ -2383,16 +2697,48 @@ unsigned long long fwi_kernel_launches(void) { return fwi::g_launches.load(); }
 
 unsigned long long fwi_memory_calls(void) { return fwi::g_memcalls.load(); }
 
-int fwi_stencil_timer(fwi_ctx *ctx, int enable, double *ms, double *bytes, long long *launches) {
+int fwi_stencil_timer(fwi_ctx *ctx, int enable, double *ms, double *bytes, long long *launches,
+                      double *pass_bytes) {
   API_BEGIN(ctx)
   Ctx &c = ctx->c;
   if (c.st) c.sync();
   if (ms) *ms = c.timer_ms;
   if (bytes) *bytes = c.timer_bytes;
   if (launches) *launches = c.timer_n;
+  if (pass_bytes) *pass_bytes = c.timer_pbytes;
   if (enable >= 0) {
     c.timer_on = enable > 0;
-    c.timer_ms = 0.0; c.timer_bytes = 0.0; c.timer_n = 0;
+    c.timer_ms = 0.0; c.timer_bytes = 0.0; c.timer_pbytes = 0.0; c.timer_n = 0;
+  }
+  return FWI_OK;
+  API_END(ctx)
+}
+
+int fwi_kernel_profile(fwi_ctx *ctx, int enable, char *buf, long long buflen) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  if (c.st) c.sync();
+  fwi::Prof &P = fwi::g_prof;
+  if (P.used) P.harvest();
+  if (buf) {
+    std::string js = "{\"gap_ms\": " + std::to_string(P.gap_ms) + ", \"gaps\": " + std::to_string(P.gaps) +
+                     ", \"rows\": [";
+    bool first = true;
+    char line[512];
+    for (auto &kv : P.rows) {
+      snprintf(line, sizeof line, "%s{\"kernel\": \"%s\", \"level\": %d, \"launches\": %lld, \"ms\": %.6f, \"bytes\": %.1f}",
+               first ? "" : ", ", kv.first.first.c_str(), kv.first.second, kv.second.n, kv.second.ms, kv.second.bytes);
+      js += line;
+      first = false;
+    }
+    js += "]}";
+    if ((long long)js.size() + 1 > buflen)
+      fwi::fail(FWI_E_INVAL, "fwi_kernel_profile: buffer too small, need " + std::to_string(js.size() + 1) + " bytes");
+    std::memcpy(buf, js.c_str(), js.size() + 1);
+  }
+  if (enable >= 0) {
+    P.clear();
+    P.on = enable > 0;
   }
   return FWI_OK;
   API_END(ctx)

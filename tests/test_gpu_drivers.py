@@ -158,8 +158,36 @@ def test_graph_replay_equals_direct_launches_and_precisions_agree(lib):
         ds, st = f.kkt_solve(opts)
         assert st["rel_res"] <= 1e-8
         out[name] = ds
+        out[name + "_iters"] = st["outer_iters"]
     assert _rel(out["graph"], out["direct"]) < 1e-12
+    assert out["graph_iters"] == out["direct_iters"]
     assert _rel(out["c128"], out["graph"]) < 1e-6
+    f.close()
+
+
+@pytest.mark.parametrize("restart,max_outer", [(5, 600), (4, 9)])
+def test_device_controlled_cycles_equal_the_host_loop(lib, restart, max_outer):
+    """With graph replay the FGMRES restart cycle runs as one CUDA graph under
+    device control (a WHILE node over the Arnoldi steps, the step index and
+    the convergence test on the device).  Over several restarts, and when the
+    iteration cap stops the solve (FWI_E_NOCONV), it takes the same steps as
+    the host-driven loop: same iteration count, same update."""
+    import paper_2204_06489_gb300 as P
+    wl = FI.micro_workload(seed=12, nx=41, nz=21, npml=8, n_src=3, n_rec=8)
+    Pm, f, prob, d = _setup(wl)
+    res = {}
+    for g in (1, 0):
+        opts = P.default_opts(eps=1e-2, tol=1e-8, restart=restart, max_outer=max_outer, use_graph=g)
+        f.forward(opts, want_data=False)
+        ds, st = f.kkt_solve(opts, allow_noconv=True)
+        res[g] = (ds, st)
+    assert res[1][1]["outer_iters"] == res[0][1]["outer_iters"]
+    assert res[1][1]["refinements"] == res[0][1]["refinements"]
+    assert _rel(res[1][0], res[0][0]) < 1e-12
+    if max_outer < 100:
+        assert res[1][1]["outer_iters"] == max_outer and res[1][1]["rel_res"] > 1e-8
+    else:
+        assert res[1][1]["rel_res"] <= 1e-8
     f.close()
 
 
@@ -249,4 +277,28 @@ def test_arnoldi_dot_precision_options(lib, fp64):
     assert st["rel_res"] <= 1e-7
     assert _rel(ds, K.delta_s(K.solve_direct())) < 1e-5
     assert 0.0 < st["orth_loss"] < 1e-5, st["orth_loss"]
+    f.close()
+
+
+def test_kernel_profile_counts_every_direct_launch(lib):
+    """fwi_kernel_profile brackets every direct launch: over one multigrid
+    cycle its launch total equals the library's launch counter, and the
+    level-0 two-sweep smoother rows carry the stated bytes (five complex
+    elements per node from zero, six otherwise)."""
+    wl = FI.micro_workload(seed=8, nx=61, nz=31, npml=8, n_src=2, n_rec=5)
+    P, f, prob, d = _setup(wl)
+    opts = P.default_opts()
+    n = f.layout()["field_elems"]
+    b = torch.ones(n, dtype=torch.complex64, device="cuda")
+    f.mg_cycle(b, opts)                                   # builds the hierarchy
+    f.kernel_profile(1)
+    l0 = lib.fwi_kernel_launches()
+    f.mg_cycle(b, opts)
+    launched = lib.fwi_kernel_launches() - l0
+    prof = f.kernel_profile(0)
+    assert sum(r["launches"] for r in prof["rows"]) == launched
+    rows = [r for r in prof["rows"] if r["kernel"] == "k_jacobi2_march" and r["level"] == 0]
+    assert len(rows) == 1 and rows[0]["launches"] == 2 and rows[0]["ms"] > 0
+    assert rows[0]["bytes"] == (5 + 6) * 8 * n
+    assert prof["gaps"] == launched - 1
     f.close()
