@@ -276,7 +276,7 @@ def run_extra_case(args):
         o.max_outer = args.max_outer
         _, table = tune_kkt(f, o, (2, 4, 6, 8, 12, 16, 24, 48), (2,), (30,))
         out["sweep"] = [{"inner_iters": n, "kkt_s": round(t, 3), "outer": k, "converged": ok}
-                        for n, wd, rs, t, k, ok in table]
+                        for n, wd, rs, t, k, ok, _, _ in table]
     elif args.case == "rsgn":
         o = P.Opts.from_buffer_copy(opts)
         o.max_outer = args.max_outer
@@ -548,8 +548,10 @@ def run_newton(args):
         f.set_model(0, wl.gamma_start)
         f.forward(opts, want_data=False)
         opts, table = tune_kkt(f, opts, (4, 6, 8, 12, 16), (1, 2), (30,))
-        tuned = [{"inner_iters": n, "wdepth": wd, "restart": rs, "s": round(t, 3), "outer": o, "ok": ok}
-                 for n, wd, rs, t, o, ok in table]
+        # second stage at the chosen schedule: strip height x coarse-cycle CTA size
+        opts, table2 = tune_kkt(f, opts, (opts.inner_iters,), (None,), (None,), (8, 16, 32), (512, 1024))
+        tuned = [{"inner_iters": n, "wdepth": wd, "restart": rs, "strip_rows": sr, "coarse_threads": ct,
+                  "s": round(t, 3), "outer": o, "ok": ok} for n, wd, rs, t, o, ok, sr, ct in table + table2]
     g0 = torch.from_numpy(wl.gamma_start).cuda()
     ds_dev = torch.zeros(wl.grid.nx * wl.grid.nz, dtype=torch.float64, device="cuda")
 
@@ -633,29 +635,36 @@ def run_newton(args):
         extras["c128"] = {"ms_step1": round(ms128, 1), "outer_iters": st128.outer_iters,
                           "rel_res": st128.rel_res, "mixed_ms_step1": round(sum(step1) / len(step1), 1),
                           "mixed_speedup": round(ms128 / (sum(step1) / len(step1)), 2)}
-        # (b) per-kernel table of step 1 with direct launches (no graph replay),
-        # CUDA events around every launch
+        # (b) per-kernel table of one whole trajectory (steps 1-5) with direct
+        # launches (no graph replay), CUDA events around every launch
         op = P.Opts.from_buffer_copy(opts)
         op.use_graph = 0
-        step_device(0, op)
+        for k in range(NEWTON_STEPS):                       # warm-up of the direct path
+            step_device(k, op)
         f.kernel_profile(1)
         e_a.record(stream)
-        stp = step_device(0, op)
+        stp = [step_device(k, op) for k in range(NEWTON_STEPS)]
         e_b.record(stream)
         torch.cuda.synchronize()
         prof = f.kernel_profile(0)
         kt = _kernel_table(prof, peak, e_a.elapsed_time(e_b))
-        kt["outer_iters"] = stp.outer_iters
-        kt["note"] = ("step 1 of the trajectory with direct launches; kernel_ms = sum of per-launch event times; "
-                      "gap_share_of_graph_step = 1 - kernel_ms / the timed (graph-replayed) step-1 time")
-        kt["gap_share_of_graph_step"] = round(1.0 - kt["kernel_ms"] / (sum(step1) / len(step1)), 4)
+        for r in kt["rows"]:
+            r["launches_per_step"] = round(r["launches"] / NEWTON_STEPS, 1)
+        traj_ms = sum(step_ms[k] for k in range(min(args.steps, NEWTON_STEPS)))
+        kt["outer_iters"] = [s.outer_iters for s in stp]
+        kt["note"] = (f"the {NEWTON_STEPS}-step trajectory with direct launches (no graph replay); kernel_ms = sum of "
+                      "per-launch event times; gap_share_of_graph_steps = 1 - kernel_ms / the timed (graph-replayed) "
+                      "time of the same trajectory")
+        if args.steps >= NEWTON_STEPS:
+            kt["gap_share_of_graph_steps"] = round(1.0 - kt["kernel_ms"] / traj_ms, 4)
         extras["kernel_table"] = kt
-        # (c) the two forms of the Arnoldi inner products, with the measured loss
-        # of orthogonality of the complex64 basis (max |I - V^T V|)
+        # (c) the three forms of the Arnoldi inner products (0 FP32 runs, 1 FP64
+        # products, 2 compensated Dot2), with the measured loss of orthogonality
+        # of the complex64 basis (max |I - V^T V|)
         arn = []
-        for fp64 in (1, 0):
+        for fp64 in (2, 1, 0):
             oa = P.Opts.from_buffer_copy(opts)
-            oa.arnoldi_fp64 = fp64
+            oa.arnoldi_dots = fp64
             oa.check_orth = 1
             f.set_model(0, g0)
             f.forward(oa, want_data=False)
@@ -663,7 +672,7 @@ def run_newton(args):
             t1 = time.perf_counter()
             _, sa = f.kkt_solve(oa, allow_noconv=True)
             torch.cuda.synchronize()
-            arn.append({"arnoldi_fp64": fp64, "outer_iters": sa["outer_iters"], "rel_res": sa["rel_res"],
+            arn.append({"arnoldi_dots": fp64, "outer_iters": sa["outer_iters"], "rel_res": sa["rel_res"],
                         "orth_loss": sa["orth_loss"], "kkt_s_with_check": round(time.perf_counter() - t1, 3)})
         extras["arnoldi"] = arn
     outer = sum(s.outer_iters for s in stats) / len(stats)
@@ -675,7 +684,8 @@ def run_newton(args):
            "data": "synthetic (seeded layered-faulted model; data from the library's forward modelling)",
            "config": {"workload": WORKLOAD, "blocks": 120, "grid_padded": "441x181", "eps": opts.eps,
                       "tol": 1e-6, "restart": opts.restart, "inner_iters": opts.inner_iters,
-                      "include_Ls_n": INCLUDE_LS_N,
+                      "include_Ls_n": INCLUDE_LS_N, "strip_rows": opts.strip_rows,
+                      "coarse_threads": opts.coarse_threads, "arnoldi_dots": opts.arnoldi_dots,
                       "mg": f"W(2,2) to level {opts.mg_wdepth}, V below",
                       "steps": f"each timed step is one of the {NEWTON_STEPS} Gauss-Newton steps of the "
                                f"trajectory from the starting model (reset after {NEWTON_STEPS})",

@@ -47,6 +47,16 @@ extern "C" {
 #define FWI_E_NOCONV (-4)  /* iteration cap reached; results and stats valid  */
 #define FWI_E_NUMERIC (-5) /* NaN/Inf detected, or gamma <= 0                 */
 
+/* ---- inner products of the FGMRES orthogonalisation (fwi_opts.arnoldi_dots) --
+ * RUNS: FP32 products summed in FP32 runs of 64 per thread, runs summed in FP64.
+ * FP64: every product formed and summed in FP64 (exact products of floats).
+ * COMP: compensated dot product (Dot2 of Ogita, Rump & Oishi 2005): exact FP32
+ *       product splitting and error-free sums per thread, as accurate as a dot
+ *       product in twice the working precision; threads summed in FP64. */
+#define FWI_DOT_RUNS 0
+#define FWI_DOT_FP64 1
+#define FWI_DOT_COMP 2
+
 /* ---- precision modes ---------------------------------------------------- */
 #define FWI_C128 0        /* complex128 throughout ("plain FP64 GPU form")       */
 #define FWI_C64_REFINE 1  /* complex64 bulk, FP64 dots / coarsest level / refinement */
@@ -90,11 +100,19 @@ typedef struct {
                              doubled (up to 8x) after a sweep that gains < 20x [60]   */
   int max_fwd_refine;     /* cap on forward refinement sweeps                  [20]   */
   int use_graph;          /* replay the preconditioner from a CUDA graph       [1]    */
-  int arnoldi_fp64;       /* FGMRES inner products (orthogonalisation, norms) with
-                             FP64 products and sums; 0: FP32 runs of complex64
-                             products summed in FP64 (faster, less exact)       [1]    */
+  int arnoldi_dots;       /* FGMRES inner products (orthogonalisation, norms) of complex64
+                             vectors: FWI_DOT_RUNS, FWI_DOT_FP64 or FWI_DOT_COMP (see below);
+                             complex128 vectors always use FP64                  [COMP] */
   int check_orth;         /* measure max |I - V^T V| of every FGMRES basis into
                              fwi_stats.orth_loss (diagnostics, costs extra dots) [0]   */
+  int strip_rows;         /* rows per warp of the column-strip stencil kernels (2..64) [16]  */
+  int coarse_threads;     /* threads per CTA of the shared-memory coarse cycle (512 | 1024) [512] */
+  int fwd_warm;           /* start the forward solve from the previous forward wavefields
+                             of this context (same tolerance; 0: from zero)      [1]    */
+  int outer_solver;       /* KKT Krylov method: 0 FGMRES(restart); 1 BiCGStab in the real
+                             inner product (eight KKT-size vectors, no basis; the
+                             memory-lean option of Sec. 7); outer_iters then counts
+                             BiCGStab iterations (two preconditioner applications each) [0] */
 } fwi_opts;
 
 typedef struct {
@@ -107,6 +125,7 @@ typedef struct {
   double t_setup_ms, t_forward_ms, t_solve_ms;
   double fwd_rel_res;     /* final max_b ||f_b - A u_b|| / ||f_b|| of the forward / adjoint solve */
   double orth_loss;       /* max |I - V^T V| over the FGMRES bases (with opts.check_orth), else 0 */
+  int fwd_warm;           /* 1 if the forward solve started from the previous wavefields */
 } fwi_stats;
 
 /* Layout of the context's buffers (element counts). */

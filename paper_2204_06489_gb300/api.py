@@ -24,6 +24,9 @@ FWI_E_NOCONV = -4
 FWI_E_NUMERIC = -5
 FWI_C128 = 0
 FWI_C64_REFINE = 1
+FWI_DOT_RUNS = 0
+FWI_DOT_FP64 = 1
+FWI_DOT_COMP = 2
 
 _ERRNAMES = {FWI_E_INVAL: "FWI_E_INVAL", FWI_E_NOMEM: "FWI_E_NOMEM", FWI_E_CUDA: "FWI_E_CUDA",
              FWI_E_NOCONV: "FWI_E_NOCONV", FWI_E_NUMERIC: "FWI_E_NUMERIC"}
@@ -47,15 +50,17 @@ class Opts(C.Structure):
                 ("inner_tol", C.c_double), ("mg_cycle", C.c_int), ("mg_wdepth", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("omega_jac", C.c_double), ("shift_beta", C.c_double), ("sigma_cap", C.c_double),
                 ("mg_levels", C.c_int), ("fwd_tol", C.c_double), ("fwd_iters", C.c_int),
-                ("max_fwd_refine", C.c_int), ("use_graph", C.c_int), ("arnoldi_fp64", C.c_int),
-                ("check_orth", C.c_int)]
+                ("max_fwd_refine", C.c_int), ("use_graph", C.c_int), ("arnoldi_dots", C.c_int),
+                ("check_orth", C.c_int), ("strip_rows", C.c_int), ("coarse_threads", C.c_int),
+                ("fwd_warm", C.c_int), ("outer_solver", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("refinements", C.c_int), ("fwd_sweeps", C.c_int),
                 ("inner_iters", C.c_longlong), ("rel_res", C.c_double), ("misfit", C.c_double),
                 ("t_setup_ms", C.c_double), ("t_forward_ms", C.c_double), ("t_solve_ms", C.c_double),
-                ("fwd_rel_res", C.c_double), ("orth_loss", C.c_double)]
+                ("fwd_rel_res", C.c_double), ("orth_loss", C.c_double),
+                ("fwd_warm", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -54,29 +54,38 @@ def tune_inner(fwi: FWI, b, base: Optional[Opts] = None, nus: Iterable[int] = (1
 
 
 def tune_kkt(fwi: FWI, base: Optional[Opts] = None, inner_iters: Iterable[int] = (4, 6, 8, 12),
-             wdepths: Iterable[int] = (None,), restarts: Iterable[int] = (None,)):
+             wdepths: Iterable[int] = (None,), restarts: Iterable[int] = (None,),
+             strip_rows: Iterable[int] = (None,), coarse_threads: Iterable[int] = (None,)):
     """Time one whole KKT solve (after ``fwi.forward``) per (inner-iteration
-    count, W-cycle depth, FGMRES restart) and keep the fastest that converges.
-    Returns (best Opts, table of (inner_iters, wdepth, restart, seconds, outer
-    iterations, converged))."""
+    count, W-cycle depth, FGMRES restart, column-strip height of the stencil
+    kernels, threads per CTA of the shared-memory coarse cycle) and keep the
+    fastest that converges.  Returns (best Opts, table of (inner_iters,
+    wdepth, restart, seconds, outer iterations, converged, strip_rows,
+    coarse_threads))."""
     import torch
     base = base if base is not None else default_opts()
     table = []
     best, best_t = None, math.inf
-    for n, wd, rs in itertools.product(inner_iters, wdepths, restarts):
+    for n, wd, rs, sr, ct in itertools.product(inner_iters, wdepths, restarts, strip_rows, coarse_threads):
         o = Opts.from_buffer_copy(base)
         o.inner_iters = n
         if wd is not None:
             o.mg_wdepth = wd
         if rs is not None:
             o.restart = rs
+        if sr is not None:
+            o.strip_rows = sr
+        if ct is not None:
+            o.coarse_threads = ct
+        if sr is not None:
+            fwi.kkt_solve(o, allow_noconv=True)      # untimed: rebuilds the strip tables for this height
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ds, st = fwi.kkt_solve(o, allow_noconv=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         ok = st["rel_res"] <= o.tol
-        table.append((n, o.mg_wdepth, o.restart, dt, st["outer_iters"], ok))
+        table.append((n, o.mg_wdepth, o.restart, dt, st["outer_iters"], ok, o.strip_rows, o.coarse_threads))
         if ok and dt < best_t:
             best, best_t = o, dt
     return (best if best is not None else base), table

@@ -8,7 +8,7 @@
 //   * kernels over fields are launched on "row tiles" (a tile is TILE_ROWS
 //     consecutive rows of one block, one warp per row: elementwise updates,
 //     dots, prolongation, small levels) or on "column strips" (a warp walks up
-//     to MARCH_ROWS rows of a band of columns of one block: the fine-level
+//     to fwi_opts.strip_rows rows of a band of columns of one block: the fine-level
 //     stencils).  Either way a CTA or warp belongs to exactly one block
 //     (per-block scalars, deterministic per-block reductions, ragged batches
 //     of different grid sizes without padding).
@@ -23,9 +23,6 @@
 #define MARCH2_COLS 60     // output columns per strip of the two-sweep smoother (two per lane)
 #define RM_COLS 14          // coarse columns per strip of the residual-restriction kernel
 #define RM_ROWS 8           // coarse rows per strip
-#ifndef MARCH_ROWS
-#define MARCH_ROWS 16
-#endif
 #define MARCH_THREADS 256
 
 namespace fwi {

@@ -27,6 +27,14 @@ namespace fwi {
 // the math headers promotes float operands to double).
 __device__ __forceinline__ float tfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double tfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+// Separately rounded product, sum and difference (never contracted into an
+// FMA): the error-free transformations of the compensated dot product need them.
+__device__ __forceinline__ float tmul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double tmul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float tadd_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double tadd_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float tsub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double tsub_rn(double a, double b) { return __dsub_rn(a, b); }
 
 // Loads of the small per-operator arrays (stretch factors, diagonal) that every
 // source of a frequency re-reads: keep them in L2 while the fields stream past.
@@ -45,6 +53,14 @@ __device__ __forceinline__ double2 ld_keep(const double2 *p) {
   asm("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(keep_policy()));
   return v;
 }
+
+// Per-block BiCGStab scalars (double2 = complex FP64):
+//   st[b] = {rho, rho_old, alpha, omega, beta, bnorm2(re), rnorm2(re)}, done[b]
+struct BiState {
+  double2 rho, rho_old, alpha, omega, beta;
+  double bnorm2, rnorm2;
+  int done, it;
+};
 
 // ---------------------------------------------------------------------------
 // stencil coefficients
@@ -113,7 +129,7 @@ __device__ __forceinline__ double2 ld_keep_p(const double2 *p, unsigned long lon
 
 // ---------------------------------------------------------------------------
 // Register-marching variant for the fine levels.  A warp owns a strip of
-// MARCH_COLS columns and up to MARCH_ROWS rows of one block and walks down it:
+// MARCH_COLS columns and up to fwi_opts.strip_rows rows of one block and walks down it:
 // lane l holds column col0 - 1 + l, so lanes 0 and 31 carry the strip's halo
 // columns and lanes 1 .. MARCH_COLS compute.  The three rows of x the stencil
 // needs (north, centre, south) stay in registers, east / west neighbours come
@@ -288,11 +304,23 @@ template <typename T2> __device__ __forceinline__ void pair_neighbours(const T2 
   w[1] = lane == 0 ? p : q;
 }
 
-template <typename T, bool CJ, bool ZERO>
+// The BiCGStab vector update a smoothing pass can form on the fly (BF):
+//   BF = 1: b = r + beta (p - omega v)   (p: the previous search direction)
+//   BF = 2: b = r - alpha v
+// with the block's scalars; the pass stores b (own lanes and rows) to out.
+template <typename T> struct BFuse {
+  const typename cplx<T>::t *r, *v, *pold;
+  typename cplx<T>::t *out;
+  const BiState *S;
+};
+
+template <typename T, bool CJ, bool ZERO, int BF = 0>
 __global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 2 : 1)
 k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
-                const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y) {
+                const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y,
+                BFuse<T> fz = BFuse<T>{}) {
   typedef typename cplx<T>::t T2;
+  static_assert(BF == 0 || ZERO, "the update is fused into a pass that starts from zero");
   const int gw = blockIdx.x * (MARCH_THREADS / 32) + (threadIdx.x >> 5);
   if (gw >= L.n_strips2) return;                      // whole warps leave together
   const StripDev s = L.strips2[gw];
@@ -330,7 +358,22 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
   // column pointers (row 0); column 1 is 32 elements to the right of column 0
   const int ic = in[0] ? ii[0] : (in[1] ? ii[1] - 32 : 0);
   const T2 *xb = ZERO ? nullptr : x + bk.off + ic;
-  const T2 *bb = b + bk.off + ic;
+  const T2 *bb = (BF ? fz.out : b) + bk.off + ic;
+  const T2 *rb = BF ? fz.r + bk.off + ic : nullptr;
+  const T2 *vb = BF ? fz.v + bk.off + ic : nullptr;
+  const T2 *pb = BF == 1 ? fz.pold + bk.off + ic : nullptr;
+  T2 *ob = BF ? fz.out + bk.off + ic : nullptr;
+  T2 f_al = zero, f_om = zero, f_be = zero;
+  if (BF) {
+    const BiState sc = fz.S[s.blk];
+    f_al = mk<T2>(sc.alpha.x, sc.alpha.y); f_om = mk<T2>(sc.omega.x, sc.omega.y); f_be = mk<T2>(sc.beta.x, sc.beta.y);
+  }
+  // b at element offset e of the strip's column pointers (formed on the fly when fused)
+  auto bval = [&](long long e) -> T2 {
+    if (BF == 1) return cadd(rb[e], cmul(f_be, csub(pb[e], cmul(f_om, vb[e]))));
+    if (BF == 2) return csub(rb[e], cmul(f_al, vb[e]));
+    return bb[e];
+  };
   T2 *yb = y + bk.off + ic;
   const T2 *db = L.dg + op.dg + ic;
   const T2 *dib = L.dgi + op.dg + ic;
@@ -341,7 +384,15 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
       if (!ZERO && in[c])
         for (int r = max(kb - 1, 0); r < min(ke + 2, nz); ++r) prefetch_l2(xb + 32 * c + r * nx);
       if (mid[c])
-        for (int r = max(kb, 0); r < min(ke + 1, nz); ++r) prefetch_l2(bb + 32 * c + r * nx);
+        for (int r = max(kb, 0); r < min(ke + 1, nz); ++r) {
+          if (BF) {
+            prefetch_l2(rb + 32 * c + r * nx);
+            prefetch_l2(vb + 32 * c + r * nx);
+            if (BF == 1) prefetch_l2(pb + 32 * c + r * nx);
+          } else {
+            prefetch_l2(bb + 32 * c + r * nx);
+          }
+        }
     }
   }
   auto inside = [&](int k) { return k >= 0 && k < nz; };
@@ -361,7 +412,7 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
     x0[c] = (okx && inside(kb)) ? xb[32 * c + kb * nx] : zero;
     xp[c] = (okx && inside(kb + 1)) ? xb[32 * c + (kb + 1) * nx] : zero;
     const bool okr = mid[c] && inside(kb);
-    b0[c] = okr ? bb[32 * c + kb * nx] : zero;
+    b0[c] = okr ? bval(32 * c + kb * nx) : zero;
     d0[c] = okr ? cmaybe_conj(ld_keep_p(db + 32 * c + kb * nx, pol), CJ) : zero;
     di0[c] = okr ? cmaybe_conj(ld_keep_p(dib + 32 * c + kb * nx, pol), CJ) : zero;
     bm[c] = dm[c] = dim[c] = ym2[c] = ym1[c] = zero;
@@ -381,7 +432,8 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
     for (int c = 0; c < 2; ++c) {
       xn[c] = (!ZERO && xn_ok && in[c]) ? xb[32 * c + o1 + nx] : zero;
       const bool okr = rn && mid[c];
-      bn[c] = okr ? bb[32 * c + o1] : zero;
+      bn[c] = okr ? bval(32 * c + o1) : zero;
+      if (BF && okr && own[c] && k + 1 >= s.row0 && k + 1 < s.row1) ob[32 * c + o1] = bn[c];
       dn[c] = okr ? cmaybe_conj(ld_keep_p(db + 32 * c + o1, pol), CJ) : zero;   // (the second sweep needs it)
       din[c] = okr ? cmaybe_conj(ld_keep_p(dib + 32 * c + o1, pol), CJ) : zero;
     }
@@ -603,7 +655,7 @@ __host__ __device__ __forceinline__ size_t smem_level_bytes(int nx, int nz, size
 // holds x (one parity bit per level) and the remaining coarse-grid
 // corrections of each level (two bits per level), so no per-thread array is
 // indexed dynamically and nothing goes to local memory.
-template <typename T, bool CJ>
+template <typename T, bool CJ, int UNR>
 struct SmemCycle {
   typedef typename cplx<T>::t T2;
   SmemLevel<T> *lvl;       // [MAX_LEVELS] in shared memory
@@ -632,7 +684,7 @@ struct SmemCycle {
     return cadd(cmul(Zj, hx), cmul(Xi, hz));
   }
   // One damped-Jacobi sweep on level l (from x = 0 when from_zero): a warp
-  // takes a row, a lane the columns lane + 32 q (q < SC_UNROLL) at a time;
+  // takes a row, a lane the columns lane + 32 q (q < UNR) at a time;
   // results go to the other vector, which then becomes x.
   __device__ void jacobi(int l, bool from_zero) {
     const SmemLevel<T> L = lvl[l];
@@ -644,10 +696,10 @@ struct SmemCycle {
       const T2 *xr = xs + j * L.nx;
       const T2 *br = L.b + j * L.nx;
       const T2 *dr = L.di + j * L.nx;
-      for (int i0 = lane; i0 < L.nx; i0 += 32 * SC_UNROLL) {
-        T2 out[SC_UNROLL];
+      for (int i0 = lane; i0 < L.nx; i0 += 32 * UNR) {
+        T2 out[UNR];
 #pragma unroll
-        for (int q = 0; q < SC_UNROLL; ++q) {
+        for (int q = 0; q < UNR; ++q) {
           const int i = i0 + 32 * q;
           if (i < L.nx) {
             const T2 d = dr[i];
@@ -657,7 +709,7 @@ struct SmemCycle {
           }
         }
 #pragma unroll
-        for (int q = 0; q < SC_UNROLL; ++q)
+        for (int q = 0; q < UNR; ++q)
           if (i0 + 32 * q < L.nx) ts[j * L.nx + i0 + 32 * q] = out[q];
       }
     }
@@ -675,16 +727,16 @@ struct SmemCycle {
       const T2 *br = L.b + j * L.nx;
       const T2 *dr = L.di + j * L.nx;
       T2 *tr = ts + j * L.nx;
-      for (int i0 = lane; i0 < L.nx; i0 += 32 * SC_UNROLL) {
-        T2 out[SC_UNROLL];
+      for (int i0 = lane; i0 < L.nx; i0 += 32 * UNR) {
+        T2 out[UNR];
 #pragma unroll
-        for (int q = 0; q < SC_UNROLL; ++q) {
+        for (int q = 0; q < UNR; ++q) {
           const int i = i0 + 32 * q;
           if (i < L.nx)   // b - (cc x - Z_j h_x - X_i h_z), cc = 1/d
             out[q] = cadd(csub(br[i], cmul(cinv(dr[i]), xr[i])), offdiag(L, xr, j, i, Zj, iZn, iZs));
         }
 #pragma unroll
-        for (int q = 0; q < SC_UNROLL; ++q)
+        for (int q = 0; q < UNR; ++q)
           if (i0 + 32 * q < L.nx) tr[i0 + 32 * q] = out[q];
       }
     }
@@ -805,9 +857,10 @@ struct SmemCycle {
   }
 };
 
-#define COARSE_THREADS 512
-template <typename T, bool CJ>
-__global__ void __launch_bounds__(COARSE_THREADS, 1)
+// NT threads per CTA (512 or 1024, chosen per workload by the autotuner); a
+// lane keeps SC_UNROLL (512) or 2 (1024) columns of a row in flight.
+template <typename T, bool CJ, int NT>
+__global__ void __launch_bounds__(NT, 1)
 k_coarse_cycle(const __grid_constant__ CoarseArgs a, const typename cplx<T>::t *__restrict__ st,
                const typename cplx<T>::t *__restrict__ dgi, const typename cplx<T>::t *__restrict__ b,
                typename cplx<T>::t *__restrict__ x) {
@@ -846,7 +899,7 @@ k_coarse_cycle(const __grid_constant__ CoarseArgs a, const typename cplx<T>::t *
     }
   }
   __syncthreads();
-  SmemCycle<T, CJ> c;
+  SmemCycle<T, CJ, NT == 1024 ? 2 : SC_UNROLL> c;
   c.lvl = s_lvl;
   c.op = s_op;
   c.inv = a.inv + a.inv_off[a.blks[nlev - 1][blk].op];
@@ -1136,13 +1189,6 @@ k_block_dots(LevelView<T> L, int nd, const typename cplx<T>::t *a0, const typena
   tile_dots_store<T>(nd, rre, rim, tre, tim, partial);
 }
 
-// Per-block BiCGStab scalars (double2 = complex FP64):
-//   st[b] = {rho, rho_old, alpha, omega, beta, bnorm2(re), rnorm2(re)}, done[b]
-struct BiState {
-  double2 rho, rho_old, alpha, omega, beta;
-  double bnorm2, rnorm2;
-  int done, it;
-};
 
 // Sum of partial[t][q] over t0 <= t < t1 by one warp: lane-strided sums, then
 // a fixed-order butterfly, so every lane gets the same (deterministic) value.
@@ -1228,15 +1274,16 @@ k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1, const double2 *
   }
 }
 
-// BiCGStab updates on a field (per-block scalars):
+// BiCGStab updates on a field (per-block scalars), the update kind OPK a
+// template parameter:
 //  op 0: p = r + beta (p - omega v)
 //  op 1: s = r - alpha v
 //  op 3: y = a (copy)            op 4: y = 0
 // (the x / r update is k_bicg_xr, fused with the dots that follow it)
-template <typename T>
+template <typename T, int OPK>
 __global__ void __launch_bounds__(TILE_THREADS)
-k_bicg_update(LevelView<T> L, int opk, const BiState *S, typename cplx<T>::t *y,
-              const typename cplx<T>::t *a, const typename cplx<T>::t *c) {
+k_bicg_update(LevelView<T> L, const BiState *S, typename cplx<T>::t *y, const typename cplx<T>::t *a,
+              const typename cplx<T>::t *c) {
   typedef typename cplx<T>::t T2;
   const TileDev t = L.tiles[blockIdx.x];
   if (L.skip && L.skip[t.blk]) return;
@@ -1244,21 +1291,18 @@ k_bicg_update(LevelView<T> L, int opk, const BiState *S, typename cplx<T>::t *y,
   const OpDev op = L.ops[bk.op];
   const int j = t.row0 + (threadIdx.x >> 5);
   if (j >= op.nz) return;
-  const BiState s = S[t.blk];
-  const T2 al = mk<T2>(s.alpha.x, s.alpha.y), om = mk<T2>(s.omega.x, s.omega.y),
-           be = mk<T2>(s.beta.x, s.beta.y);
-  long long base = bk.off + (long long)j * op.nx;
+  T2 al = mk<T2>(0, 0), om = al, be = al;
+  if (OPK <= 1) {
+    const BiState s = S[t.blk];
+    al = mk<T2>(s.alpha.x, s.alpha.y); om = mk<T2>(s.omega.x, s.omega.y); be = mk<T2>(s.beta.x, s.beta.y);
+  }
+  const long long base = bk.off + (long long)j * op.nx;
   for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
-    long long k = base + i;
-    if (opk == 0) {
-      y[k] = cadd(a[k], cmul(be, csub(y[k], cmul(om, c[k]))));
-    } else if (opk == 1) {
-      y[k] = csub(a[k], cmul(al, c[k]));
-    } else if (opk == 3) {
-      y[k] = a[k];
-    } else {
-      y[k] = mk<T2>(0, 0);
-    }
+    const long long k = base + i;
+    if (OPK == 0) y[k] = cadd(a[k], cmul(be, csub(y[k], cmul(om, c[k]))));
+    else if (OPK == 1) y[k] = csub(a[k], cmul(al, c[k]));
+    else if (OPK == 3) y[k] = a[k];
+    else y[k] = mk<T2>(0, 0);
   }
 }
 
@@ -1535,33 +1579,58 @@ __global__ void k_update_model(const InstDev *inst, double *const *s_core, const
 #define FLAT_THREADS 256
 #define MD_CHUNK 8
 
-// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv, deterministic (fixed
-// grid and order).  EXACT = true (the Arnoldi inner products): every product
-// is formed and summed in FP64 (the product of two floats is exact in double),
-// so the orthogonalisation of complex64 vectors runs in FP64 arithmetic.
-// EXACT = false: complex64 data accumulate FP32 runs of MD_RUN products per
-// vector (two independent chains of interleaved elements) and add each run
-// into an FP64 total.  complex128 data are FP64 throughout either way.
+// Inner-product modes of the FGMRES dots (complex64 data; complex128 data are
+// FP64 throughout in every mode):
+//   DOT_RUNS  products in FP32, summed in FP32 runs of MD_RUN per thread, each
+//             run added into an FP64 total;
+//   DOT_FP64  every product formed and summed in FP64 (the product of two
+//             floats is exact in double);
+//   DOT_COMP  compensated dot product Dot2 (Ogita, Rump & Oishi, SIAM J. Sci.
+//             Comput. 26, 2005): each product split exactly into p + e with
+//             one FMA (TwoProduct), p added by the error-free TwoSum, all
+//             error terms summed alongside in FP32; per thread the result is
+//             as accurate as a dot product in twice the working precision,
+//             and threads combine in FP64.
+#define DOT_RUNS 0
+#define DOT_FP64 1
+#define DOT_COMP 2
 #define MD_RUN 64
-template <typename T, bool EXACT = false>
-__global__ void __launch_bounds__(FLAT_THREADS)
-k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, double *partial) {
+
+// partial[v][blockIdx.x] = sum_i vp[v][i] w[i] for v < nv (fixed grid and
+// order: deterministic).
+template <typename T, int PM>
+__device__ __forceinline__ void multidot_body(long long n, int nv, const T *const *vp, const T *__restrict__ w,
+                                              double *partial) {
   double tot[MD_CHUNK];
   T ra[MD_CHUNK], rb[MD_CHUNK];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) { tot[v] = 0.0; ra[v] = 0; rb[v] = 0; }
-  const T *vp[MD_CHUNK];
-#pragma unroll
-  for (int v = 0; v < MD_CHUNK; ++v) vp[v] = v < nv ? V[v] : nullptr;
   const long long stride = (long long)gridDim.x * FLAT_THREADS;
   int cnt = 0;
   long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x;
-  if (EXACT && sizeof(T) == 4) {
+  if (PM == DOT_FP64 && sizeof(T) == 4) {
     for (; i < n; i += stride) {
       const double wa = (double)w[i];
 #pragma unroll
       for (int v = 0; v < MD_CHUNK; ++v)
         if (v < nv) tot[v] = tfma((double)vp[v][i], wa, tot[v]);
+    }
+  } else if (PM == DOT_COMP && sizeof(T) == 4) {
+    // ra: running sum s, rb: accumulated error terms c
+    for (; i < n; i += stride) {
+      const T wa = w[i];
+#pragma unroll
+      for (int v = 0; v < MD_CHUNK; ++v)
+        if (v < nv) {
+          const T a = vp[v][i];
+          const T p = tmul_rn(a, wa);
+          const T e = tfma(a, wa, -p);                          // a wa = p + e exactly
+          const T t = tadd_rn(ra[v], p);                        // TwoSum: s + p = t + f exactly
+          const T z = tsub_rn(t, ra[v]);
+          const T f = tadd_rn(tsub_rn(ra[v], tsub_rn(t, z)), tsub_rn(p, z));
+          ra[v] = t;
+          rb[v] = tadd_rn(rb[v], tadd_rn(f, e));
+        }
     }
   } else {
     for (; i + stride < n; i += 2 * stride) {
@@ -1587,7 +1656,7 @@ k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, doub
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) {
     if (v < nv) {
-      double x = tot[v] + (double)(ra[v] + rb[v]);
+      double x = tot[v] + (double)ra[v] + (double)rb[v];
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
       if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = x;
     }
@@ -1598,6 +1667,16 @@ k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, doub
     for (int q = 0; q < FLAT_THREADS / 32; ++q) s += red[threadIdx.x][q];
     partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = s;
   }
+}
+
+// partial[v][blockIdx.x] = sum_i V_v[i] w[i] for v < nv (host-given count).
+template <typename T, int PM = DOT_RUNS>
+__global__ void __launch_bounds__(FLAT_THREADS)
+k_multidot(long long n, int nv, const T *const *V, const T *__restrict__ w, double *partial) {
+  const T *vp[MD_CHUNK];
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v) vp[v] = v < nv ? V[v] : nullptr;
+  multidot_body<T, PM>(n, nv, vp, w, partial);
 }
 
 // out[v] (+)= sum_b partial[v][b]   (one warp per v, fixed order)
@@ -1628,23 +1707,30 @@ k_multi_axpy(long long n, int nv, const T *const *V, const double *coef, double 
   }
 }
 
-// partial[blockIdx.x] = sum x[i] y[i], FP64 across threads, fixed grid.  EXACT:
-// products and sums in FP64; else FP32 runs of DOT_RUN for float data.
-template <typename T, bool EXACT = false>
+// partial[blockIdx.x] = sum x[i] y[i], FP64 across threads, fixed grid; PM as
+// for the multi-dot (DOT_RUNS: FP32 runs of DOT_RUN for float data).
+template <typename T, int PM = DOT_RUNS>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_dot2(long long n, const T *__restrict__ x, const T *__restrict__ y, double *partial) {
   double tot = 0.0;
-  T run = 0;
+  T run = 0, comp = 0;
   int cnt = 0;
   for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
-    if (EXACT) {
+    if (PM == DOT_FP64) {
       tot = tfma((double)x[i], (double)y[i], tot);
+    } else if (PM == DOT_COMP && sizeof(T) == 4) {
+      const T p = tmul_rn(x[i], y[i]);
+      const T e = tfma(x[i], y[i], -p);
+      const T t = tadd_rn(run, p);
+      const T z = tsub_rn(t, run);
+      comp = tadd_rn(comp, tadd_rn(tadd_rn(tsub_rn(run, tsub_rn(t, z)), tsub_rn(p, z)), e));
+      run = t;
     } else {
       run = tfma(x[i], y[i], run);
       if (sizeof(T) == 4 && ++cnt == DOT_RUN) { tot += run; run = 0; cnt = 0; }
     }
   }
-  double acc = tot + (double)run;
+  double acc = tot + (double)run + (double)comp;
   __shared__ double red[FLAT_THREADS / 32];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -1758,65 +1844,16 @@ __device__ __forceinline__ int chunk_count(const FgCtl *c, int which, int c0) {
   return min(MD_CHUNK, cnt - c0);
 }
 
-template <typename T, bool EXACT>
+template <typename T, int PM>
 __global__ void __launch_bounds__(FLAT_THREADS)
 k_multidot_dev(long long n, const FgCtl *c, int which, int c0, const T *const *V, const T *__restrict__ w,
                double *partial) {
   const int nv = chunk_count(c, which, c0);
   if (nv <= 0) return;
-  // the body of k_multidot for nv vectors starting at V[c0]
-  double tot[MD_CHUNK];
-  T ra[MD_CHUNK], rb[MD_CHUNK];
-#pragma unroll
-  for (int v = 0; v < MD_CHUNK; ++v) { tot[v] = 0.0; ra[v] = 0; rb[v] = 0; }
   const T *vp[MD_CHUNK];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) vp[v] = v < nv ? V[c0 + v] : nullptr;
-  const long long stride = (long long)gridDim.x * FLAT_THREADS;
-  int cnt = 0;
-  long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x;
-  if (EXACT && sizeof(T) == 4) {
-    for (; i < n; i += stride) {
-      const double wa = (double)w[i];
-#pragma unroll
-      for (int v = 0; v < MD_CHUNK; ++v)
-        if (v < nv) tot[v] = tfma((double)vp[v][i], wa, tot[v]);
-    }
-  } else {
-    for (; i + stride < n; i += 2 * stride) {
-      const T wa = w[i], wb = w[i + stride];
-#pragma unroll
-      for (int v = 0; v < MD_CHUNK; ++v)
-        if (v < nv) { ra[v] = tfma(vp[v][i], wa, ra[v]); rb[v] = tfma(vp[v][i + stride], wb, rb[v]); }
-      if (sizeof(T) == 4 && (cnt += 2) >= MD_RUN) {
-#pragma unroll
-        for (int v = 0; v < MD_CHUNK; ++v)
-          if (v < nv) { tot[v] += (double)(ra[v] + rb[v]); ra[v] = 0; rb[v] = 0; }
-        cnt = 0;
-      }
-    }
-    if (i < n) {
-      const T wa = w[i];
-#pragma unroll
-      for (int v = 0; v < MD_CHUNK; ++v)
-        if (v < nv) ra[v] = tfma(vp[v][i], wa, ra[v]);
-    }
-  }
-  __shared__ double red[MD_CHUNK][FLAT_THREADS / 32];
-#pragma unroll
-  for (int v = 0; v < MD_CHUNK; ++v) {
-    if (v < nv) {
-      double x = tot[v] + (double)(ra[v] + rb[v]);
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = x;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double s = 0.0;
-    for (int q = 0; q < FLAT_THREADS / 32; ++q) s += red[threadIdx.x][q];
-    partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = s;
-  }
+  multidot_body<T, PM>(n, nv, vp, w, partial);
 }
 
 // out[c0 + v] = sum_b partial[v][b] for v < the chunk's count (one warp per v)

@@ -220,7 +220,7 @@ template <typename T> struct Work {
   // multigrid fields per global level (index 0 unused for b, x)
   DBuf<T2> lx[MAX_LEVELS], lb[MAX_LEVELS], lt[MAX_LEVELS];
   DBuf<T2> t0a, t0b;                                   // level-0 smoother buffers
-  DBuf<T2> r, rh, p, v, s, t, ph, sh;                  // BiCGStab
+  DBuf<T2> r, rh, p, p2, v, s, t, ph, sh;              // BiCGStab (p2: ping-pong partner of p)
   DBuf<BiState> bst;
   DBuf<int> done;                                      // per-block "finished" flags of the inner solve
   DBuf<T2> u;                                          // forward wavefields (precision T)
@@ -241,6 +241,7 @@ template <typename T> struct Work {
   unsigned long long cyc_body_kernels = 0, cyc_tail_kernels = 0;
   DBuf<FgCtl> ctl;
   DBuf<T> wst;                                         // staging of the new Arnoldi vector
+  DBuf<T> ob[8];                                       // outer BiCGStab: r, rh, p, v, s, t, ph, sh
   ~Work() {
     if (graph) cudaGraphExecDestroy(graph);
     if (cyc) cudaGraphExecDestroy(cyc);
@@ -293,6 +294,7 @@ struct Ctx {
   size_t smem_bytes[2] = {0, 0};
   // forward state
   bool have_fwd = false;
+  bool u64_valid = false;          // u64 holds converged wavefields of the current layout
   int fwd_version = 0;
   DBuf<double2> u64, f64, rho64, e64;
   DBuf<double2> q, r;                         // predicted data, residual per receiver entry
@@ -368,7 +370,7 @@ struct Ctx {
   template <typename T> void ensure_work(const fwi_opts &o);
   template <typename T> void ensure_krylov(const fwi_opts &o);
   template <typename T> void launch_coarse(const CoarseArgs &ca, size_t smem, const typename cplx<T>::t *b,
-                                           typename cplx<T>::t *x, int cj);
+                                           typename cplx<T>::t *x, int cj, int nthreads);
   template <typename T> const typename cplx<T>::t *u_T();
   int gradient(const fwi_opts &o, double *misfit_out, double *grad, int on_device, fwi_stats *stats);
   int newton_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats);
@@ -378,7 +380,8 @@ struct Ctx {
   void apply_update(double *ds, int on_device);
   void write_ctrl(const double *src_ctrl_dev, double *dst, int on_device, const double *fac);
   template <typename T> void mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
-                                      const fwi_opts &o);
+                                      const fwi_opts &o, const BFuse<T> *fz = nullptr);
+  template <typename T> void bicg_update_into(const BFuse<T> &fz);
   template <typename T> void inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
                                          int iters, double tol, const fwi_opts &o, long long *count);
   template <typename T> void mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
@@ -387,14 +390,15 @@ struct Ctx {
                                            typename cplx<T>::t *t0);
   template <typename T> bool timer_begin(int level, LevelView<T> &L);
   template <typename T> void smooth(int nu, bool zero, int cj, T wj, const typename cplx<T>::t *bl,
-                                    typename cplx<T>::t *&cur, typename cplx<T>::t *&oth, int l);
+                                    typename cplx<T>::t *&cur, typename cplx<T>::t *&oth, int l,
+                                    const BFuse<T> *fz = nullptr);
   template <typename T> void resid_restrict(int cj, int l, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
                                             typename cplx<T>::t *bc);
   void timer_end(int streams, int pass_streams, size_t elem_bytes);
   template <typename T> void apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *y,
                                         const typename cplx<T>::t *a, int nd);
   template <typename T> void jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
-                                     typename cplx<T>::t *y, int level);
+                                     typename cplx<T>::t *y, int level, const BFuse<T> *fz = nullptr);
   template <typename T> void field_op(int mode, int cj, T w, const typename cplx<T>::t *x,
                                       const typename cplx<T>::t *b, typename cplx<T>::t *y, bool opA,
                                       int level);
@@ -409,13 +413,15 @@ struct Ctx {
   template <typename T> int fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi_opts &o,
                                    int *iters, long long *inner, const typename cplx<T>::t *u);
   template <typename T> void multidot(long long n, int nv, T *const *dV, const T *w, double *out, int acc,
-                                      bool exact);
+                                      int pm);
   template <typename T> void multi_axpy(long long n, int nv, T *const *dV, const double *coef, double sign, T *w);
   template <typename T> void fgmres_cycle_graph(const fwi_opts &o, double eps, T *x, const typename cplx<T>::t *u);
+  template <typename T> int bicgstab_outer(const T *rhs, T *x, double tol, int maxit, double eps, const fwi_opts &o,
+                                           int *iters, long long *inner, const typename cplx<T>::t *u);
   double orth_loss = 0.0;   // max |I - V^T V| of the FGMRES bases of the last KKT solve (check_orth)
   void forward(const fwi_opts &o, fwi_stats *stats);
   template <typename T> int refined_solve(const double2 *rhs, double2 *x, int cj, const fwi_opts &o,
-                                          fwi_stats *stats);
+                                          fwi_stats *stats, bool warm = false);
   void seg_norms(const double *x);
   int kkt_solve(const fwi_opts &o, fwi_stats *stats);
   void sync() {
@@ -443,10 +449,15 @@ template <> const double *gam_ptr<double>(Ctx &c) { return c.gam64.p; }
 
 template <typename T>
 void Ctx::launch_coarse(const CoarseArgs &ca, size_t smem, const typename cplx<T>::t *b, typename cplx<T>::t *x,
-                        int cj) {
+                        int cj, int nthreads) {
   KPROF("k_coarse_cycle", ca.ls, 2.0 * sizeof(typename cplx<T>::t) * lv[ca.ls].field, st);
-  if (cj) k_coarse_cycle<T, true><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
-  else k_coarse_cycle<T, false><<<B, COARSE_THREADS, smem, st>>>(ca, st_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+  if (nthreads == 1024) {
+    if (cj) k_coarse_cycle<T, true, 1024><<<B, 1024, smem, st>>>(ca, st_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+    else k_coarse_cycle<T, false, 1024><<<B, 1024, smem, st>>>(ca, st_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+  } else {
+    if (cj) k_coarse_cycle<T, true, 512><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+    else k_coarse_cycle<T, false, 512><<<B, 512, smem, st>>>(ca, st_ptr<T>(*this), dgi_ptr<T>(*this), b, x);
+  }
   KCHECK();
 }
 
@@ -588,6 +599,7 @@ void Ctx::build_layout() {
     g_memcalls.fetch_add(2);
   }
   layout_ok = true;
+  u64_valid = false;
   hier_key.clear();
   w32.ready = 0;
   w64.ready = 0;
@@ -597,11 +609,20 @@ void Ctx::build_layout() {
 // a1: per-frequency set-up -- stretch arrays, gamma on every level, operator
 // tables, coarsest dense inverses (FP64)
 // --------------------------------------------------------------------------
+// Key of the multigrid hierarchy and launch tables built for these options
+// and the current models.
+static std::string hierarchy_key(int model_version, const fwi_opts &o) {
+  char key[256];
+  snprintf(key, sizeof key, "%d|%d|%.17g|%.17g|%d", model_version, o.mg_levels, o.shift_beta, o.sigma_cap,
+           o.strip_rows);
+  return key;
+}
+
 void Ctx::build_hierarchy(const fwi_opts &o) {
   build_layout();
-  char key[256];
-  snprintf(key, sizeof key, "%d|%d|%.17g|%.17g", model_version, o.mg_levels, o.shift_beta, o.sigma_cap);
+  const std::string key = hierarchy_key(model_version, o);
   if (hier_key == key) return;
+  const int srows = o.strip_rows;
   const int n_inst = (int)inst.size();
   // levels per instance
   nlev_max = 1;
@@ -804,11 +825,11 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
       // (which share halo rows and columns) run close together
       T.hs0[b] = (int)T.hstrips.size();
       if (l < std::max(ls, 1))   // level 0 always (operator apply, dots), the other global levels
-        for (int r0 = 0; r0 < nz; r0 += MARCH_ROWS) {
+        for (int r0 = 0; r0 < nz; r0 += srows) {
           for (int c0 = 0; c0 < nx; c0 += MARCH_COLS)
-            T.hstrips.push_back(StripDev{b, c0, r0, std::min(r0 + MARCH_ROWS, nz)});
+            T.hstrips.push_back(StripDev{b, c0, r0, std::min(r0 + srows, nz)});
           for (int c0 = 0; c0 < nx; c0 += MARCH2_COLS)
-            T.hstrips2.push_back(StripDev{b, c0, r0, std::min(r0 + MARCH_ROWS, nz)});
+            T.hstrips2.push_back(StripDev{b, c0, r0, std::min(r0 + srows, nz)});
         }
       T.hs1[b] = (int)T.hstrips.size();
       if (l < ls) {
@@ -854,6 +875,14 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
   w64.ready = 0;
 }
 
+// Dynamic shared-memory limit of every instantiation of the coarse-cycle kernel.
+template <typename T> static void set_coarse_smem(int bytes) {
+  CK(cudaFuncSetAttribute(k_coarse_cycle<T, false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_coarse_cycle<T, true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_coarse_cycle<T, false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CK(cudaFuncSetAttribute(k_coarse_cycle<T, true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+}
+
 template <typename T> void Ctx::ensure_work(const fwi_opts &o) {
   Work<T> &w = work<T>();
   if (w.ready) return;
@@ -861,7 +890,7 @@ template <typename T> void Ctx::ensure_work(const fwi_opts &o) {
     w.lx[l].alloc(lv[l].field); w.lb[l].alloc(lv[l].field); w.lt[l].alloc(lv[l].field);
   }
   w.t0a.alloc(F0); w.t0b.alloc(F0);
-  w.r.alloc(F0); w.rh.alloc(F0); w.p.alloc(F0); w.v.alloc(F0);
+  w.r.alloc(F0); w.rh.alloc(F0); w.p.alloc(F0); w.p2.alloc(F0); w.v.alloc(F0);
   w.s.alloc(F0); w.t.alloc(F0); w.ph.alloc(F0); w.sh.alloc(F0);
   w.bst.alloc(B);
   w.done.alloc(B);
@@ -869,12 +898,7 @@ template <typename T> void Ctx::ensure_work(const fwi_opts &o) {
   w.vin.alloc(nkkt); w.zout.alloc(nkkt); w.tmp.alloc(nkkt);
   w.scal.alloc(8);
   w.partial_flat.alloc((size_t)MD_CHUNK * FLAT_BLOCKS);
-  if (smem_bytes[sizeof(T) == 8] > 48 * 1024) {
-    CK(cudaFuncSetAttribute(k_coarse_cycle<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_bytes[sizeof(T) == 8]));
-    CK(cudaFuncSetAttribute(k_coarse_cycle<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_bytes[sizeof(T) == 8]));
-  }
+  if (smem_bytes[sizeof(T) == 8] > 48 * 1024) set_coarse_smem<T>((int)smem_bytes[sizeof(T) == 8]);
   if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
   w.graph_key.clear();
   if (w.cyc) { cudaGraphExecDestroy(w.cyc); w.cyc = nullptr; }
@@ -993,10 +1017,29 @@ void Ctx::apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *
 // first sweep starts from zero); y must not alias x or b.
 template <typename T>
 void Ctx::jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
-                  typename cplx<T>::t *y, int level) {
+                  typename cplx<T>::t *y, int level, const BFuse<T> *fz) {
   LevelView<T> L = viewM<T>(level);
   const bool timed = timer_begin<T>(level, L);
   const int grid = std::max(1, (L.n_strips2 + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
+  if (fz) {
+    // first pass from zero with the BiCGStab update formed on the fly (b = fz->out)
+    const int bf = fz->pold ? 1 : 2;
+    KPROF(bf == 1 ? "k_jacobi2_march+p_update" : "k_jacobi2_march+s_update", level,
+          (5.0 + (bf == 1 ? 4.0 : 3.0)) * sizeof(typename cplx<T>::t) * lv[level].field, st);
+    if (bf == 1) {
+      if (cj) k_jacobi2_march<T, true, true, 1><<<grid, MARCH_THREADS, 0, st>>>(L, wj, nullptr, nullptr, y, *fz);
+      else k_jacobi2_march<T, false, true, 1><<<grid, MARCH_THREADS, 0, st>>>(L, wj, nullptr, nullptr, y, *fz);
+    } else {
+      if (cj) k_jacobi2_march<T, true, true, 2><<<grid, MARCH_THREADS, 0, st>>>(L, wj, nullptr, nullptr, y, *fz);
+      else k_jacobi2_march<T, false, true, 2><<<grid, MARCH_THREADS, 0, st>>>(L, wj, nullptr, nullptr, y, *fz);
+    }
+    KCHECK();
+    // algorithmic bytes per node: the update's operands (r, v, old p) and result,
+    // then the two sweeps (b and the result, x and b and the result); the pass
+    // itself reads r, v (and old p) and writes b and y
+    if (timed) timer_end(5 + (bf == 1 ? 4 : 3), bf == 1 ? 5 : 4, sizeof(typename cplx<T>::t));
+    return;
+  }
   KPROF("k_jacobi2_march", level, (x == nullptr ? 5.0 : 6.0) * sizeof(typename cplx<T>::t) * lv[level].field, st);
   if (x == nullptr) {
     if (cj) k_jacobi2_march<T, true, true><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
@@ -1043,11 +1086,11 @@ void Ctx::block_dots(int nd, const typename cplx<T>::t *a0, const typename cplx<
 // on the fine levels.
 template <typename T>
 void Ctx::smooth(int nu, bool zero, int cj, T wj, const typename cplx<T>::t *bl, typename cplx<T>::t *&cur,
-                 typename cplx<T>::t *&oth, int l) {
+                 typename cplx<T>::t *&oth, int l, const BFuse<T> *fz) {
   int s = 0;
   if (lv[l].n_strips2 > 0) {
     if (zero && nu >= 2) {
-      jacobi2<T>(cj, wj, nullptr, bl, cur, l);
+      jacobi2<T>(cj, wj, nullptr, bl, cur, l, fz);
       s = 2;
     }
     for (; s + 1 < nu; s += 2) {
@@ -1066,9 +1109,16 @@ void Ctx::smooth(int nu, bool zero, int cj, T wj, const typename cplx<T>::t *bl,
 }
 
 template <typename T>
-void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj, const fwi_opts &o) {
+void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj, const fwi_opts &o,
+                   const BFuse<T> *fz) {
   typedef typename cplx<T>::t T2;
   Work<T> &w = work<T>();
+  // a BiCGStab update fused into the first level-0 pass needs that pass to be
+  // a two-sweep pass from zero on the global level 0; otherwise form it first
+  if (fz && !(ls_p[sizeof(T) == 8] > 0 && o.nu1 >= 2 && lv[0].n_strips2 > 0)) {
+    bicg_update_into<T>(*fz);
+    fz = nullptr;
+  }
   const T wj = (T)o.omega_jac;
   CoarseArgs ca;
   for (int l = 0; l < MAX_LEVELS; ++l) ca.blks[l] = l < nlev_max ? lv[l].blksM.p : nullptr;
@@ -1079,7 +1129,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
   ca.wdepth = o.mg_wdepth;
   size_t smem = smem_bytes[sizeof(T) == 8];
   if (ls == 0) {
-    launch_coarse<T>(ca, smem, b, x, cj);
+    launch_coarse<T>(ca, smem, b, x, cj, o.coarse_threads);
     return;
   }
   // recursive cycle over the global levels 0..ls-1; returns the buffer that
@@ -1087,12 +1137,12 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
   std::function<T2 *(int, const T2 *, T2 *, T2 *)> cyc;
   cyc = [&](int l, const T2 *bl, T2 *xa, T2 *xb) -> T2 * {
     if (l == ls) {
-      launch_coarse<T>(ca, smem, bl, xa, cj);
+      launch_coarse<T>(ca, smem, bl, xa, cj, o.coarse_threads);
       return xa;
     }
     T2 *cur = xa, *oth = xb;
     if (o.nu1 == 0) CK(cudaMemsetAsync(cur, 0, lv[l].field * sizeof(T2), st));
-    smooth<T>(o.nu1, true, cj, wj, bl, cur, oth, l);
+    smooth<T>(o.nu1, true, cj, wj, bl, cur, oth, l, l == 0 ? fz : nullptr);
     int reps = (l > 0 && l <= o.mg_wdepth) ? o.mg_cycle : 1;
     for (int r = 0; r < reps; ++r) {
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
@@ -1126,13 +1176,13 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
   ca.wdepth = o.mg_wdepth;
   size_t smem = smem_bytes[sizeof(T) == 8];
   if (ls == 0) {
-    launch_coarse<T>(ca, smem, b, x, cj);
+    launch_coarse<T>(ca, smem, b, x, cj, o.coarse_threads);
     return;
   }
   std::function<T2 *(int, const T2 *, T2 *, T2 *)> cyc;
   cyc = [&](int l, const T2 *bl, T2 *xa, T2 *xb) -> T2 * {
     if (l == ls) {
-      launch_coarse<T>(ca, smem, bl, xa, cj);
+      launch_coarse<T>(ca, smem, bl, xa, cj, o.coarse_threads);
       return xa;
     }
     T2 *cur = xa, *oth = xb;
@@ -1154,6 +1204,30 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
   if (res != x) CK(cudaMemcpyAsync(x, res, F0 * sizeof(T2), cudaMemcpyDeviceToDevice, st));
 }
 
+// The BiCGStab update of a fused descriptor as separate passes (for cycles
+// whose first level-0 pass cannot form it): out = r + beta (pold - omega v)
+// or out = r - alpha v.
+template <typename T>
+void Ctx::bicg_update_into(const BFuse<T> &fz) {
+  typedef typename cplx<T>::t T2;
+  LevelView<T> L = viewA<T>();
+  const int nt = L.n_tiles;
+  if (fz.pold) {
+    if (fz.pold != fz.out) {
+      KPROF("k_bicg_update", 3, 2.0 * sizeof(T2) * F0, st);
+      k_bicg_update<T, 3><<<nt, TILE_THREADS, 0, st>>>(L, fz.S, fz.out, fz.pold, nullptr);
+      KCHECK();
+    }
+    KPROF("k_bicg_update", 0, 4.0 * sizeof(T2) * F0, st);
+    k_bicg_update<T, 0><<<nt, TILE_THREADS, 0, st>>>(L, fz.S, fz.out, fz.r, fz.v);
+    KCHECK();
+  } else {
+    KPROF("k_bicg_update", 1, 3.0 * sizeof(T2) * F0, st);
+    k_bicg_update<T, 1><<<nt, TILE_THREADS, 0, st>>>(L, fz.S, fz.out, fz.r, fz.v);
+    KCHECK();
+  }
+}
+
 // Batched right-preconditioned BiCGStab, one independent system per block
 // (per-block scalars), x = approx A'^{-1} b (cj = 1: A'^H).
 template <typename T>
@@ -1165,8 +1239,11 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   const int nt = L.n_tiles;
   const int sb = (B + BICG_WARPS - 1) / BICG_WARPS;
   auto upd = [&](int opk, T2 *y, const T2 *a, const T2 *c) {
-    KPROF("k_bicg_update", opk, (opk == 0 ? 4.0 : opk == 1 ? 3.0 : opk == 3 ? 2.0 : 1.0) * sizeof(typename cplx<T>::t) * F0, st);
-    k_bicg_update<T><<<nt, TILE_THREADS, 0, st>>>(L, opk, w.bst.p, y, a, c);
+    KPROF("k_bicg_update", opk, (opk == 0 ? 4.0 : opk == 1 ? 3.0 : opk == 3 ? 2.0 : 1.0) * sizeof(T2) * F0, st);
+    if (opk == 0) k_bicg_update<T, 0><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+    else if (opk == 1) k_bicg_update<T, 1><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+    else if (opk == 3) k_bicg_update<T, 3><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+    else k_bicg_update<T, 4><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
     KCHECK();
   };
   auto scal = [&](int stage) {
@@ -1199,12 +1276,19 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   L = viewA<T>();
   // rho = <rh, r> = <b, b> for the first iteration: the partials still hold <b, b>
   scal(1);
+  // the p update is formed inside the first smoothing pass of the cycle that
+  // consumes it (its separate pass was the slower one; the s update stays a
+  // separate pass, which costs less than the loads it would add to the
+  // latency-bound smoother); p alternates between two buffers because that
+  // pass reads the previous p around its strips while writing the new one
+  T2 *pc = w.p.p, *pn = w.p2.p;
   for (int it = 0; it < iters; ++it) {
-    upd(0, w.p.p, w.r.p, w.v.p);          // p = r + beta (p - omega v)
-    mg_cycle<T>(w.p.p, w.ph.p, cj, o);                                 // ph = K p
+    const BFuse<T> fp{w.r.p, w.v.p, pc, pn, w.bst.p};                 // p = r + beta (p - omega v)
+    mg_cycle<T>(pn, w.ph.p, cj, o, &fp);                               // ph = K p
+    std::swap(pc, pn);
     apply_dots<T>(cj, w.ph.p, w.v.p, w.rh.p, 1);                       // v = A ph, <rh, v>
     scal_s(2);
-    upd(1, w.s.p, w.r.p, w.v.p);          // s = r - alpha v
+    upd(1, w.s.p, w.r.p, w.v.p);                                       // s = r - alpha v
     mg_cycle<T>(w.s.p, w.sh.p, cj, o);                                 // sh = K s
     apply_dots<T>(cj, w.sh.p, w.t.p, w.s.p, 2);                        // t = A sh, <t, s>, <t, t>
     scal_s(3);
@@ -1285,8 +1369,8 @@ void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, con
   bool graphable = o.use_graph && !(o.inner_tol > 0.0);
   if (!graphable) { precond<T>(v, z, o, count, u); return; }
   char key[256];
-  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p", hier_key.c_str(), o.inner_iters, o.mg_cycle,
-           o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta, (const void *)u);
+  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d", hier_key.c_str(), o.inner_iters, o.mg_cycle,
+           o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta, (const void *)u, o.coarse_threads);
   if (w.graph_key != key) {
     if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
     cudaGraph_t gr;
@@ -1314,13 +1398,15 @@ void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, con
 }
 
 template <typename T>
-void Ctx::multidot(long long n, int nv, T *const *dV, const T *wv, double *out, int acc, bool exact) {
+void Ctx::multidot(long long n, int nv, T *const *dV, const T *wv, double *out, int acc, int pm) {
   Work<T> &w = work<T>();
   for (int c0 = 0; c0 < nv; c0 += MD_CHUNK) {
     int c = std::min(MD_CHUNK, nv - c0);
-    KPROF(exact ? "k_multidot:fp64" : "k_multidot:runs", -1, (double)(c + 1) * n * sizeof(T), st);
-    if (exact) k_multidot<T, true><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
-    else k_multidot<T, false><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
+    KPROF(pm == DOT_FP64 ? "k_multidot:fp64" : pm == DOT_COMP ? "k_multidot:comp" : "k_multidot:runs", -1,
+          (double)(c + 1) * n * sizeof(T), st);
+    if (pm == DOT_FP64) k_multidot<T, DOT_FP64><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
+    else if (pm == DOT_COMP) k_multidot<T, DOT_COMP><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
+    else k_multidot<T, DOT_RUNS><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, dV + c0, wv, w.partial_flat.p);
     KCHECK();
     KPROF("k_reduce_partials", -1, 0, st);
     k_reduce_partials<<<c, 32, 0, st>>>(c, FLAT_BLOCKS, w.partial_flat.p, out + c0, acc);
@@ -1342,10 +1428,11 @@ void Ctx::multi_axpy(long long n, int nv, T *const *dV, const double *coef, doub
 // ||x||^2 or x.y over a flat array into *out (FP64, deterministic).
 template <typename T>
 static void flat_dot(cudaStream_t st, long long n, const T *x, const T *y, double *partial, double *out,
-                     bool exact = false) {
-  KPROF(exact ? "k_dot2:fp64" : "k_dot2:runs", -1, 2.0 * n * sizeof(T), st);
-  if (exact) k_dot2<T, true><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
-  else k_dot2<T, false><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
+                     int pm = DOT_RUNS) {
+  KPROF(pm == DOT_FP64 ? "k_dot2:fp64" : pm == DOT_COMP ? "k_dot2:comp" : "k_dot2:runs", -1, 2.0 * n * sizeof(T), st);
+  if (pm == DOT_FP64) k_dot2<T, DOT_FP64><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
+  else if (pm == DOT_COMP) k_dot2<T, DOT_COMP><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
+  else k_dot2<T, DOT_RUNS><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, x, y, partial);
   KCHECK();
   KPROF("k_reduce_partials", -1, 0, st);
   k_reduce_partials<<<1, 32, 0, st>>>(1, FLAT_BLOCKS, partial, out, 0);
@@ -1364,14 +1451,14 @@ template <typename T>
 void Ctx::fgmres_cycle_graph(const fwi_opts &o, double eps, T *x, const typename cplx<T>::t *u) {
   Work<T> &w = work<T>();
   char key[320];
-  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d|%d|%p", hier_key.c_str(), o.inner_iters,
+  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d|%d|%p|%d", hier_key.c_str(), o.inner_iters,
            o.mg_cycle, o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, eps, o.shift_beta, (const void *)u, w.m,
-           o.arnoldi_fp64, (void *)x);
+           o.arnoldi_dots, (void *)x, o.coarse_threads);
   if (w.cyc && w.cyc_key == key) return;
   if (w.cyc) { cudaGraphExecDestroy(w.cyc); w.cyc = nullptr; }
   const long long n = nkkt;
   const int m = w.m;
-  const bool exact = o.arnoldi_fp64 != 0;
+  const int pm = o.arnoldi_dots;
   T *const *dV = w.dptrV.p;
   T *const *dZ = w.dptrZ.p;
   FgCtl *c = w.ctl.p;
@@ -1394,9 +1481,14 @@ void Ctx::fgmres_cycle_graph(const fwi_opts &o, double eps, T *x, const typename
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   auto dots = [&](double *out) {          // out[0..j] = V[0..j] . wst, chunk by chunk
     for (int q = 0; q < nchunk; ++q) {
-      if (exact) k_multidot_dev<T, true><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, 0, q * MD_CHUNK, dV, w.wst.p,
-                                                                              w.partial_flat.p);
-      else k_multidot_dev<T, false><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, 0, q * MD_CHUNK, dV, w.wst.p,
+      if (pm == DOT_FP64)
+        k_multidot_dev<T, DOT_FP64><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, 0, q * MD_CHUNK, dV, w.wst.p,
+                                                                          w.partial_flat.p);
+      else if (pm == DOT_COMP)
+        k_multidot_dev<T, DOT_COMP><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, 0, q * MD_CHUNK, dV, w.wst.p,
+                                                                          w.partial_flat.p);
+      else
+        k_multidot_dev<T, DOT_RUNS><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, c, 0, q * MD_CHUNK, dV, w.wst.p,
                                                                           w.partial_flat.p);
       KCHECK();
       k_reduce_partials_dev<<<MD_CHUNK, 32, 0, st>>>(c, 0, q * MD_CHUNK, FLAT_BLOCKS, w.partial_flat.p, out);
@@ -1425,7 +1517,7 @@ void Ctx::fgmres_cycle_graph(const fwi_opts &o, double eps, T *x, const typename
     axpys(dV, 0, w.hsum.p, -1.0, w.wst.p);
     k_dadd_dev<<<1, 64, 0, st>>>(c, w.hcol.p, w.hsum.p);
     KCHECK();
-    flat_dot<T>(st, n, w.wst.p, w.wst.p, w.partial_flat.p, w.scal.p + 2, exact);
+    flat_dot<T>(st, n, w.wst.p, w.wst.p, w.partial_flat.p, w.scal.p + 2, pm);
     k_givens_dev<<<1, 1, 0, st>>>(c, w.H.p, w.cs.p, w.sn.p, w.g.p, w.hcol.p, w.scal.p + 2, w.scal.p + 3,
                                   w.scal.p + 4);
     KCHECK();
@@ -1473,12 +1565,12 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
   T *const *dV = w.dptrV.p;
   T *const *dZ = w.dptrZ.p;
   CK(cudaMemsetAsync(x, 0, n * sizeof(T), st));
-  const bool exact = o.arnoldi_fp64 != 0;
+  const int pm = o.arnoldi_dots;
   // device control of each restart cycle whenever the preconditioner is
   // graph-replayable (fixed inner iterations); otherwise the host loop below
   const bool devctl = o.use_graph && !(o.inner_tol > 0.0);
   if (devctl) fgmres_cycle_graph<T>(o, eps, x, u);
-  flat_dot<T>(st, n, rhs, rhs, w.partial_flat.p, w.scal.p, exact);
+  flat_dot<T>(st, n, rhs, rhs, w.partial_flat.p, w.scal.p, pm);
   CK(cudaMemcpyAsync(pin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
   sync();
   const double bnorm = std::sqrt(pin[0]);
@@ -1494,7 +1586,7 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
     if (k <= 0) return;
     std::vector<double> hh(k + 1);
     for (int jj = 0; jj <= k; ++jj) {
-      multidot<T>(n, jj + 1, dV, w.V.p + (size_t)jj * w.ld, w.hsum.p, 0, true);
+      multidot<T>(n, jj + 1, dV, w.V.p + (size_t)jj * w.ld, w.hsum.p, 0, DOT_FP64);
       CK(cudaMemcpyAsync(hh.data(), w.hsum.p, (jj + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
       sync();
       for (int ii = 0; ii <= jj; ++ii) orth_loss = std::max(orth_loss, std::fabs((ii == jj ? 1.0 : 0.0) - hh[ii]));
@@ -1535,14 +1627,14 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
       precond_any<T>(vj, zj, o, inner, u);
       kkt_matvec<T>(zj, wv, eps, u);
       // classical Gram-Schmidt, twice
-      multidot<T>(n, j + 1, dV, wv, w.hcol.p, 0, exact);
+      multidot<T>(n, j + 1, dV, wv, w.hcol.p, 0, pm);
       multi_axpy<T>(n, j + 1, dV, w.hcol.p, -1.0, wv);
-      multidot<T>(n, j + 1, dV, wv, w.hsum.p, 0, exact);
+      multidot<T>(n, j + 1, dV, wv, w.hsum.p, 0, pm);
       multi_axpy<T>(n, j + 1, dV, w.hsum.p, -1.0, wv);
       KPROF("k_dadd", -1, 0, st);
       k_dadd<<<1, 64, 0, st>>>(j + 1, w.hcol.p, w.hsum.p);
       KCHECK();
-      flat_dot<T>(st, n, wv, wv, w.partial_flat.p, w.scal.p + 2, exact);
+      flat_dot<T>(st, n, wv, wv, w.partial_flat.p, w.scal.p + 2, pm);
       KPROF("k_givens", -1, 0, st);
       k_givens<<<1, 1, 0, st>>>(j, m, w.H.p, w.cs.p, w.sn.p, w.g.p, w.hcol.p, w.scal.p + 2, w.scal.p + 3,
                                 w.scal.p + 4);
@@ -1570,7 +1662,7 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
     k_axpby<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, 1.0, rhs, -1.0, w.tmp.p);
     KCHECK();
     r = w.tmp.p;
-    flat_dot<T>(st, n, r, r, w.partial_flat.p, w.scal.p, exact);
+    flat_dot<T>(st, n, r, r, w.partial_flat.p, w.scal.p, pm);
     CK(cudaMemcpyAsync(pin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
     sync();
     beta = std::sqrt(pin[0]);
@@ -1580,6 +1672,76 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
   return conv ? 0 : 1;
 }
 
+
+// Outer BiCGStab (van der Vorst 1992) on the KKT matrix in the real inner
+// product, right-preconditioned by the block-triangular preconditioner: the
+// memory-lean alternative to FGMRES named in the paper's conclusions (eight
+// KKT-size vectors instead of 2m + 1).  Two preconditioner applications and two
+// KKT products per iteration; x = 0 initially; stops when the recursively
+// updated residual reaches tol * ||rhs|| (the caller's FP64 refinement checks
+// the true residual).  Returns 0 when converged.
+template <typename T>
+int Ctx::bicgstab_outer(const T *rhs, T *x, double tol, int maxit, double eps, const fwi_opts &o, int *iters,
+                        long long *inner, const typename cplx<T>::t *u) {
+  Work<T> &w = work<T>();
+  const long long n = nkkt;
+  for (auto &v : w.ob) v.alloc(n);
+  T *r = w.ob[0].p, *rh = w.ob[1].p, *p = w.ob[2].p, *v = w.ob[3].p, *sv = w.ob[4].p, *t = w.ob[5].p,
+    *ph = w.ob[6].p, *sh = w.ob[7].p;
+  const int pm = o.arnoldi_dots;
+  auto dot = [&](const T *a, const T *b) {
+    flat_dot<T>(st, n, a, b, w.partial_flat.p, w.scal.p, pm);
+    CK(cudaMemcpyAsync(pin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    return pin[0];
+  };
+  auto axpby = [&](double a, const T *xx, double b, T *yy) {   // yy = a xx + b yy
+    KPROF("k_axpby", -1, 3.0 * n * sizeof(T), st);
+    k_axpby<T><<<FLAT_BLOCKS, FLAT_THREADS, 0, st>>>(n, a, xx, b, yy);
+    KCHECK();
+  };
+  CK(cudaMemsetAsync(x, 0, n * sizeof(T), st));
+  CK(cudaMemcpyAsync(r, rhs, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(rh, rhs, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(p, 0, n * sizeof(T), st));
+  CK(cudaMemsetAsync(v, 0, n * sizeof(T), st));
+  const double bnorm = std::sqrt(dot(rhs, rhs));
+  if (!(bnorm > 0.0)) return 0;
+  if (!std::isfinite(bnorm)) fail(FWI_E_NUMERIC, "non-finite right-hand side in BiCGStab");
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  int it = 0;
+  bool conv = false;
+  while (it < maxit) {
+    const double rho_new = dot(rh, r);
+    if (rho_new == 0.0 || !std::isfinite(rho_new)) break;
+    const double beta = it == 0 ? 0.0 : (rho_new / rho) * (alpha / omega);
+    axpby(-omega, v, 1.0, p);                 // p = p - omega v
+    axpby(1.0, r, beta, p);                   // p = r + beta p
+    precond_any<T>(p, ph, o, inner, u);       // ph = P~^{-1} p
+    kkt_matvec<T>(ph, v, eps, u);             // v = M ph
+    const double rv = dot(rh, v);
+    if (rv == 0.0 || !std::isfinite(rv)) break;
+    alpha = rho_new / rv;
+    CK(cudaMemcpyAsync(sv, r, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    axpby(-alpha, v, 1.0, sv);                // s = r - alpha v
+    precond_any<T>(sv, sh, o, inner, u);      // sh = P~^{-1} s
+    kkt_matvec<T>(sh, t, eps, u);             // t = M sh
+    const double tt = dot(t, t);
+    omega = tt > 0.0 ? dot(t, sv) / tt : 0.0;
+    axpby(alpha, ph, 1.0, x);                 // x += alpha ph + omega sh
+    axpby(omega, sh, 1.0, x);
+    CK(cudaMemcpyAsync(r, sv, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    axpby(-omega, t, 1.0, r);                 // r = s - omega t
+    rho = rho_new;
+    ++it;
+    const double rn = std::sqrt(dot(r, r));
+    if (!std::isfinite(rn)) fail(FWI_E_NUMERIC, "non-finite residual in BiCGStab");
+    if (rn <= tol * bnorm) { conv = true; break; }
+    if (omega == 0.0) break;
+  }
+  if (iters) *iters += it;
+  return conv ? 0 : 1;
+}
 
 template <> const float2 *Ctx::u_T<float>() {
   if (u_version32 != fwd_version) {
@@ -1596,7 +1758,7 @@ template <> const double2 *Ctx::u_T<double>() { return u64.p; }
 // precision T on the normalised residual, update and residual in FP64, until
 // every block satisfies ||rhs - A' x|| <= fwd_tol ||rhs|| (Sec. 2, Au = f).
 template <typename T>
-int Ctx::refined_solve(const double2 *rhs, double2 *x, int cj, const fwi_opts &o, fwi_stats *stats) {
+int Ctx::refined_solve(const double2 *rhs, double2 *x, int cj, const fwi_opts &o, fwi_stats *stats, bool warm) {
   typedef typename cplx<T>::t T2;
   ensure_work<T>(o);
   Work<T> &w = work<T>();
@@ -1604,8 +1766,13 @@ int Ctx::refined_solve(const double2 *rhs, double2 *x, int cj, const fwi_opts &o
   LevelView<T> LT = viewA<T>();
   const int nt = L64.n_tiles;
   rho64.alloc(F0);
-  CK(cudaMemsetAsync(x, 0, F0 * sizeof(double2), st));
-  CK(cudaMemcpyAsync(rho64.p, rhs, F0 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  if (warm) {
+    // start from the wavefields x already holds: rho = rhs - A' x in FP64
+    field_op<double>(FM_RESID, cj, 0.0, x, rhs, rho64.p, true, 0);
+  } else {
+    CK(cudaMemsetAsync(x, 0, F0 * sizeof(double2), st));
+    CK(cudaMemcpyAsync(rho64.p, rhs, F0 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  }
   std::vector<double> n0(B), nb(B), fac(B);
   auto block_norms = [&](const double2 *v, std::vector<double> &out) {
     block_dots<double>(1, v, v, nullptr, nullptr, nullptr, nullptr);
@@ -1675,8 +1842,14 @@ void Ctx::forward(const fwi_opts &o, fwi_stats *stats) {
   KPROF("k_set_sources", -1, 0, st);
   k_set_sources<<<grid_for(B, 128), 128, 0, st>>>(B, d_src_node.p, d_src_amp.p, f64.p);
   KCHECK();
-  int rc = o.precision == FWI_C128 ? refined_solve<double>(f64.p, u64.p, 0, o, stats)
-                                   : refined_solve<float>(f64.p, u64.p, 0, o, stats);
+  // warm start from the previous forward wavefields of this layout (a Newton
+  // trajectory changes the model a little per step); same fwd_tol either way
+  const bool warm = o.fwd_warm && u64_valid && u64.n == (size_t)F0;
+  u64_valid = false;
+  int rc = o.precision == FWI_C128 ? refined_solve<double>(f64.p, u64.p, 0, o, stats, warm)
+                                   : refined_solve<float>(f64.p, u64.p, 0, o, stats, warm);
+  u64_valid = rc == FWI_OK;
+  if (stats) stats->fwd_warm = warm ? 1 : 0;
   ++fwd_version;
   // receivers: q = Q u, r = d - q
   int nrec = (int)rec_node.size();
@@ -1817,7 +1990,12 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
   CK(cudaMemsetAsync(xi64.p, 0, nkkt * sizeof(double), st));
   CK(cudaMemcpyAsync(rho_k64.p, b64.p, nkkt * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const bool c128 = o.precision == FWI_C128;
-  if (c128) ensure_krylov<double>(o); else ensure_krylov<float>(o);
+  if (o.outer_solver == 1) {
+    // the outer BiCGStab allocates its eight vectors itself (no Krylov basis)
+    if (c128) ensure_work<double>(o); else ensure_work<float>(o);
+  } else {
+    if (c128) ensure_krylov<double>(o); else ensure_krylov<float>(o);
+  }
   int outer = 0, sweeps = 0;
   long long inner = 0;
   double worst = 0.0;
@@ -1845,7 +2023,11 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
       KPROF("k_seg_scale", -1, 16.0 * nkkt, st);
       k_seg_scale<double, double><<<g, 256, 0, st>>>(d_segs.p, rho_k64.p, inst_fac.p, w.rhs.p);
       KCHECK();
-      fgmres<double>(w.rhs.p, w.sol.p, std::max(o.tol * 0.5, 1e-14), left, o.eps, o, &outer, &inner, u_T<double>());
+      if (o.outer_solver == 1)
+        bicgstab_outer<double>(w.rhs.p, w.sol.p, std::max(o.tol * 0.5, 1e-14), left, o.eps, o, &outer, &inner,
+                               u_T<double>());
+      else
+        fgmres<double>(w.rhs.p, w.sol.p, std::max(o.tol * 0.5, 1e-14), left, o.eps, o, &outer, &inner, u_T<double>());
       inst_fac.upload(back, st);
       KPROF("k_seg_axpy", -1, 24.0 * nkkt, st);
       k_seg_axpy<double><<<g, 256, 0, st>>>(d_segs.p, w.sol.p, inst_fac.p, xi64.p);
@@ -1855,7 +2037,10 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
       KPROF("k_seg_scale", -1, 12.0 * nkkt, st);
       k_seg_scale<double, float><<<g, 256, 0, st>>>(d_segs.p, rho_k64.p, inst_fac.p, w.rhs.p);
       KCHECK();
-      fgmres<float>(w.rhs.p, w.sol.p, o.sweep_tol, left, o.eps, o, &outer, &inner, u_T<float>());
+      if (o.outer_solver == 1)
+        bicgstab_outer<float>(w.rhs.p, w.sol.p, o.sweep_tol, left, o.eps, o, &outer, &inner, u_T<float>());
+      else
+        fgmres<float>(w.rhs.p, w.sol.p, o.sweep_tol, left, o.eps, o, &outer, &inner, u_T<float>());
       inst_fac.upload(back, st);
       KPROF("k_seg_axpy", -1, 20.0 * nkkt, st);
       k_seg_axpy<float><<<g, 256, 0, st>>>(d_segs.p, w.sol.p, inst_fac.p, xi64.p);
@@ -2189,7 +2374,10 @@ static int check_opts(const fwi_opts *o) {
   if (!o) return 0;
   if (o->restart < 1 || o->restart > 200 || o->nu1 < 0 || o->nu2 < 0 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_wdepth < 0 ||
       o->inner_iters < 1 || o->fwd_iters < 1 || !(o->tol > 0.0) || o->max_outer < 1 ||
-      (o->precision != FWI_C128 && o->precision != FWI_C64_REFINE))
+      (o->precision != FWI_C128 && o->precision != FWI_C64_REFINE) || o->mg_wdepth > MAX_LEVELS ||
+      o->arnoldi_dots < FWI_DOT_RUNS || o->arnoldi_dots > FWI_DOT_COMP || o->strip_rows < 2 ||
+      o->strip_rows > 64 || (o->coarse_threads != 512 && o->coarse_threads != 1024) || o->outer_solver < 0 ||
+      o->outer_solver > 1)
     return 0;
   return 1;
 }
@@ -2220,7 +2408,11 @@ void fwi_default_opts(fwi_opts *o) {
   o->fwd_iters = 60;
   o->max_fwd_refine = 20;
   o->use_graph = 1;
-  o->arnoldi_fp64 = 1;
+  o->arnoldi_dots = FWI_DOT_COMP;
+  o->strip_rows = 16;
+  o->fwd_warm = 1;
+  o->outer_solver = 0;
+  o->coarse_threads = 512;
   o->check_orth = 0;
 }
 
@@ -2641,10 +2833,7 @@ static int mg_cycle_noalloc_impl(fwi::Ctx &c, const fwi_opts &o, const void *b, 
     lt[l] = (T2 *)(base + off); off += bytes;
   }
   size_t smem = c.smem_bytes[sizeof(T) == 8];
-  if (smem > 48 * 1024) {
-    CK(cudaFuncSetAttribute(fwi::k_coarse_cycle<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CK(cudaFuncSetAttribute(fwi::k_coarse_cycle<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
+  if (smem > 48 * 1024) fwi::set_coarse_smem<T>((int)smem);
   // no live stencil timing inside this call: its event buffers are allocated
   // on first use, and this call allocates nothing
   struct TimerBlock {
@@ -2667,9 +2856,7 @@ int fwi_mg_cycle_noalloc(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void
   fwi_default_opts(&o);
   if (opts) o = *opts;
   if (!b || !x || !check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid arguments");
-  char key[256];
-  snprintf(key, sizeof key, "%d|%d|%.17g|%.17g", c.model_version, o.mg_levels, o.shift_beta, o.sigma_cap);
-  if (!c.layout_ok || c.hier_key != key)
+  if (!c.layout_ok || c.hier_key != fwi::hierarchy_key(c.model_version, o))
     fwi::fail(FWI_E_INVAL, "fwi_mg_cycle_noalloc: no multigrid hierarchy for these options and the current "
                            "models; call fwi_mg_cycle (or fwi_forward) with the same options first");
   if (precision == FWI_C128) return mg_cycle_noalloc_impl<double>(c, o, b, x);

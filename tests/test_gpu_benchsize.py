@@ -130,7 +130,7 @@ def test_kkt_solve_at_benchmark_size(bench, forward_bench, oracle_gmres_full, pr
     ds, st = f.kkt_solve(opts)
     assert st["rel_res"] <= 1e-7
     assert _rel(ds, ds_ref) < 1e-5, _rel(ds, ds_ref)
-    # FP64 Arnoldi inner products keep the basis orthogonal to rounding level
+    # the Arnoldi inner products keep the basis orthogonal to rounding level
     assert st["orth_loss"] < 1e-5, st["orth_loss"]
 
 
@@ -140,3 +140,23 @@ def test_gradient_at_benchmark_size(bench, forward_bench):
     phi, gr = fwi.gradient(prob, wl.gamma_start.ravel(), d)
     assert _rel(g, gr) < 1e-4, _rel(g, gr)
     assert abs(mis[0] - phi) <= 1e-6 * phi
+
+
+@pytest.mark.parametrize("strip_rows,coarse_threads", [(8, 1024), (32, 512), (5, 1024)])
+def test_layout_options_keep_the_cycle(bench, strip_rows, coarse_threads):
+    """The autotuned launch layout (column-strip height, threads of the
+    shared-memory coarse cycle) changes no arithmetic: complex128 cycle and
+    inner solve equal the oracle as with the defaults."""
+    P, f, wl, prob, d = bench
+    opts = P.default_opts(strip_rows=strip_rows, coarse_threads=coarse_threads, inner_iters=3)
+    N = prob.operator(wl.gamma_start.ravel(), 0).shape[0]
+    bt, b = _field(prob.n_blocks * N, 33)
+    x = f.mg_cycle(bt, opts).cpu().numpy()
+    xi = f.inner_solve(bt, opts).cpu().numpy()
+    for blk in range(prob.n_blocks):
+        fi = prob.block_freq(blk)
+        h = _hier(P, wl, prob, fi, opts)
+        sl = slice(blk * N, (blk + 1) * N)
+        assert _rel(x[sl], h.vcycle(b[sl])) < 1e-10
+        ref, _ = mg.inner_solve(prob.operator(wl.gamma_start.ravel(), fi), h, b[sl], 3)
+        assert _rel(xi[sl], ref) < 1e-8

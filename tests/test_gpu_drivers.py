@@ -263,14 +263,15 @@ def test_gauss_newton_lambda_max_matches_oracle(lib):
     f.close()
 
 
-@pytest.mark.parametrize("fp64", [1, 0])
+@pytest.mark.parametrize("fp64", [2, 1, 0])
 def test_arnoldi_dot_precision_options(lib, fp64):
-    """Both Arnoldi inner-product forms (FP64 products; FP32 runs summed in
-    FP64) reach the same KKT update, and the measured loss of orthogonality of
-    the complex64 basis stays at single-precision rounding level."""
+    """The three Arnoldi inner-product forms (compensated Dot2; FP64 products;
+    FP32 runs summed in FP64) reach the same KKT update, and the measured loss
+    of orthogonality of the complex64 basis stays at single-precision rounding
+    level."""
     wl = FI.micro_workload(seed=7, nx=41, nz=21, npml=8, n_src=3, n_rec=8)
     P, f, prob, d = _setup(wl)
-    opts = P.default_opts(eps=1e-2, tol=1e-7, arnoldi_fp64=fp64, check_orth=1)
+    opts = P.default_opts(eps=1e-2, tol=1e-7, arnoldi_dots=fp64, check_orth=1)
     f.forward(opts)
     ds, st = f.kkt_solve(opts)
     K = kkt.KKT(prob, wl.gamma_start.ravel(), d, 1e-2, include_Ls_n=True)
@@ -301,4 +302,28 @@ def test_kernel_profile_counts_every_direct_launch(lib):
     assert len(rows) == 1 and rows[0]["launches"] == 2 and rows[0]["ms"] > 0
     assert rows[0]["bytes"] == (5 + 6) * 8 * n
     assert prof["gaps"] == launched - 1
+    f.close()
+
+
+def test_warm_started_forward_matches_lu(lib):
+    """After a small model change the forward solve starts from the previous
+    wavefields (fwd_warm) and reaches the same tolerance: wavefields equal the
+    oracle's LU solution at the new model within 1e-5, in no more refinement
+    sweeps than a cold start."""
+    import paper_2204_06489_gb300 as P
+    wl = FI.micro_workload(seed=13, nx=61, nz=31, npml=8, n_src=3, n_rec=8)
+    Pm, f, prob, d = _setup(wl)
+    f.forward(P.default_opts(), want_data=False)
+    s1 = wl.gamma_start * (1.0 + 0.01 * gaussian_filter(np.random.default_rng(4).standard_normal(wl.gamma_start.shape), 3.0))
+    f.set_model(0, s1)
+    _, _, st_w = f.forward(P.default_opts(), want_data=False)
+    u_w = f.wavefields().cpu().numpy()
+    f.set_model(0, s1)
+    _, _, st_c = f.forward(P.default_opts(fwd_warm=0), want_data=False)
+    assert st_w["fwd_warm"] == 1 and st_c["fwd_warm"] == 0
+    assert st_w["fwd_sweeps"] <= st_c["fwd_sweeps"]
+    ref = fwi.forward(prob, s1.ravel())
+    N = ref.shape[1]
+    for b in range(prob.n_blocks):
+        assert _rel(u_w[b * N:(b + 1) * N], ref[b]) < 1e-5
     f.close()

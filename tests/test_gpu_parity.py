@@ -238,8 +238,16 @@ def test_preconditioner_apply(setup, forward_done):
             assert _rel(a, r) < 1e-8, _rel(a, r)
 
 
+@pytest.fixture(scope="module")
+def direct_updates(setup):
+    """The oracle's model update per instance from the sparse direct solve of
+    the whole KKT system (eps = 1e-2, with the -L s_n term)."""
+    P, f, wls, probs, d_obs = setup
+    return [K.delta_s(K.solve_direct()) for K in _oracle_kkts(wls, probs, d_obs, 1e-2, True)]
+
+
 @pytest.mark.parametrize("prec", [0, 1])
-def test_kkt_solve_matches_direct(setup, forward_done, prec):
+def test_kkt_solve_matches_direct(setup, forward_done, direct_updates, prec):
     """Whole KKT solve (both instances jointly) against the oracle's sparse
     direct solve per instance: relative residual <= 1e-6 recomputed in FP64 and
     model update within 1e-5."""
@@ -248,12 +256,27 @@ def test_kkt_solve_matches_direct(setup, forward_done, prec):
     opts = P.default_opts(eps=eps, precision=prec, tol=1e-7, inner_iters=6)
     ds, st = f.kkt_solve(opts)
     assert st["rel_res"] <= 1e-7
-    Ks = _oracle_kkts(wls, probs, d_obs, eps, True)
     o = 0
-    for K in Ks:
-        ref = K.delta_s(K.solve_direct())
-        got = ds[o:o + K.Nc]
-        o += K.Nc
+    for ref in direct_updates:
+        got = ds[o:o + ref.size]
+        o += ref.size
+        assert _rel(got, ref) < 1e-5, _rel(got, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kkt_solve_with_outer_bicgstab(setup, forward_done, direct_updates, prec):
+    """The memory-lean outer solver (BiCGStab in the real inner product, the
+    option of Sec. 7) reaches the same, unique KKT update as the oracle's
+    direct solve, with the FP64 residual <= 1e-7."""
+    P, f, wls, probs, d_obs = setup
+    eps = 1e-2
+    opts = P.default_opts(eps=eps, precision=prec, tol=1e-7, inner_iters=6, outer_solver=1)
+    ds, st = f.kkt_solve(opts)
+    assert st["rel_res"] <= 1e-7
+    o = 0
+    for ref in direct_updates:
+        got = ds[o:o + ref.size]
+        o += ref.size
         assert _rel(got, ref) < 1e-5, _rel(got, ref)
 
 
