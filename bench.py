@@ -121,7 +121,7 @@ def _peaks():
 # per byte of its fused pass (b and the result, plus x unless it starts from
 # zero), from the ncu capture summarised under profiles/ (None while the
 # kernel has changed since the last capture).
-TRAFFIC_PER_FUSED_BYTE = (207.3 + 116.2) / (229.9 + 153.3)
+TRAFFIC_PER_FUSED_BYTE = None
 
 
 def _roofline(ms, nbytes, n, peaks, fused_bytes=None):
@@ -275,8 +275,24 @@ def run_extra_case(args):
         o = P.Opts.from_buffer_copy(opts)
         o.max_outer = args.max_outer
         _, table = tune_kkt(f, o, (2, 4, 6, 8, 12, 16, 24, 48), (2,), (30,))
-        out["sweep"] = [{"inner_iters": n, "kkt_s": round(t, 3), "outer": k, "converged": ok}
-                        for n, wd, rs, t, k, ok, _, _ in table]
+        out["sweep"] = [{"inner_solver": "bicgstab+multigrid", "inner_iters": n, "kkt_s": round(t, 3), "outer": k,
+                         "converged": ok} for n, wd, rs, t, k, ok, _, _ in table]
+        # the paper's incomplete-LU block approximation (zero fill on the GPU):
+        # applied once as A~, and as the preconditioner of BiCGStab
+        for solver, iters in ((2, 1), (1, 4), (1, 8), (1, 16)):
+            oi = P.Opts.from_buffer_copy(o)
+            oi.inner_solver = solver
+            oi.inner_iters = iters
+            print(f"tradeoff: inner_solver {solver}, {iters} iterations", file=sys.stderr, flush=True)
+            f.kkt_solve(oi, allow_noconv=True) if solver == 2 else None   # builds the factors (untimed)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = f.kkt_solve(oi, allow_noconv=True)
+            torch.cuda.synchronize()
+            out["sweep"].append({"inner_solver": "ilu0 once" if solver == 2 else "bicgstab+ilu0",
+                                 "inner_iters": iters if solver == 1 else 0,
+                                 "kkt_s": round(time.perf_counter() - t0, 3), "outer": st["outer_iters"],
+                                 "converged": st["rel_res"] <= oi.tol})
     elif args.case == "rsgn":
         o = P.Opts.from_buffer_copy(opts)
         o.max_outer = args.max_outer
@@ -330,7 +346,7 @@ def run_kkt_case(args):
     torch.cuda.set_stream(stream)
     wl = _workload()
     opts = P.default_opts(eps=EPS, inner_iters=args.inner_iters or 12, include_Ls_n=INCLUDE_LS_N,
-                          max_outer=args.max_outer)
+                          max_outer=args.max_outer, use_graph=0 if args.no_graph else 1)
     f = _setup_ctx(P, [wl], opts, stream)
     f.forward(opts, want_data=False)
     torch.cuda.synchronize()
@@ -365,15 +381,30 @@ def run_epsrule_case(args):
     eps_rule = 1e-2 * lam
     out = {"case": "epsrule", "lambda_max": lam, "power_iters": 10, "lambda_s": round(t_lam, 2),
            "alpha": 1e-2, "eps_rule": eps_rule, "steps": []}
+    # the block solves' accuracy tied to eps: the autotuner picks the inner
+    # iteration count at each eps (one KKT solve per candidate, untimed)
+    from paper_2204_06489_gb300.autotune import tune_kkt
+    chosen = {}
+    for eps, cands in ((eps_rule, (16, 24, 32, 48, 64)), (EPS, (4, 6, 8, 12, 16))):
+        o = P.Opts.from_buffer_copy(opts)
+        o.eps = eps
+        f.set_model(0, wl.gamma_start)
+        f.forward(o, want_data=False)
+        best, table = tune_kkt(f, o, cands, (None,), (None,))
+        chosen[eps] = best.inner_iters
+        out.setdefault("autotune", []).append({"eps": eps, "table": [
+            {"inner_iters": n, "s": round(t, 3), "outer": k, "ok": ok} for n, wd, rs, t, k, ok, _, _ in table]})
     for eps in (eps_rule, EPS):
         o = P.Opts.from_buffer_copy(opts)
         o.eps = eps
+        o.inner_iters = chosen[eps]
         f.set_model(0, wl.gamma_start)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         ds, st = f.newton_step(o, allow_noconv=True)
         torch.cuda.synchronize()
-        out["steps"].append({"eps": eps, "step_s": round(time.perf_counter() - t1, 3), "outer_iters": st["outer_iters"],
+        out["steps"].append({"eps": eps, "inner_iters": o.inner_iters,
+                             "step_s": round(time.perf_counter() - t1, 3), "outer_iters": st["outer_iters"],
                              "rel_res": st["rel_res"], "converged": st["rel_res"] <= o.tol,
                              "kkt_ms": st["t_solve_ms"]})
     print(json.dumps(out))
@@ -715,6 +746,8 @@ def run_newton(args):
 
 
 def main():
+    import faulthandler
+    faulthandler.enable()            # a native crash prints the Python stack to stderr
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -725,6 +758,7 @@ def main():
                     help="skip the untimed extras of the headline line (complex128 form, kernel table, "
                          "Arnoldi precision comparison)")
     ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--no-graph", action="store_true", help="profiling cases: direct launches, no graph replay")
     ap.add_argument("--case", default="newton",
                     choices=["newton", "inner", "batch3a", "batch3b", "large", "autograd", "rsgn", "tradeoff",
                              "epsrule", "kkt"])

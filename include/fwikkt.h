@@ -113,6 +113,11 @@ typedef struct {
                              inner product (eight KKT-size vectors, no basis; the
                              memory-lean option of Sec. 7); outer_iters then counts
                              BiCGStab iterations (two preconditioner applications each) [0] */
+  int inner_solver;       /* block solves inside the preconditioner: 0 BiCGStab with the
+                             shifted-Laplacian multigrid cycle; 1 BiCGStab with ILU(0) of A';
+                             2 one ILU(0) application as A~ (the paper's incomplete-LU
+                             approximation, zero fill); forward/adjoint modelling always
+                             uses 0 (fwi_inner_solve: 1 and 2 mean BiCGStab + ILU(0)) [0] */
 } fwi_opts;
 
 typedef struct {

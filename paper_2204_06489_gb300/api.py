@@ -52,7 +52,8 @@ class Opts(C.Structure):
                 ("mg_levels", C.c_int), ("fwd_tol", C.c_double), ("fwd_iters", C.c_int),
                 ("max_fwd_refine", C.c_int), ("use_graph", C.c_int), ("arnoldi_dots", C.c_int),
                 ("check_orth", C.c_int), ("strip_rows", C.c_int), ("coarse_threads", C.c_int),
-                ("fwd_warm", C.c_int), ("outer_solver", C.c_int)]
+                ("fwd_warm", C.c_int), ("outer_solver", C.c_int),
+                ("inner_solver", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -1106,6 +1106,125 @@ __global__ void k_gauss_jordan(const int *dims, const long long *aug_off, const 
 }
 
 // ---------------------------------------------------------------------------
+// ILU(0) of the 5-point operator A' (the incomplete-LU block approximation of
+// Sec. 5, zero fill), natural ordering k = j Nx + i.  With west and north the
+// only couplings below the diagonal:
+//   d_k  = cc_k - cw_k ce_{k-1} / d_{k-1} - cn_k cs_{k-Nx} / d_{k-Nx},
+//   lw_k = cw_k / d_{k-1},  ln_k = cn_k / d_{k-Nx},  U off-diagonals = A's.
+// Node (j, i) depends on (j, i-1) and (j-1, i), so the factorisation and both
+// substitutions advance by anti-diagonal wavefronts t = i + j: thread j owns
+// grid row j and handles column t - j at step t; the value of row j - 1 (or
+// j + 1 backwards) from the previous step comes through shared memory.
+// ---------------------------------------------------------------------------
+struct IluDev {
+  long long off;   // offset of this operator's factor arrays (complex, [Nz][Nx])
+};
+
+// Factors of every A operator (one CTA per operator, FP64): dinv = 1/d, lw,
+// ln, and the east / south couplings ce, cs; stored in both precisions.
+__global__ void k_ilu_factor(const OpDev *ops, const int *op_ids, const long long *fac_off, const double2 *st64,
+                             const double *gam64, double2 *f64, float2 *f32, long long fac_stride) {
+  const OpDev o = ops[op_ids[blockIdx.x]];
+  const long long base = fac_off[blockIdx.x];
+  double2 *dinv = f64 + base, *lw = dinv + fac_stride, *ln = lw + fac_stride, *ce = ln + fac_stride,
+          *cs = ce + fac_stride;
+  float2 *g0 = f32 + base, *g1 = g0 + fac_stride, *g2 = g1 + fac_stride, *g3 = g2 + fac_stride,
+         *g4 = g3 + fac_stride;
+  extern __shared__ double2 sh_d[];            // [2][nz]: d of each row at the previous step
+  const int nx = o.nx, nz = o.nz;
+  for (int t = 0; t < nx + nz - 1; ++t) {
+    double2 *prev = sh_d + (t & 1) * nz, *cur = sh_d + ((t + 1) & 1) * nz;
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) {
+      const int i = t - j;
+      if (i < 0 || i >= nx) continue;
+      Stencil<double> sc;
+      sc.load(o, st64, gam64, j, i, false);
+      double2 d = sc.cc, vlw = make_double2(0, 0), vln = make_double2(0, 0);
+      if (i > 0) {
+        const double2 dw = prev[j];            // d of (j, i - 1): this row, previous step
+        Stencil<double> sw;
+        sw.load(o, st64, gam64, j, i - 1, false);
+        vlw = cdiv(sc.cw, dw);
+        d = csub(d, cmul(vlw, sw.ce));
+      }
+      if (j > 0) {
+        const double2 dn = prev[j - 1];        // d of (j - 1, i): the row above, previous step
+        Stencil<double> sn;
+        sn.load(o, st64, gam64, j - 1, i, false);
+        vln = cdiv(sc.cn, dn);
+        d = csub(d, cmul(vln, sn.cs));
+      }
+      cur[j] = d;
+      const long long k = (long long)j * nx + i;
+      const double2 di = cdiv(make_double2(1.0, 0.0), d);
+      dinv[k] = di; lw[k] = vlw; ln[k] = vln; ce[k] = sc.ce; cs[k] = sc.cs;
+      g0[k] = make_float2((float)di.x, (float)di.y);
+      g1[k] = make_float2((float)vlw.x, (float)vlw.y);
+      g2[k] = make_float2((float)vln.x, (float)vln.y);
+      g3[k] = make_float2((float)sc.ce.x, (float)sc.ce.y);
+      g4[k] = make_float2((float)sc.cs.x, (float)sc.cs.y);
+    }
+    __syncthreads();
+  }
+}
+
+// x_b = (L U)^{-1} b_b for every block (one CTA per block); CJ: the factors of
+// conj(A') (= conjugated factors), i.e. the adjoint block approximation.  x may
+// alias b (each element is read before it is overwritten, by its own thread).
+template <typename T, bool CJ>
+__global__ void k_ilu_solve(const BlkDev *blks, const OpDev *ops, const long long *fac_off_of_op,
+                            const typename cplx<T>::t *fac, long long fac_stride, const int *skip,
+                            const typename cplx<T>::t *b, typename cplx<T>::t *x) {
+  typedef typename cplx<T>::t T2;
+  if (skip && skip[blockIdx.x]) return;
+  const BlkDev bk = blks[blockIdx.x];
+  const OpDev o = ops[bk.op];
+  const int nx = o.nx, nz = o.nz;
+  const T2 *dinv = fac + fac_off_of_op[bk.op], *lw = dinv + fac_stride, *ln = lw + fac_stride,
+           *ce = ln + fac_stride, *cs = ce + fac_stride;
+  const T2 *bb = b + bk.off;
+  T2 *xb = x + bk.off;
+  extern __shared__ unsigned char sh_raw[];
+  T2 *sh = reinterpret_cast<T2 *>(sh_raw);       // [2][nz]
+  const T2 zero = mk<T2>(0, 0);
+  // forward: y_k = b_k - lw_k y_{k-1} - ln_k y_{k-Nx}
+  for (int j = threadIdx.x; j < nz; j += blockDim.x) sh[j] = zero;
+  __syncthreads();
+  for (int t = 0; t < nx + nz - 1; ++t) {
+    T2 *prev = sh + (t & 1) * nz, *cur = sh + ((t + 1) & 1) * nz;
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) {
+      const int i = t - j;
+      if (i < 0 || i >= nx) continue;
+      const long long k = (long long)j * nx + i;
+      T2 y = bb[k];
+      if (i > 0) y = csub(y, cmul(cmaybe_conj(lw[k], CJ), prev[j]));
+      if (j > 0) y = csub(y, cmul(cmaybe_conj(ln[k], CJ), prev[j - 1]));
+      cur[j] = y;
+      xb[k] = y;
+    }
+    __syncthreads();
+  }
+  // backward: x_k = (y_k - ce_k x_{k+1} - cs_k x_{k+Nx}) / d_k
+  for (int j = threadIdx.x; j < nz; j += blockDim.x) { sh[j] = zero; sh[nz + j] = zero; }
+  __syncthreads();
+  for (int t = nx + nz - 2; t >= 0; --t) {
+    T2 *prev = sh + (t & 1) * nz, *cur = sh + ((t + 1) & 1) * nz;
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) {
+      const int i = t - j;
+      if (i < 0 || i >= nx) continue;
+      const long long k = (long long)j * nx + i;
+      T2 acc = xb[k];
+      if (i + 1 < nx) acc = csub(acc, cmul(cmaybe_conj(ce[k], CJ), prev[j]));
+      if (j + 1 < nz) acc = csub(acc, cmul(cmaybe_conj(cs[k], CJ), prev[j + 1]));
+      const T2 v = cmul(acc, cmaybe_conj(dinv[k], CJ));
+      cur[j] = v;
+      xb[k] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // per-block reductions and BiCGStab vector updates
 // ---------------------------------------------------------------------------
 // partial[tile][q] = sum over the tile of conj(a_q) b_q (q < nd): per-thread

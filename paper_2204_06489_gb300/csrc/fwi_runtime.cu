@@ -291,6 +291,13 @@ struct Ctx {
   DBuf<float2> dg32, dgi32;
   DBuf<int> d_inst_nlev;
   DBuf<double> cfK, cfG;   // per-block coupling factors (KKT scaled, gradient)
+  // ILU(0) factors of every A operator ([5][total] complex: 1/d, lw, ln, ce, cs)
+  std::string ilu_key;
+  DBuf<double2> ilu64;
+  DBuf<float2> ilu32;
+  DBuf<long long> ilu_off;  // per operator id: offset of its factors (-1: none)
+  long long ilu_stride = 0;
+  int ilu_maxnz = 0;
   size_t smem_bytes[2] = {0, 0};
   // forward state
   bool have_fwd = false;
@@ -382,8 +389,11 @@ struct Ctx {
   template <typename T> void mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
                                       const fwi_opts &o, const BFuse<T> *fz = nullptr);
   template <typename T> void bicg_update_into(const BFuse<T> &fz);
+  void ensure_ilu();
+  template <typename T> void ilu_apply(int cj, const typename cplx<T>::t *b, typename cplx<T>::t *x);
   template <typename T> void inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
-                                         int iters, double tol, const fwi_opts &o, long long *count);
+                                         int iters, double tol, const fwi_opts &o, long long *count,
+                                         bool ilu = false);
   template <typename T> void mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
                                            const fwi_opts &o, typename cplx<T>::t *const *lx,
                                            typename cplx<T>::t *const *lb, typename cplx<T>::t *const *lt,
@@ -425,6 +435,9 @@ struct Ctx {
   void seg_norms(const double *x);
   int kkt_solve(const fwi_opts &o, fwi_stats *stats);
   void sync() {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) fail(FWI_E_CUDA, "internal: stream synchronisation during a capture");
     CK(cudaStreamSynchronize(st));
     if (ev_used) harvest();
     if (g_prof.used) g_prof.harvest();
@@ -1228,11 +1241,67 @@ void Ctx::bicg_update_into(const BFuse<T> &fz) {
   }
 }
 
+// ILU(0) factors of every A operator (level 0, one per instance and
+// frequency), built once per hierarchy (models and options).
+void Ctx::ensure_ilu() {
+  if (ilu_key == hier_key && ilu64.p) return;
+  std::vector<int> ids;
+  std::vector<long long> offs(h_ops.size(), -1), foff;
+  long long tot = 0;
+  int maxnz = 1;
+  for (int b = 0; b < B; ++b) {
+    const int id = lv[0].hA[b].op;
+    if (offs[id] >= 0) continue;
+    offs[id] = tot;
+    ids.push_back(id);
+    foff.push_back(tot);
+    tot += (long long)h_ops[id].nx * h_ops[id].nz;
+    maxnz = std::max(maxnz, h_ops[id].nz);
+  }
+  ilu64.alloc(5 * tot);
+  ilu32.alloc(5 * tot);
+  ilu_off.upload(offs, st);
+  ilu_stride = tot;
+  ilu_maxnz = maxnz;
+  DBuf<int> dids;
+  DBuf<long long> dfo;
+  dids.upload(ids, st);
+  dfo.upload(foff, st);
+  const int nth = std::min(1024, (maxnz + 31) / 32 * 32);
+  const size_t smem = 2 * (size_t)maxnz * sizeof(double2);
+  KPROF("k_ilu_factor", -1, 0, st);
+  k_ilu_factor<<<(int)ids.size(), nth, smem, st>>>(d_ops.p, dids.p, dfo.p, st64.p, gam64.p, ilu64.p, ilu32.p, tot);
+  KCHECK();
+  sync();
+  ilu_key = hier_key;
+}
+
+template <typename T> static const typename cplx<T>::t *ilu_ptr(Ctx &c);
+template <> const float2 *ilu_ptr<float>(Ctx &c) { return c.ilu32.p; }
+template <> const double2 *ilu_ptr<double>(Ctx &c) { return c.ilu64.p; }
+
+// x = (L U)^{-1} b (cj: the adjoint approximation) for every block.
+template <typename T>
+void Ctx::ilu_apply(int cj, const typename cplx<T>::t *b, typename cplx<T>::t *x) {
+  typedef typename cplx<T>::t T2;
+  // the factors are built before any stream capture (ensure_ilu allocates,
+  // uploads and synchronises); here they must already exist
+  if (!(ilu_key == hier_key && ilu64.p)) fail(FWI_E_INVAL, "internal: ILU(0) factors not built before use");
+  const int nth = std::min(1024, (ilu_maxnz + 31) / 32 * 32);
+  const size_t smem = 2 * (size_t)ilu_maxnz * sizeof(T2);
+  KPROF("k_ilu_solve", 0, 4.0 * sizeof(T2) * F0, st);
+  if (cj) k_ilu_solve<T, true><<<B, nth, smem, st>>>(lv[0].blksA.p, d_ops.p, ilu_off.p, ilu_ptr<T>(*this), ilu_stride,
+                                                    cur_skip, b, x);
+  else k_ilu_solve<T, false><<<B, nth, smem, st>>>(lv[0].blksA.p, d_ops.p, ilu_off.p, ilu_ptr<T>(*this), ilu_stride,
+                                                  cur_skip, b, x);
+  KCHECK();
+}
+
 // Batched right-preconditioned BiCGStab, one independent system per block
 // (per-block scalars), x = approx A'^{-1} b (cj = 1: A'^H).
 template <typename T>
 void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj, int iters, double tol,
-                      const fwi_opts &o, long long *count) {
+                      const fwi_opts &o, long long *count, bool ilu) {
   typedef typename cplx<T>::t T2;
   Work<T> &w = work<T>();
   LevelView<T> L = viewA<T>();
@@ -1284,12 +1353,18 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   T2 *pc = w.p.p, *pn = w.p2.p;
   for (int it = 0; it < iters; ++it) {
     const BFuse<T> fp{w.r.p, w.v.p, pc, pn, w.bst.p};                 // p = r + beta (p - omega v)
-    mg_cycle<T>(pn, w.ph.p, cj, o, &fp);                               // ph = K p
+    if (ilu) {                                                         // ph = K p
+      bicg_update_into<T>(fp);
+      ilu_apply<T>(cj, pn, w.ph.p);
+    } else {
+      mg_cycle<T>(pn, w.ph.p, cj, o, &fp);
+    }
     std::swap(pc, pn);
     apply_dots<T>(cj, w.ph.p, w.v.p, w.rh.p, 1);                       // v = A ph, <rh, v>
     scal_s(2);
     upd(1, w.s.p, w.r.p, w.v.p);                                       // s = r - alpha v
-    mg_cycle<T>(w.s.p, w.sh.p, cj, o);                                 // sh = K s
+    if (ilu) ilu_apply<T>(cj, w.s.p, w.sh.p);                          // sh = K s
+    else mg_cycle<T>(w.s.p, w.sh.p, cj, o);
     apply_dots<T>(cj, w.sh.p, w.t.p, w.s.p, 2);                        // t = A sh, <t, s>, <t, t>
     scal_s(3);
     // x += alpha ph + omega sh; r = s - omega t; <r, r>, <rh, r>
@@ -1344,8 +1419,9 @@ void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count, const t
   int iters = o.inner_iters;
   double tol = o.inner_tol;
   if (tol > 0.0) iters = std::max(iters, 2000);
-  // z_lambda = A'^{-H} v1
-  inner_solve<T>(v1, zl, 1, iters, tol, o, count);
+  // z_lambda = A'^{-H} v1 (inner_solver 2: one ILU(0) application, the paper's A~)
+  if (o.inner_solver == 2) ilu_apply<T>(1, v1, zl);
+  else inner_solve<T>(v1, zl, 1, iters, tol, o, count, o.inner_solver == 1);
   // z_s = (v2 + Re(P~^H z_lambda)) / eps
   long long mx = 0;
   for (auto &I : inst) mx = std::max(mx, (long long)I.g.nx * I.g.nz);
@@ -1358,7 +1434,8 @@ void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count, const t
   KPROF("k_coupling_scatter", 0, 3.0 * sizeof(typename cplx<T>::t) * F0, st);
   k_coupling_scatter<T><<<L.n_tiles, TILE_THREADS, 0, st>>>(L, d_inst.p, cfK.p, u, v3, zs, w.t0b.p);
   KCHECK();
-  inner_solve<T>(w.t0b.p, zu, 0, iters, tol, o, count);
+  if (o.inner_solver == 2) ilu_apply<T>(0, w.t0b.p, zu);
+  else inner_solve<T>(w.t0b.p, zu, 0, iters, tol, o, count, o.inner_solver == 1);
 }
 
 // Preconditioner application, replayed from a CUDA graph when requested (the
@@ -1370,7 +1447,7 @@ void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, con
   if (!graphable) { precond<T>(v, z, o, count, u); return; }
   char key[256];
   snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d", hier_key.c_str(), o.inner_iters, o.mg_cycle,
-           o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta, (const void *)u, o.coarse_threads);
+           o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta, (const void *)u, o.coarse_threads * 10 + o.inner_solver);
   if (w.graph_key != key) {
     if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
     cudaGraph_t gr;
@@ -1394,7 +1471,7 @@ void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, con
   CK(cudaGraphLaunch(w.graph, st));
   g_launches.fetch_add(w.graph_kernels);
   CK(cudaMemcpyAsync(z, w.zout.p, nkkt * sizeof(T), cudaMemcpyDeviceToDevice, st));
-  if (count) *count += 2LL * o.inner_iters * B;
+  if (count && o.inner_solver != 2) *count += 2LL * o.inner_iters * B;
 }
 
 template <typename T>
@@ -1453,7 +1530,7 @@ void Ctx::fgmres_cycle_graph(const fwi_opts &o, double eps, T *x, const typename
   char key[320];
   snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d|%d|%p|%d", hier_key.c_str(), o.inner_iters,
            o.mg_cycle, o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, eps, o.shift_beta, (const void *)u, w.m,
-           o.arnoldi_dots, (void *)x, o.coarse_threads);
+           o.arnoldi_dots, (void *)x, o.coarse_threads * 10 + o.inner_solver);
   if (w.cyc && w.cyc_key == key) return;
   if (w.cyc) { cudaGraphExecDestroy(w.cyc); w.cyc = nullptr; }
   const long long n = nkkt;
@@ -1611,7 +1688,7 @@ int Ctx::fgmres(const T *rhs, T *x, double tol, int maxit, double eps, const fwi
       sync();
       const int kk = hc->k;
       g_launches.fetch_add(w.cyc_body_kernels * (unsigned long long)kk + w.cyc_tail_kernels);
-      if (inner) *inner += 2LL * o.inner_iters * B * kk;
+      if (inner && o.inner_solver != 2) *inner += 2LL * o.inner_iters * B * kk;
       total = hc->total;
       const int state = hc->state;
       if (state == 2) fail(FWI_E_NUMERIC, "non-finite residual in FGMRES");
@@ -1990,6 +2067,7 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
   CK(cudaMemsetAsync(xi64.p, 0, nkkt * sizeof(double), st));
   CK(cudaMemcpyAsync(rho_k64.p, b64.p, nkkt * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const bool c128 = o.precision == FWI_C128;
+  if (o.inner_solver >= 1) ensure_ilu();     // before any graph capture
   if (o.outer_solver == 1) {
     // the outer BiCGStab allocates its eight vectors itself (no Krylov basis)
     if (c128) ensure_work<double>(o); else ensure_work<float>(o);
@@ -2377,7 +2455,7 @@ static int check_opts(const fwi_opts *o) {
       (o->precision != FWI_C128 && o->precision != FWI_C64_REFINE) || o->mg_wdepth > MAX_LEVELS ||
       o->arnoldi_dots < FWI_DOT_RUNS || o->arnoldi_dots > FWI_DOT_COMP || o->strip_rows < 2 ||
       o->strip_rows > 64 || (o->coarse_threads != 512 && o->coarse_threads != 1024) || o->outer_solver < 0 ||
-      o->outer_solver > 1)
+      o->outer_solver > 1 || o->inner_solver < 0 || o->inner_solver > 2)
     return 0;
   return 1;
 }
@@ -2412,6 +2490,7 @@ void fwi_default_opts(fwi_opts *o) {
   o->strip_rows = 16;
   o->fwd_warm = 1;
   o->outer_solver = 0;
+  o->inner_solver = 0;
   o->coarse_threads = 512;
   o->check_orth = 0;
 }
@@ -2729,6 +2808,7 @@ int fwi_apply_precond(fwi_ctx *ctx, const fwi_opts *opts, const void *v, void *z
   if (!v || !z || !check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid arguments");
   if (!c.have_fwd) fwi::fail(FWI_E_INVAL, "fwi_apply_precond needs fwi_forward");
   c.build_hierarchy(o);
+  if (o.inner_solver >= 1) c.ensure_ilu();
   long long cnt = 0;
   if (precision == FWI_C128) {
     c.ensure_work<double>(o);
@@ -2750,14 +2830,17 @@ int fwi_inner_solve(fwi_ctx *ctx, const fwi_opts *opts, const void *b, void *x, 
   if (opts) o = *opts;
   if (!b || !x || !check_opts(&o)) fwi::fail(FWI_E_INVAL, "invalid arguments");
   c.build_hierarchy(o);
+  if (o.inner_solver >= 1) c.ensure_ilu();
   int iters = o.inner_iters;
   long long cnt = 0;
   if (precision == FWI_C128) {
     c.ensure_work<double>(o);
-    c.inner_solve<double>((const double2 *)b, (double2 *)x, adjoint ? 1 : 0, iters, o.inner_tol, o, &cnt);
+    c.inner_solve<double>((const double2 *)b, (double2 *)x, adjoint ? 1 : 0, iters, o.inner_tol, o, &cnt,
+                          o.inner_solver >= 1);
   } else if (precision == FWI_C64_REFINE) {
     c.ensure_work<float>(o);
-    c.inner_solve<float>((const float2 *)b, (float2 *)x, adjoint ? 1 : 0, iters, o.inner_tol, o, &cnt);
+    c.inner_solve<float>((const float2 *)b, (float2 *)x, adjoint ? 1 : 0, iters, o.inner_tol, o, &cnt,
+                         o.inner_solver >= 1);
   } else fwi::fail(FWI_E_INVAL, "bad precision");
   c.sync();
   return FWI_OK;

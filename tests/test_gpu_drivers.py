@@ -327,3 +327,36 @@ def test_warm_started_forward_matches_lu(lib):
     for b in range(prob.n_blocks):
         assert _rel(u_w[b * N:(b + 1) * N], ref[b]) < 1e-5
     f.close()
+
+
+def test_autograd_at_the_differentiation_workload_size(lib):
+    """The differentiation workload's size (801 x 281 at h = 10 m, 30-node
+    layer, 861 x 341 padded; 64 sources, 801 receivers, 6 Hz; complex64
+    wavefields with FP64 refinement, recomputed for the backward pass): the
+    hand-written adjoint gradient against central differences of the misfit
+    along 16 smooth random directions (Gaussian-filtered noise, 10 cells,
+    seeds 0-15), relative error <= 1e-3."""
+    import paper_2204_06489_gb300 as P
+    from paper_2204_06489_gb300.autograd import misfit
+    wl = FI.autograd_workload()
+    f = P.FWI([wl.grid])
+    f.set_survey(0, wl.survey)
+    f.set_model(0, wl.gamma_true)
+    d, _, _ = f.forward(P.default_opts(), want_data=True)
+    f.set_observed(0, d[0])
+    f.set_model(0, wl.gamma_start)
+    opts = P.default_opts()
+    g0 = torch.tensor(wl.gamma_start, dtype=torch.float64, device="cuda", requires_grad=True)
+    phi = misfit(g0, f, mode="recompute", opts=opts)
+    phi.backward()
+    grad = g0.grad.detach().cpu().numpy()
+    s0 = wl.gamma_start
+    for seed in range(16):
+        dirn = gaussian_filter(np.random.default_rng(seed).standard_normal(s0.shape), 10.0)
+        dirn *= 0.003 * s0.mean() / np.abs(dirn).max()
+        with torch.no_grad():
+            fp = misfit(torch.tensor(s0 + dirn, device="cuda"), f, opts=opts).item()
+            fm = misfit(torch.tensor(s0 - dirn, device="cuda"), f, opts=opts).item()
+        an = float(np.sum(grad * dirn))
+        assert abs((fp - fm) / 2 - an) <= 1e-3 * abs(an), (seed, (fp - fm) / 2, an)
+    f.close()

@@ -381,3 +381,53 @@ def test_exact_block_mode_is_gmres_full(lib):
     assert st["rel_res"] <= 1e-10
     assert _rel(ds, K.delta_s(K.solve_direct())) < 1e-8
     f.close()
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_inner_solve_with_ilu0(setup, adjoint):
+    """BiCGStab preconditioned by ILU(0) of A' (the incomplete-LU block
+    approximation of Sec. 5 with zero fill; wavefront substitutions on the
+    GPU), complex128, 5 iterations, against the oracle's same iteration."""
+    from oracle.ilu import ILU0
+    P, f, wls, probs, _ = setup
+    opts = P.default_opts(inner_iters=5, inner_solver=1)
+    n = f.layout()["field_elems"]
+    bt, b = _rand_field(n, 17)
+    x = f.inner_solve(bt, opts, adjoint=adjoint).cpu().numpy()
+    bs, xs = _split(wls, probs, b), _split(wls, probs, x)
+    for i, (w, p) in enumerate(zip(wls, probs)):
+        Nz, Nx = G.padded_shape(w.grid)
+        for blk in range(p.n_blocks):
+            A = p.operator(w.gamma_start.ravel(), p.block_freq(blk))
+            F = ILU0(A, Nz, Nx)
+            if adjoint:
+                ref = np.conj(krylov.bicgstab(lambda v: A @ v, np.conj(bs[i][blk]), F.solve, iters=5, tol=0.0)[0])
+            else:
+                ref = krylov.bicgstab(lambda v: A @ v, bs[i][blk], F.solve, iters=5, tol=0.0)[0]
+            assert _rel(xs[i][blk], ref) < 1e-8, (i, blk, _rel(xs[i][blk], ref))
+
+
+def test_preconditioner_with_ilu0_blocks(setup, forward_done):
+    """The paper's inexact preconditioner with A~ = ILU(0) (inner_solver 2: one
+    factorised application per block, no Krylov iteration), complex128,
+    against the oracle's eq. precond_approx with the same A~."""
+    from oracle.ilu import ILU0
+    P, f, wls, probs, d_obs = setup
+    eps = 1e-2
+    opts = P.default_opts(eps=eps, inner_solver=2)
+    Ks = _oracle_kkts(wls, probs, d_obs, eps, True)
+    rng = np.random.default_rng(18)
+    parts = [(rng.standard_normal((K.B, K.N)) + 1j * rng.standard_normal((K.B, K.N)), rng.standard_normal(K.Nc),
+              rng.standard_normal((K.B, K.N)) + 1j * rng.standard_normal((K.B, K.N))) for K in Ks]
+    z = f.apply_precond(torch.from_numpy(_pack_gpu(Ks, parts)).cuda(), opts).cpu().numpy()
+    got = _unpack_gpu(Ks, z)
+    for K, w, p, pr, g in zip(Ks, wls, probs, parts, got):
+        Nz, Nx = G.padded_shape(w.grid)
+        Fs = {fi: ILU0(K.A[fi], Nz, Nx) for fi in range(w.survey.n_freq)}
+
+        def inner(b, rhs, adj):
+            F = Fs[p.block_freq(b)]
+            return F.solve_adjoint(rhs) if adj else F.solve(rhs)
+        ref = K.unpack(K.precond(K.pack(*pr), inner))
+        for a, r in zip(g, ref):
+            assert _rel(a, r) < 1e-9, _rel(a, r)
