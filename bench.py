@@ -118,10 +118,13 @@ def _peaks():
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the level-0 smoother launches
-# per byte of its fused pass (b and the result, plus x unless it starts from
-# zero), from the ncu capture summarised under profiles/ (None while the
-# kernel has changed since the last capture).
-TRAFFIC_PER_FUSED_BYTE = None
+# per byte of the pass itself (b and the result, plus x unless it starts from
+# zero, plus r, v and the old p when it forms the p update), from the ncu
+# capture of its three variants summarised under profiles/, weighted as the
+# timed forward solves launch them (per BiCGStab iteration: one with the p
+# update, one from zero, two from x): (364.3 + 115.5 + 2 x 206.8) MB over
+# (383.2 + 153.3 + 2 x 229.9) MB.  None once the kernel changes.
+TRAFFIC_PER_FUSED_BYTE = (364.3 + 115.5 + 2 * 206.8) / (383.2 + 153.3 + 2 * 229.9)
 
 
 def _roofline(ms, nbytes, n, peaks, fused_bytes=None):
