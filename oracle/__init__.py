@@ -21,6 +21,8 @@ kkt        scaled KKT matvec / RHS, exact and inexact preconditioners, direct
            matrix-free normal operator of RSGN-CG (Sec. 3)
 krylov     flexible GMRES in the real inner product, BiCGStab, CG
 mg         geometric multigrid for the shifted operator (the inner block solver)
+ilu        ILU(0) of the 5-point operator (the paper's incomplete-LU block approximation)
+lbfgs      L-BFGS inverse of the reduced Hessian for the preconditioner's H block
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, a library routine, an invariant or brute force.  The multigrid

@@ -113,11 +113,14 @@ class KKT:
         b3 = np.zeros((self.B, self.N), dtype=np.complex128)
         return self.pack(b1, b2, b3)
 
-    def precond(self, v: np.ndarray, inner=None, inner_batch=None) -> np.ndarray:
+    def precond(self, v: np.ndarray, inner=None, inner_batch=None, hblock=None) -> np.ndarray:
         """z = P^{-1} v (eq. precond) or P~^{-1} v (eq. precond_approx) when
         ``inner(b, rhs, adjoint)`` approximates A'^{-1} / A'^{-H}.
         ``inner_batch(rhs [B, N], adjoint) -> [B, N]`` may replace the loop of
-        per-block solves (the same solves, e.g. spread over processes)."""
+        per-block solves (the same solves, e.g. spread over processes).
+        ``hblock(t) -> z_s`` replaces the H-block solve t / eps by another
+        approximation of the reduced Hessian's inverse (Sec. 5 after eq.
+        precond: e.g. L-BFGS, :mod:`oracle.lbfgs`)."""
         v1, v2, v3 = self.unpack(v)
         if inner_batch is None:
             if inner is None:
@@ -127,7 +130,8 @@ class KKT:
             def inner_batch(rhs, adjoint):
                 return np.array([inner(b, rhs[b], adjoint) for b in range(self.B)])
         zl = inner_batch(v1, True)
-        zs = (v2 + sum(self.PH_apply_re(b, zl[b]) for b in range(self.B))) / self.eps
+        t = v2 + sum(self.PH_apply_re(b, zl[b]) for b in range(self.B))
+        zs = t / self.eps if hblock is None else hblock(t)
         zu = inner_batch(np.array([v3[b] + self.P_apply(b, zs) for b in range(self.B)]), False)
         return self.pack(zu, zs, zl)
 

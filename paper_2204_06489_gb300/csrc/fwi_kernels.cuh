@@ -486,7 +486,7 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
 // I = C0 + m) and across rows in two running sums, and stores a coarse row
 // every second fine row.  Fine nodes outside the grid have zero residual.
 template <typename T, bool CJ>
-__global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 4 : 2)
 k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__restrict__ xf,
                        const typename cplx<T>::t *__restrict__ bf, typename cplx<T>::t *__restrict__ bc,
                        const StripDev *__restrict__ rstrips, int n_rstrips) {
@@ -530,37 +530,25 @@ k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>:
       for (int r = jb; r < min(je + 1, nz); ++r) prefetch_l2(bf + ef0 + (long long)r * nx);
   }
   auto ldx = [&](int k) -> T2 { return (in_grid && k >= 0 && k < nz) ? xf[ef0 + (long long)k * nx] : zero; };
-  // b and the diagonal of row k (lanes with a residual), the row constants
-  auto ldb = [&](int k) -> T2 { return (mid && k < nz) ? bf[ef0 + (long long)k * nx] : zero; };
-  auto ldd = [&](int k) -> T2 {
-    return (mid && k < nz) ? cmaybe_conj(ld_keep_p(Lf.dg + eo0 + (long long)k * nx, pol), CJ) : zero;
-  };
   T2 xm = ldx(jb - 1), x0 = ldx(jb), xp = ldx(jb + 1);
-  // loaded one row ahead, so their latency overlaps the current row's arithmetic
-  T2 bcur = ldb(jb), dcur = ldd(jb);
-  T2 Zc = jb < nz ? cmaybe_conj(Zr[jb], CJ) : zero;
-  T2 iZc = jb <= nz ? cmaybe_conj(iZh[jb], CJ) : zero;
-  T2 iZd = jb + 1 <= nz ? cmaybe_conj(iZh[jb + 1], CJ) : zero;
   T2 acc0 = zero;                // running sum of the coarse row being formed
   T2 *cout = bc + bkc.off + (cown ? I : 0);
   for (int j = jb; j <= je; ++j) {
     const T2 xn = (j < je) ? ldx(j + 2) : zero;
-    const bool more = j < je;
-    const T2 bnx = more ? ldb(j + 1) : zero, dnx = more ? ldd(j + 1) : zero;
-    const T2 Znx = (more && j + 1 < nz) ? cmaybe_conj(Zr[j + 1], CJ) : zero;
-    const T2 iZnx = (more && j + 2 <= nz) ? cmaybe_conj(iZh[j + 2], CJ) : zero;
     const bool rk = mid && j < nz;
     T2 r = zero;
     {
       const T2 xe = shfl_down1(x0), xw = shfl_up1(x0);
       if (rk) {
+        const long long k = (long long)j * nx;
+        const T2 Zj = cmaybe_conj(Zr[j], CJ), iZn = cmaybe_conj(iZh[j], CJ), iZs = cmaybe_conj(iZh[j + 1], CJ);
+        const T2 d = cmaybe_conj(ld_keep_p(Lf.dg + eo0 + k, pol), CJ);
         const T2 hx = cadd(cmul(ie, xe), cmul(iw, xw));
-        const T2 hz = cadd(cmul(iZd, xp), cmul(iZc, xm));
-        const T2 ax = csub(csub(cmul(dcur, x0), cmul(Zc, hx)), cmul(Xi, hz));
-        r = csub(bcur, ax);
+        const T2 hz = cadd(cmul(iZs, xp), cmul(iZn, xm));
+        const T2 ax = csub(csub(cmul(d, x0), cmul(Zj, hx)), cmul(Xi, hz));
+        r = csub(bf[ef0 + k], ax);
       }
     }
-    bcur = bnx; dcur = dnx; Zc = Znx; iZc = iZd; iZd = iZnx;
     // horizontal weights at the centre lanes: (r[l-1] + r[l+1]) / 2 + r[l]
     const T2 re = shfl_down1(r), rw = shfl_up1(r);
     const T2 h = cadd(r, cscale(cadd(re, rw), (T)0.5));
