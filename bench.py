@@ -414,6 +414,66 @@ def run_epsrule_case(args):
     f.close()
 
 
+def run_hblock_case(args):
+    """The quasi-Newton H block (L-BFGS in place of L = eps I; Sec. 5 after eq.
+    precond, Sec. 7) against the paper's block along the benchmark's 5-step
+    trajectory.  After each step the pair (ds~_k, H~(s_{k+1}) ds~_k) is formed
+    with the library's Hessian product at the new model (one forward and one
+    adjoint refined solve per block, timed as pair_s); the newest 5 pairs are
+    kept.  At the headline eps (inner iterations --inner-iters, default 6) and,
+    with --eps, at another eps (e.g. the epsrule case's eps_rule, with the inner
+    iterations that case picked).  One JSON line."""
+    import numpy as np
+    import torch
+    import paper_2204_06489_gb300 as P
+    P.load(build_if_missing=True)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    wl = _workload()
+    eps = args.eps or EPS
+    opts = P.default_opts(eps=eps, inner_iters=args.inner_iters or 6, max_outer=args.max_outer,
+                          include_Ls_n=INCLUDE_LS_N)
+    f = _setup_ctx(P, [wl], opts, stream)
+    gref = float(np.mean(wl.gamma_true))
+    out = {"case": "hblock", "eps": eps, "inner_iters": opts.inner_iters, "pairs_kept": 5, "runs": []}
+    for hb in (0, 1):
+        o = P.Opts.from_buffer_copy(opts)
+        o.hblock = hb
+        f.set_model(0, wl.gamma_start)
+        f.hblock_set()
+        S, Y, rows = [], [], []
+        prev = None
+        for k in range(NEWTON_STEPS):
+            pair_s = 0.0
+            if hb and prev is not None:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                f.forward(o, want_data=False)
+                y, _ = f.hessian_apply(prev, o)
+                torch.cuda.synchronize()
+                pair_s = time.perf_counter() - t0
+                if float(prev @ y) > 0.0:
+                    S.append(prev); Y.append(y)
+                    S, Y = S[-5:], Y[-5:]
+                    f.hblock_set(np.array(S), np.array(Y))
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ds, st = f.newton_step(o, allow_noconv=True)
+            torch.cuda.synchronize()
+            rows.append({"newton_step": k + 1, "pairs": len(S), "outer_iters": st["outer_iters"],
+                         "kkt_ms": round(st["t_solve_ms"], 1), "step_s": round(time.perf_counter() - t1, 3),
+                         "pair_s": round(pair_s, 3), "rel_res": st["rel_res"],
+                         "converged": st["rel_res"] <= o.tol, "misfit": st["misfit"]})
+            prev = np.asarray(ds, dtype=np.float64).ravel() / gref
+        out["runs"].append({"hblock": "L-BFGS" if hb else "eps I", "steps": rows,
+                            "total_s": round(sum(r["step_s"] + r["pair_s"] for r in rows), 3),
+                            "outer_total": sum(r["outer_iters"] for r in rows)})
+        print(json.dumps(out["runs"][-1]), file=sys.stderr, flush=True)
+    f.hblock_set()
+    print(json.dumps(out))
+    f.close()
+
+
 def _workload():
     import fwi_inputs as FI
     return FI.marmousi_shaped_workload()
@@ -764,7 +824,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="profiling cases: direct launches, no graph replay")
     ap.add_argument("--case", default="newton",
                     choices=["newton", "inner", "batch3a", "batch3b", "large", "autograd", "rsgn", "tradeoff",
-                             "epsrule", "kkt"])
+                             "epsrule", "kkt", "hblock"])
     ap.add_argument("--max-outer", type=int, default=60)
     ap.add_argument("--fd-dirs", type=int, default=4)
     ap.add_argument("--inner-iters", type=int, default=None)
@@ -782,6 +842,8 @@ def main():
         return run_epsrule_case(args)
     if args.case == "kkt":
         return run_kkt_case(args)
+    if args.case == "hblock":
+        return run_hblock_case(args)
     if args.case != "newton":
         return run_extra_case(args)
     return run_newton(args)

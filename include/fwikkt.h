@@ -56,6 +56,7 @@ extern "C" {
 #define FWI_DOT_RUNS 0
 #define FWI_DOT_FP64 1
 #define FWI_DOT_COMP 2
+#define FWI_HBLOCK_MAX 8   /* pairs of the quasi-Newton H block */
 
 /* ---- precision modes ---------------------------------------------------- */
 #define FWI_C128 0        /* complex128 throughout ("plain FP64 GPU form")       */
@@ -118,6 +119,9 @@ typedef struct {
                              2 one ILU(0) application as A~ (the paper's incomplete-LU
                              approximation, zero fill); forward/adjoint modelling always
                              uses 0 (fwi_inner_solve: 1 and 2 mean BiCGStab + ILU(0)) [0] */
+  int hblock;             /* H block of the preconditioner (Sec. 5 after eq. precond):
+                             0 the paper's L = eps I; 1 the L-BFGS inverse built from the
+                             pairs of fwi_hblock_set with H_0 = (1/eps) I (no pairs: as 0) [0] */
 } fwi_opts;
 
 typedef struct {
@@ -244,6 +248,32 @@ int fwi_rsgn_step(fwi_ctx *ctx, const fwi_opts *opts, double *ds, int on_device,
  * FWI_E_NOCONV if a block solve missed fwd_tol (lambda still written). */
 int fwi_normal_lambda_max(fwi_ctx *ctx, const fwi_opts *opts, int iters, double *lambda,
                           fwi_stats *stats);
+
+/* Hessian-vector product of the reduced Gauss-Newton system at the current
+ * models (Sec. 3, eq. normal_system_discrete_sum) in the scaled control of
+ * fwi_kkt_solve (ds~ = ds / gamma_ref of each instance):
+ *   hv = eps v + Re(J~^H W^T W J~) v,  eps = opts->eps (0: the Gauss-Newton part),
+ * one forward and one adjoint refined block solve of every block
+ * (opts->fwd_tol, opts->precision).  v, hv: ctrl_elems doubles, host
+ * (on_device = 0) or device buffers.  Needs fwi_forward.  FWI_E_NOCONV if a
+ * block solve missed fwd_tol (hv still written).  Used to build exact
+ * curvature pairs (s, H s) for the quasi-Newton H block. */
+int fwi_hessian_apply(fwi_ctx *ctx, const fwi_opts *opts, const double *v, double *hv, int on_device,
+                      fwi_stats *stats);
+
+/* Curvature pairs of the quasi-Newton H block (opts->hblock = 1; Sec. 5
+ * after eq. precond and Sec. 7: the block-triangular preconditioner's
+ * H ~ L may be replaced by L-BFGS).  S and Y: m x ctrl_elems doubles,
+ * row-major, pair j = (S[j], Y[j]) in the scaled control, oldest first, with
+ * Y[j] = H~ S[j] or a secant difference; every pair needs S[j]^T Y[j] > 0
+ * (else FWI_E_INVAL and no pairs are kept).  0 <= m <= FWI_HBLOCK_MAX; m = 0
+ * removes the pairs.  The pairs are copied (host or device source); they
+ * belong to the control layout, so they stay valid across model updates and
+ * are used until replaced.  The preconditioner then forms
+ * z_s = B^{-1} (v2 + Re(P~^H z_lambda)), B^{-1} the L-BFGS inverse with
+ * H_0 = (1/eps) I, in the compact representation of Byrd, Nocedal & Schnabel
+ * (two kernels: 2m FP64 dot products and one update). */
+int fwi_hblock_set(fwi_ctx *ctx, int m, const double *S, const double *Y, int on_device);
 
 /* ---- operator-level entry points (device buffers, for checks and tools) ----
  * x, y: device field buffers in the given precision (float2 or double2

@@ -27,6 +27,7 @@ FWI_C64_REFINE = 1
 FWI_DOT_RUNS = 0
 FWI_DOT_FP64 = 1
 FWI_DOT_COMP = 2
+FWI_HBLOCK_MAX = 8
 
 _ERRNAMES = {FWI_E_INVAL: "FWI_E_INVAL", FWI_E_NOMEM: "FWI_E_NOMEM", FWI_E_CUDA: "FWI_E_CUDA",
              FWI_E_NOCONV: "FWI_E_NOCONV", FWI_E_NUMERIC: "FWI_E_NUMERIC"}
@@ -53,7 +54,7 @@ class Opts(C.Structure):
                 ("max_fwd_refine", C.c_int), ("use_graph", C.c_int), ("arnoldi_dots", C.c_int),
                 ("check_orth", C.c_int), ("strip_rows", C.c_int), ("coarse_threads", C.c_int),
                 ("fwd_warm", C.c_int), ("outer_solver", C.c_int),
-                ("inner_solver", C.c_int)]
+                ("inner_solver", C.c_int), ("hblock", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -113,6 +114,8 @@ def load(build_if_missing: bool = False):
         "fwi_newton_step": (C.c_int, [P, C.POINTER(Opts), P, C.c_int, C.POINTER(Stats)]),
         "fwi_rsgn_step": (C.c_int, [P, C.POINTER(Opts), P, C.c_int, C.POINTER(Stats)]),
         "fwi_normal_lambda_max": (C.c_int, [P, C.POINTER(Opts), C.c_int, DP, C.POINTER(Stats)]),
+        "fwi_hessian_apply": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int, C.POINTER(Stats)]),
+        "fwi_hblock_set": (C.c_int, [P, C.c_int, P, P, C.c_int]),
         "fwi_apply_helmholtz": (C.c_int, [P, P, P, C.c_int, C.c_int]),
         "fwi_apply_kkt": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
         "fwi_apply_precond": (C.c_int, [P, C.POINTER(Opts), P, P, C.c_int]),
@@ -322,6 +325,41 @@ class FWI:
                                            C.byref(st))
         self._check(rc)
         return lam.value, st.as_dict()
+
+    def hessian_apply(self, v, opts: Optional[Opts] = None, allow_noconv: bool = False):
+        """H~ v of the reduced Gauss-Newton system at the current models, in the
+        scaled control (ds / gamma_ref); ``v`` a numpy array (returns numpy) or
+        a CUDA float64 tensor (returns a tensor).  Needs ``forward``."""
+        st = Stats()
+        o = C.byref(opts) if opts else None
+        if isinstance(v, np.ndarray):
+            vv = np.ascontiguousarray(v, dtype=np.float64)
+            out = np.empty_like(vv)
+            rc = self._L.fwi_hessian_apply(self._h, o, vv.ctypes.data, out.ctypes.data, 0, C.byref(st))
+        else:
+            vv = v.contiguous()
+            out = vv.new_empty(vv.shape)
+            rc = self._L.fwi_hessian_apply(self._h, o, _tensor_ptr(vv), _tensor_ptr(out), 1, C.byref(st))
+        self._check(rc, allow_noconv)
+        return out, st.as_dict()
+
+    def hblock_set(self, S=None, Y=None):
+        """Curvature pairs (rows of S, Y, scaled control, oldest first) of the
+        quasi-Newton H block (opts.hblock = 1); no arguments removes them."""
+        if S is None:
+            self._check(self._L.fwi_hblock_set(self._h, 0, None, None, 0))
+            return
+        if isinstance(S, np.ndarray):
+            Sa = np.ascontiguousarray(S, dtype=np.float64)
+            Ya = np.ascontiguousarray(Y, dtype=np.float64)
+            if Sa.shape != Ya.shape or Sa.ndim != 2:
+                raise ValueError("S and Y must be [m, ctrl_elems]")
+            self._check(self._L.fwi_hblock_set(self._h, Sa.shape[0], Sa.ctypes.data, Ya.ctypes.data, 0))
+        else:
+            Sa, Ya = S.contiguous(), Y.contiguous()
+            if Sa.shape != Ya.shape or Sa.dim() != 2:
+                raise ValueError("S and Y must be [m, ctrl_elems]")
+            self._check(self._L.fwi_hblock_set(self._h, Sa.shape[0], _tensor_ptr(Sa), _tensor_ptr(Ya), 1))
 
     def kernel_profile(self, enable: int):
         """The library's kernel profile since the last reset (a dict with

@@ -486,7 +486,7 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
 // I = C0 + m) and across rows in two running sums, and stores a coarse row
 // every second fine row.  Fine nodes outside the grid have zero residual.
 template <typename T, bool CJ>
-__global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 3 : 2)
 k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__restrict__ xf,
                        const typename cplx<T>::t *__restrict__ bf, typename cplx<T>::t *__restrict__ bc,
                        const StripDev *__restrict__ rstrips, int n_rstrips) {
@@ -530,25 +530,37 @@ k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>:
       for (int r = jb; r < min(je + 1, nz); ++r) prefetch_l2(bf + ef0 + (long long)r * nx);
   }
   auto ldx = [&](int k) -> T2 { return (in_grid && k >= 0 && k < nz) ? xf[ef0 + (long long)k * nx] : zero; };
+  // b and the diagonal of row k (lanes with a residual), the row constants
+  auto ldb = [&](int k) -> T2 { return (mid && k < nz) ? bf[ef0 + (long long)k * nx] : zero; };
+  auto ldd = [&](int k) -> T2 {
+    return (mid && k < nz) ? cmaybe_conj(ld_keep_p(Lf.dg + eo0 + (long long)k * nx, pol), CJ) : zero;
+  };
   T2 xm = ldx(jb - 1), x0 = ldx(jb), xp = ldx(jb + 1);
+  // loaded one row ahead, so their latency overlaps the current row's arithmetic
+  T2 bcur = ldb(jb), dcur = ldd(jb);
+  T2 Zc = jb < nz ? cmaybe_conj(Zr[jb], CJ) : zero;
+  T2 iZc = jb <= nz ? cmaybe_conj(iZh[jb], CJ) : zero;
+  T2 iZd = jb + 1 <= nz ? cmaybe_conj(iZh[jb + 1], CJ) : zero;
   T2 acc0 = zero;                // running sum of the coarse row being formed
   T2 *cout = bc + bkc.off + (cown ? I : 0);
   for (int j = jb; j <= je; ++j) {
     const T2 xn = (j < je) ? ldx(j + 2) : zero;
+    const bool more = j < je;
+    const T2 bnx = more ? ldb(j + 1) : zero, dnx = more ? ldd(j + 1) : zero;
+    const T2 Znx = (more && j + 1 < nz) ? cmaybe_conj(Zr[j + 1], CJ) : zero;
+    const T2 iZnx = (more && j + 2 <= nz) ? cmaybe_conj(iZh[j + 2], CJ) : zero;
     const bool rk = mid && j < nz;
     T2 r = zero;
     {
       const T2 xe = shfl_down1(x0), xw = shfl_up1(x0);
       if (rk) {
-        const long long k = (long long)j * nx;
-        const T2 Zj = cmaybe_conj(Zr[j], CJ), iZn = cmaybe_conj(iZh[j], CJ), iZs = cmaybe_conj(iZh[j + 1], CJ);
-        const T2 d = cmaybe_conj(ld_keep_p(Lf.dg + eo0 + k, pol), CJ);
         const T2 hx = cadd(cmul(ie, xe), cmul(iw, xw));
-        const T2 hz = cadd(cmul(iZs, xp), cmul(iZn, xm));
-        const T2 ax = csub(csub(cmul(d, x0), cmul(Zj, hx)), cmul(Xi, hz));
-        r = csub(bf[ef0 + k], ax);
+        const T2 hz = cadd(cmul(iZd, xp), cmul(iZc, xm));
+        const T2 ax = csub(csub(cmul(dcur, x0), cmul(Zc, hx)), cmul(Xi, hz));
+        r = csub(bcur, ax);
       }
     }
+    bcur = bnx; dcur = dnx; Zc = Znx; iZc = iZd; iZd = iZnx;
     // horizontal weights at the centre lanes: (r[l-1] + r[l+1]) / 2 + r[l]
     const T2 re = shfl_down1(r), rw = shfl_up1(r);
     const T2 h = cadd(r, cscale(cadd(re, rw), (T)0.5));
@@ -2171,6 +2183,85 @@ k_blk_scale(LevelView<T> L, const TI *x, const double *f, TO *y, int accumulate)
     double v = (double)x[base + i] * fv;
     if (accumulate) y[base + i] = (TO)((double)y[base + i] + v);
     else y[base + i] = (TO)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Quasi-Newton H block of the preconditioner (Sec. 5 after eq. precond: the
+// block-triangular preconditioner approximates the reduced Hessian by L; an
+// L-BFGS approximation may take its place).  With m stored pairs (s_j, y_j)
+// and H_0 = (1/eps) I the inverse approximation is applied in the compact form
+// of Byrd, Nocedal & Schnabel (1994, Thm 2.2):
+//   B^{-1} t = H_0 t + [S  H_0 Y] M [S^T t; Y^T H_0 t],
+// M = [[R^-T (D + Y^T H_0 Y) R^-1, -R^-T], [-R^-1, 0]], R the upper triangle of
+// S^T Y and D its diagonal.  The preconditioner has already formed
+// q = t / eps = H_0 t in the control slot, so q <- q + sum_k c_k w_k with
+// w = (s_0 .. s_{m-1}, y_0 .. y_{m-1}) and c = Mf [S^T q; Y^T q], where the
+// host folds the eps scalings into the 2m x 2m matrix Mf.  Two launches: the
+// 2m dot products (FP64 products and sums, per-CTA partials in a fixed order)
+// and the update (every CTA reduces the partials itself, forms c, updates its
+// share of q).
+#define QN_MAX 8
+
+template <typename T>
+__global__ void __launch_bounds__(FLAT_THREADS)
+k_qn_dots(long long n, const T *__restrict__ q, const double *__restrict__ S, const double *__restrict__ Y, int m,
+          double *__restrict__ part) {
+  double acc[2 * QN_MAX];
+#pragma unroll
+  for (int k = 0; k < 2 * QN_MAX; ++k) acc[k] = 0.0;
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
+    const double qi = (double)q[i];
+#pragma unroll
+    for (int j = 0; j < QN_MAX; ++j)
+      if (j < m) {
+        acc[j] = fma(qi, S[(long long)j * n + i], acc[j]);
+        acc[QN_MAX + j] = fma(qi, Y[(long long)j * n + i], acc[QN_MAX + j]);
+      }
+  }
+  __shared__ double red[FLAT_THREADS / 32][2 * QN_MAX];
+#pragma unroll
+  for (int k = 0; k < 2 * QN_MAX; ++k) {
+    double a = acc[k];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * QN_MAX) {
+    double t = 0.0;
+    for (int w = 0; w < FLAT_THREADS / 32; ++w) t += red[w][threadIdx.x];
+    part[(long long)blockIdx.x * 2 * QN_MAX + threadIdx.x] = t;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FLAT_THREADS)
+k_qn_apply(long long n, T *__restrict__ q, const double *__restrict__ S, const double *__restrict__ Y, int m,
+           const double *__restrict__ part, int nparts, const double *__restrict__ Mf) {
+  __shared__ double dots[2 * QN_MAX], coef[2 * QN_MAX];
+  if (threadIdx.x < 2 * m) {
+    // compact index k: k < m -> s_k, else y_{k-m}
+    const int slot = threadIdx.x < m ? threadIdx.x : QN_MAX + threadIdx.x - m;
+    double t = 0.0;
+    for (int p = 0; p < nparts; ++p) t += part[(long long)p * 2 * QN_MAX + slot];
+    dots[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * m) {
+    double c = 0.0;
+    for (int k = 0; k < 2 * m; ++k) c = fma(Mf[threadIdx.x * 2 * m + k], dots[k], c);
+    coef[threadIdx.x] = c;
+  }
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
+    double v = (double)q[i];
+#pragma unroll
+    for (int j = 0; j < QN_MAX; ++j)
+      if (j < m) {
+        v = fma(coef[j], S[(long long)j * n + i], v);
+        v = fma(coef[m + j], Y[(long long)j * n + i], v);
+      }
+    q[i] = (T)v;
   }
 }
 

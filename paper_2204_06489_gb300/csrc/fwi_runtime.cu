@@ -319,6 +319,13 @@ struct Ctx {
   int u_version32 = -1, u_version64 = -1;
   Work<float> w32;
   Work<double> w64;
+  // quasi-Newton H block of the preconditioner (opts.hblock = 1): m pairs of
+  // the scaled control, S and Y as [m][Nc]; the folded 2m x 2m matrix of the
+  // compact form for the eps in qn_eps
+  int qn_m = 0, qn_version = 0;
+  double qn_eps = 0.0;
+  DBuf<double> qnS, qnY, qnMf, qnPart;
+  std::vector<double> qn_SY, qn_YY;
   double *pin = nullptr;  // pinned scalars
   int *pinflag = nullptr;
   // live timing of the level-0 stencil kernel (k_field_op): event pairs around
@@ -384,6 +391,12 @@ struct Ctx {
   int rsgn_solve(const fwi_opts &o, fwi_stats *stats);
   int normal_lambda_max(const fwi_opts &o, int iters, double *lambda, fwi_stats *stats);
   int rsgn_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats);
+  int hessian_apply(const fwi_opts &o, const double *v, double *hv, int on_device, fwi_stats *stats);
+  void hblock_set(int m, const double *S, const double *Y, int on_device);
+  void hblock_prepare(const fwi_opts &o);
+  template <typename T> void hblock_apply(T *zs, const fwi_opts &o);
+  int qn_grid() const { return (int)std::max(1LL, std::min((long long)FLAT_BLOCKS, (Nc + FLAT_THREADS - 1) / FLAT_THREADS)); }
+  int hb_key(const fwi_opts &o) const { return (o.hblock && qn_m > 0) ? qn_version : 0; }
   void apply_update(double *ds, int on_device);
   void write_ctrl(const double *src_ctrl_dev, double *dst, int on_device, const double *fac);
   template <typename T> void mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
@@ -1406,6 +1419,109 @@ void Ctx::kkt_matvec(const T *xi, T *y, double eps, const typename cplx<T>::t *u
   KCHECK();
 }
 
+static_assert(QN_MAX == FWI_HBLOCK_MAX, "pair capacity of the H-block kernels");
+
+// Quasi-Newton H block (Sec. 5 after eq. precond; Sec. 7): m pairs (s_j, y_j)
+// of the scaled control, oldest first, with s_j^T y_j > 0.  The pairs are
+// copied; their Gram matrices S^T Y and Y^T Y are formed once here (FP64).
+void Ctx::hblock_set(int m, const double *S, const double *Y, int on_device) {
+  if (m < 0 || m > QN_MAX) fail(FWI_E_INVAL, "hblock: m must be in 0 .. FWI_HBLOCK_MAX");
+  if (!layout_ok || Nc <= 0) fail(FWI_E_INVAL, "hblock: set the surveys first (the control size is not known)");
+  ++qn_version;
+  qn_eps = 0.0;
+  if (m == 0) { qn_m = 0; return; }
+  if (!S || !Y) fail(FWI_E_INVAL, "hblock: null pair buffer");
+  const size_t n = (size_t)m * Nc;
+  qnS.alloc(n); qnY.alloc(n);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(qnS.p, S, n * sizeof(double), kind, st));
+  CK(cudaMemcpyAsync(qnY.p, Y, n * sizeof(double), kind, st));
+  const int g = qn_grid();
+  qnPart.alloc((size_t)FLAT_BLOCKS * 2 * QN_MAX);
+  qn_SY.assign((size_t)m * m, 0.0);
+  qn_YY.assign((size_t)m * m, 0.0);
+  std::vector<double> hp((size_t)g * 2 * QN_MAX);
+  for (int k = 0; k < m; ++k) {
+    // column k: s_j^T y_k and y_j^T y_k for every j
+    KPROF("k_qn_dots", -1, 8.0 * (2 * m + 1) * Nc, st);
+    k_qn_dots<double><<<g, FLAT_THREADS, 0, st>>>(Nc, qnY.p + (size_t)k * Nc, qnS.p, qnY.p, m, qnPart.p);
+    KCHECK();
+    CK(cudaMemcpyAsync(hp.data(), qnPart.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    for (int j = 0; j < m; ++j) {
+      double a = 0.0, b = 0.0;
+      for (int p = 0; p < g; ++p) { a += hp[(size_t)p * 2 * QN_MAX + j]; b += hp[(size_t)p * 2 * QN_MAX + QN_MAX + j]; }
+      qn_SY[(size_t)j * m + k] = a;
+      qn_YY[(size_t)j * m + k] = b;
+    }
+  }
+  for (int j = 0; j < m; ++j) {
+    const double c = qn_SY[(size_t)j * m + j];
+    if (!(c > 0.0) || !std::isfinite(c)) {
+      qn_m = 0;
+      fail(FWI_E_INVAL, "hblock: pair " + std::to_string(j) + " has no positive curvature (s^T y <= 0)");
+    }
+  }
+  qn_m = m;
+}
+
+// Fold the compact form for this eps: with q = t / eps (what the
+// preconditioner has formed), B^{-1} t = q + S c_S + Y c_Y, c = Mf [S^T q; Y^T q],
+//   Mf = [[eps R^-T (D + Y^T Y / eps) R^-1, -R^-T], [-R^-1, 0]].
+void Ctx::hblock_prepare(const fwi_opts &o) {
+  if (!o.hblock || qn_m == 0 || qn_eps == o.eps) return;
+  const int m = qn_m;
+  const double eps = o.eps, gam = 1.0 / o.eps;
+  // Ri = R^{-1}, R the upper triangle of S^T Y (back substitution, column by column)
+  std::vector<double> Ri((size_t)m * m, 0.0);
+  auto R = [&](int i, int j) { return qn_SY[(size_t)i * m + j]; };
+  for (int c = 0; c < m; ++c)
+    for (int i = c; i >= 0; --i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= c; ++k) v -= R(i, k) * Ri[(size_t)k * m + c];
+      Ri[(size_t)i * m + c] = v / R(i, i);
+    }
+  // C1 = Ri^T (D + gam YY) Ri
+  std::vector<double> Mid((size_t)m * m), T1((size_t)m * m, 0.0), C1((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) Mid[(size_t)i * m + j] = gam * qn_YY[(size_t)i * m + j] + (i == j ? R(i, i) : 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < m; ++k) v += Mid[(size_t)i * m + k] * Ri[(size_t)k * m + j];
+      T1[(size_t)i * m + j] = v;
+    }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < m; ++k) v += Ri[(size_t)k * m + i] * T1[(size_t)k * m + j];
+      C1[(size_t)i * m + j] = v;
+    }
+  std::vector<double> Mf((size_t)4 * m * m, 0.0);
+  const int w = 2 * m;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      Mf[(size_t)i * w + j] = eps * C1[(size_t)i * m + j];
+      Mf[(size_t)i * w + m + j] = -Ri[(size_t)j * m + i];       // -R^{-T}
+      Mf[(size_t)(m + i) * w + j] = -Ri[(size_t)i * m + j];     // -R^{-1}
+    }
+  qnMf.upload(Mf, st);
+  sync();
+  qn_eps = o.eps;
+}
+
+template <typename T> void Ctx::hblock_apply(T *zs, const fwi_opts &o) {
+  if (!o.hblock || qn_m == 0) return;
+  if (qn_eps != o.eps) fail(FWI_E_CUDA, "internal: H block not prepared for this eps");
+  const int g = qn_grid();
+  KPROF("k_qn_dots", 0, (double)sizeof(T) * Nc + 16.0 * qn_m * Nc, st);
+  k_qn_dots<T><<<g, FLAT_THREADS, 0, st>>>(Nc, zs, qnS.p, qnY.p, qn_m, qnPart.p);
+  KCHECK();
+  KPROF("k_qn_apply", 0, 2.0 * sizeof(T) * Nc + 16.0 * qn_m * Nc, st);
+  k_qn_apply<T><<<g, FLAT_THREADS, 0, st>>>(Nc, zs, qnS.p, qnY.p, qn_m, qnPart.p, g, qnMf.p);
+  KCHECK();
+}
+
 template <typename T>
 void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count, const typename cplx<T>::t *u) {
   typedef typename cplx<T>::t T2;
@@ -1429,6 +1545,8 @@ void Ctx::precond(const T *v, T *z, const fwi_opts &o, long long *count, const t
   KPROF("k_coupling_reduce", 1, 2.0 * sizeof(typename cplx<T>::t) * cpl_nodes() + 2.0 * sizeof(T) * Nc, st);
   k_coupling_reduce<T, T><<<g, dim3(128, CPL_ROWS), 0, st>>>(d_inst.p, d_blk_off.p, cfK.p, u, zl, v2, o.eps, 1, zs);
   KCHECK();
+  // quasi-Newton H block: z_s = B^{-1} (v2 + Re(P~^H z_lambda)) instead of ( ) / eps
+  hblock_apply<T>(zs, o);
   // z_u = A'^{-1} (v3 + P~ z_s)
   LevelView<T> L = viewA<T>();
   KPROF("k_coupling_scatter", 0, 3.0 * sizeof(typename cplx<T>::t) * F0, st);
@@ -1446,8 +1564,9 @@ void Ctx::precond_any(const T *v, T *z, const fwi_opts &o, long long *count, con
   bool graphable = o.use_graph && !(o.inner_tol > 0.0);
   if (!graphable) { precond<T>(v, z, o, count, u); return; }
   char key[256];
-  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d", hier_key.c_str(), o.inner_iters, o.mg_cycle,
-           o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta, (const void *)u, o.coarse_threads * 10 + o.inner_solver);
+  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d|%d", hier_key.c_str(), o.inner_iters, o.mg_cycle,
+           o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, o.eps, o.shift_beta, (const void *)u, o.coarse_threads * 10 + o.inner_solver,
+           hb_key(o));
   if (w.graph_key != key) {
     if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
     cudaGraph_t gr;
@@ -1528,9 +1647,9 @@ template <typename T>
 void Ctx::fgmres_cycle_graph(const fwi_opts &o, double eps, T *x, const typename cplx<T>::t *u) {
   Work<T> &w = work<T>();
   char key[320];
-  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d|%d|%p|%d", hier_key.c_str(), o.inner_iters,
+  snprintf(key, sizeof key, "%s|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%p|%d|%d|%p|%d|%d", hier_key.c_str(), o.inner_iters,
            o.mg_cycle, o.mg_wdepth, o.nu1, o.nu2, o.omega_jac, eps, o.shift_beta, (const void *)u, w.m,
-           o.arnoldi_dots, (void *)x, o.coarse_threads * 10 + o.inner_solver);
+           o.arnoldi_dots, (void *)x, o.coarse_threads * 10 + o.inner_solver, hb_key(o));
   if (w.cyc && w.cyc_key == key) return;
   if (w.cyc) { cudaGraphExecDestroy(w.cyc); w.cyc = nullptr; }
   const long long n = nkkt;
@@ -2068,6 +2187,7 @@ int Ctx::kkt_solve(const fwi_opts &o, fwi_stats *stats) {
   CK(cudaMemcpyAsync(rho_k64.p, b64.p, nkkt * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const bool c128 = o.precision == FWI_C128;
   if (o.inner_solver >= 1) ensure_ilu();     // before any graph capture
+  hblock_prepare(o);
   if (o.outer_solver == 1) {
     // the outer BiCGStab allocates its eight vectors itself (no Krylov basis)
     if (c128) ensure_work<double>(o); else ensure_work<float>(o);
@@ -2409,6 +2529,27 @@ int Ctx::normal_lambda_max(const fwi_opts &o, int iters, double *lambda, fwi_sta
   return N.solve_rc;
 }
 
+// H~ v = eps v + Re(P~^H A'^{-H} F A'^{-1} P~ v) (Sec. 3, eq.
+// normal_system_discrete_sum, scaled control): one forward and one adjoint
+// refined solve of every block.
+int Ctx::hessian_apply(const fwi_opts &o, const double *v, double *hv, int on_device, fwi_stats *stats) {
+  if (!have_fwd) fail(FWI_E_INVAL, "fwi_hessian_apply needs fwi_forward at the current model");
+  if (!(o.eps >= 0.0)) fail(FWI_E_INVAL, "eps must be >= 0");
+  NormalOp N(*this, o, stats);
+  DBuf<double> dv, dh;
+  const double *vin = v;
+  double *out = hv;
+  if (!on_device) {
+    dv.alloc(Nc); dh.alloc(Nc);
+    CK(cudaMemcpyAsync(dv.p, v, Nc * sizeof(double), cudaMemcpyHostToDevice, st));
+    vin = dv.p; out = dh.p;
+  }
+  N.apply(vin, o.eps, out);
+  if (!on_device) CK(cudaMemcpyAsync(hv, dh.p, Nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+  sync();
+  return N.solve_rc;
+}
+
 int Ctx::rsgn_step(const fwi_opts &o, double *ds, int on_device, fwi_stats *stats) {
   auto t0 = std::chrono::steady_clock::now();
   build_hierarchy(o);
@@ -2455,7 +2596,7 @@ static int check_opts(const fwi_opts *o) {
       (o->precision != FWI_C128 && o->precision != FWI_C64_REFINE) || o->mg_wdepth > MAX_LEVELS ||
       o->arnoldi_dots < FWI_DOT_RUNS || o->arnoldi_dots > FWI_DOT_COMP || o->strip_rows < 2 ||
       o->strip_rows > 64 || (o->coarse_threads != 512 && o->coarse_threads != 1024) || o->outer_solver < 0 ||
-      o->outer_solver > 1 || o->inner_solver < 0 || o->inner_solver > 2)
+      o->outer_solver > 1 || o->inner_solver < 0 || o->inner_solver > 2 || o->hblock < 0 || o->hblock > 1)
     return 0;
   return 1;
 }
@@ -2491,6 +2632,7 @@ void fwi_default_opts(fwi_opts *o) {
   o->fwd_warm = 1;
   o->outer_solver = 0;
   o->inner_solver = 0;
+  o->hblock = 0;
   o->coarse_threads = 512;
   o->check_orth = 0;
 }
@@ -2763,6 +2905,29 @@ int fwi_normal_lambda_max(fwi_ctx *ctx, const fwi_opts *opts, int iters, double 
   API_END(ctx)
 }
 
+int fwi_hessian_apply(fwi_ctx *ctx, const fwi_opts *opts, const double *v, double *hv, int on_device,
+                      fwi_stats *stats) {
+  API_BEGIN(ctx)
+  Ctx &c = ctx->c;
+  fwi_opts o;
+  fwi_default_opts(&o);
+  if (opts) o = *opts;
+  if (!check_opts(&o) || !v || !hv) fwi::fail(FWI_E_INVAL, "invalid arguments");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  c.build_hierarchy(o);
+  int rc = c.hessian_apply(o, v, hv, on_device, stats);
+  if (rc != FWI_OK) c.err = "a block solve of the Hessian product missed fwd_tol";
+  return rc;
+  API_END(ctx)
+}
+
+int fwi_hblock_set(fwi_ctx *ctx, int m, const double *S, const double *Y, int on_device) {
+  API_BEGIN(ctx)
+  ctx->c.hblock_set(m, S, Y, on_device);
+  return FWI_OK;
+  API_END(ctx)
+}
+
 int fwi_apply_helmholtz(fwi_ctx *ctx, const void *x, void *y, int adjoint, int precision) {
   API_BEGIN(ctx)
   Ctx &c = ctx->c;
@@ -2809,6 +2974,7 @@ int fwi_apply_precond(fwi_ctx *ctx, const fwi_opts *opts, const void *v, void *z
   if (!c.have_fwd) fwi::fail(FWI_E_INVAL, "fwi_apply_precond needs fwi_forward");
   c.build_hierarchy(o);
   if (o.inner_solver >= 1) c.ensure_ilu();
+  c.hblock_prepare(o);
   long long cnt = 0;
   if (precision == FWI_C128) {
     c.ensure_work<double>(o);
