@@ -642,8 +642,10 @@ def run_newton(args):
         f.set_model(0, wl.gamma_start)
         f.forward(opts, want_data=False)
         opts, table = tune_kkt(f, opts, (4, 6, 8, 12, 16), (1, 2), (30,))
-        # second stage at the chosen schedule: strip height x coarse-cycle CTA size
-        opts, table2 = tune_kkt(f, opts, (opts.inner_iters,), (None,), (None,), (8, 16, 32), (512, 1024))
+        # second stage at the chosen schedule: strip height x coarse-cycle CTA size, scored by
+        # time per FGMRES iteration (the layout changes no arithmetic)
+        opts, table2 = tune_kkt(f, opts, (opts.inner_iters,), (None,), (None,), (8, 16, 32), (512, 1024),
+                                per_iteration=True)
         tuned = [{"inner_iters": n, "wdepth": wd, "restart": rs, "strip_rows": sr, "coarse_threads": ct,
                   "s": round(t, 3), "outer": o, "ok": ok} for n, wd, rs, t, o, ok, sr, ct in table + table2]
     g0 = torch.from_numpy(wl.gamma_start).cuda()

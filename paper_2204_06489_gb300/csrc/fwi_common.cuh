@@ -21,8 +21,10 @@
 #define MAX_LEVELS 12
 #define MARCH_COLS 30
 #define MARCH2_COLS 60     // output columns per strip of the two-sweep smoother (two per lane)
-#define RM_COLS 14          // coarse columns per strip of the residual-restriction kernel
+#define RM_COLS 30          // coarse columns per strip of the residual-restriction kernel (two fine columns per lane)
 #define RM_ROWS 8           // coarse rows per strip
+#define PM_COLS 31          // coarse columns per strip of the prolongation kernel (plus one halo lane)
+#define PM_ROWS 4           // coarse rows per strip of the prolongation kernel
 #define MARCH_THREADS 256
 
 namespace fwi {

@@ -478,12 +478,15 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
 
 // Residual + restriction by column strips (R = P^T, 4x full weighting):
 //   bc[J][I] = sum_{a,b in -1..1} w_a w_b (bf - Op xf)[2J+1+b][2I+1+a],  w = (1/2, 1, 1/2).
-// A warp owns coarse columns C0 .. C0 + RM_COLS - 1 and coarse rows J0 .. J1 - 1
-// of one block (a StripDev in coarse coordinates).  Lane l holds fine column
-// 2 C0 - 1 + l; the warp walks the fine rows 2 J0 .. 2 J1 keeping three rows of
-// x in registers, forms the residual on lanes 1 .. 30, combines it across
-// columns with shuffles (lane 2m + 2 is the fine column 2I + 1 of coarse column
-// I = C0 + m) and across rows in two running sums, and stores a coarse row
+// A warp owns coarse columns C0 .. C0 + RM_COLS - 1 (RM_COLS = 30) and coarse
+// rows J0 .. J1 - 1 of one block (a StripDev in coarse coordinates).  Lane l
+// holds two fine columns, cA = 2 C0 - 1 + 2 l (odd) and cB = cA + 1 (even),
+// and owns coarse column I = C0 + l, whose centre 2I + 1 is the cA of lane
+// l + 1.  The warp walks the fine rows 2 J0 .. 2 J1 keeping three rows of x in
+// registers; per row it forms the residual at cA (lanes 1 .. 30) and cB
+// (lanes 0 .. 30), taking the neighbours across lanes with two shuffles; lane
+// l + 1 sends r(cA) + r(cB)/2 to lane l (one shuffle), which adds its own
+// r(cB)/2; the rows combine in two running sums and a coarse row is stored
 // every second fine row.  Fine nodes outside the grid have zero residual.
 template <typename T, bool CJ>
 __global__ void __launch_bounds__(MARCH_THREADS, sizeof(T) == 4 ? 3 : 2)
@@ -501,69 +504,78 @@ k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>:
   const OpDev opc = Lc.ops[bkc.op];
   const int nx = op.nx, nz = op.nz;
   const int lane = threadIdx.x & 31;
-  const int i = 2 * s.col0 - 1 + lane;
-  const bool in_grid = i >= 0 && i < nx;
-  const bool mid = lane >= 1 && lane <= 30 && in_grid;
-  const int m = (lane - 2) >> 1;                      // coarse column of an even lane 2 .. 2 RM_COLS
-  const int I = s.col0 + m;
-  const bool cown = lane >= 2 && !(lane & 1) && m < RM_COLS && I < opc.nx;
+  const int iA = 2 * s.col0 - 1 + 2 * lane, iB = iA + 1;
+  const bool gA = iA >= 0 && iA < nx;                 // x of cA (every lane: neighbours of cB)
+  const bool gB = lane <= 30 && iB < nx;              // x of cB
+  const bool rA = gA && lane >= 1 && lane <= 30;      // residual at cA
+  const bool rB = gB;                                 // residual at cB
+  const int I = s.col0 + lane;
+  const bool cown = lane < RM_COLS && I < opc.nx;
   const unsigned long long pol = keep_policy();
   const T2 zero = mk<T2>(0, 0);
   const T2 *X = Lf.st + op.st;
   const T2 *iXh = X + nx;
   const T2 *Zr = iXh + nx + 1;
   const T2 *iZh = Zr + nz;
-  T2 Xi = zero, iw = zero, ie = zero;
-  if (mid) {
-    Xi = cmaybe_conj(X[i], CJ);
-    iw = cmaybe_conj(iXh[i], CJ);
-    ie = cmaybe_conj(iXh[i + 1], CJ);
-  }
-  const int ic = in_grid ? i : 0;
-  const long long ef0 = bkf.off + ic;
-  const long long eo0 = op.dg + ic;
+  // column constants: X at cA, cB; the half-node factors west of cA, between
+  // cA and cB, east of cB
+  T2 XA = zero, XB = zero, iw = zero, im = zero, ie = zero;
+  if (rA) { XA = cmaybe_conj(X[iA], CJ); iw = cmaybe_conj(iXh[iA], CJ); }
+  if (rB) { XB = cmaybe_conj(X[iB], CJ); ie = cmaybe_conj(iXh[iB + 1], CJ); }
+  if (rA || rB) im = cmaybe_conj(iXh[iB], CJ);
+  // column bases of cA (cB = cA + 1); only dereferenced where the column is in the grid
+  const long long cA = (long long)iA;
+  const T2 *px = xf + bkf.off + cA;
+  const T2 *pb = bf + bkf.off + cA;
+  const T2 *pd = Lf.dg + op.dg + cA;
   const int jb = 2 * s.row0, je = 2 * s.row1;       // fine rows with residual: jb .. je
   {
-    if (in_grid)
-      for (int r = max(jb - 1, 0); r < min(je + 2, nz); ++r) prefetch_l2(xf + ef0 + (long long)r * nx);
-    if (mid)
-      for (int r = jb; r < min(je + 1, nz); ++r) prefetch_l2(bf + ef0 + (long long)r * nx);
+    if (gA)
+      for (int r = max(jb - 1, 0); r < min(je + 2, nz); ++r) prefetch_l2(px + (long long)r * nx);
+    if (rA || rB)
+      for (int r = jb; r < min(je + 1, nz); ++r) prefetch_l2(pb + (rA ? 0 : 1) + (long long)r * nx);
   }
-  auto ldx = [&](int k) -> T2 { return (in_grid && k >= 0 && k < nz) ? xf[ef0 + (long long)k * nx] : zero; };
-  // b and the diagonal of row k (lanes with a residual), the row constants
-  auto ldb = [&](int k) -> T2 { return (mid && k < nz) ? bf[ef0 + (long long)k * nx] : zero; };
-  auto ldd = [&](int k) -> T2 {
-    return (mid && k < nz) ? cmaybe_conj(ld_keep_p(Lf.dg + eo0 + (long long)k * nx, pol), CJ) : zero;
-  };
-  T2 xm = ldx(jb - 1), x0 = ldx(jb), xp = ldx(jb + 1);
-  // loaded one row ahead, so their latency overlaps the current row's arithmetic
-  T2 bcur = ldb(jb), dcur = ldd(jb);
-  T2 Zc = jb < nz ? cmaybe_conj(Zr[jb], CJ) : zero;
-  T2 iZc = jb <= nz ? cmaybe_conj(iZh[jb], CJ) : zero;
-  T2 iZd = jb + 1 <= nz ? cmaybe_conj(iZh[jb + 1], CJ) : zero;
+  auto ldA = [&](int k) -> T2 { return (gA && k >= 0 && k < nz) ? px[(long long)k * nx] : zero; };
+  auto ldB = [&](int k) -> T2 { return (gB && k >= 0 && k < nz) ? px[(long long)k * nx + 1] : zero; };
+  // b of a row (zero where no residual is formed) is loaded one row ahead so
+  // that its latency overlaps the current row's arithmetic; the diagonal (kept
+  // in L2, shared by the blocks of a frequency) is loaded where it is used
+  auto ldbA = [&](int k) -> T2 { return (rA && k < nz) ? pb[(long long)k * nx] : zero; };
+  auto ldbB = [&](int k) -> T2 { return (rB && k < nz) ? pb[(long long)k * nx + 1] : zero; };
+  auto lddA = [&](int k) -> T2 { return (rA && k < nz) ? ld_keep_p(pd + (long long)k * nx, pol) : zero; };
+  auto lddB = [&](int k) -> T2 { return (rB && k < nz) ? ld_keep_p(pd + (long long)k * nx + 1, pol) : zero; };
+  T2 xmA = ldA(jb - 1), x0A = ldA(jb), xpA = ldA(jb + 1);
+  T2 xmB = ldB(jb - 1), x0B = ldB(jb), xpB = ldB(jb + 1);
+  T2 bA = ldbA(jb), bB = ldbB(jb);
   T2 acc0 = zero;                // running sum of the coarse row being formed
   T2 *cout = bc + bkc.off + (cown ? I : 0);
   for (int j = jb; j <= je; ++j) {
-    const T2 xn = (j < je) ? ldx(j + 2) : zero;
     const bool more = j < je;
-    const T2 bnx = more ? ldb(j + 1) : zero, dnx = more ? ldd(j + 1) : zero;
-    const T2 Znx = (more && j + 1 < nz) ? cmaybe_conj(Zr[j + 1], CJ) : zero;
-    const T2 iZnx = (more && j + 2 <= nz) ? cmaybe_conj(iZh[j + 2], CJ) : zero;
-    const bool rk = mid && j < nz;
-    T2 r = zero;
-    {
-      const T2 xe = shfl_down1(x0), xw = shfl_up1(x0);
-      if (rk) {
-        const T2 hx = cadd(cmul(ie, xe), cmul(iw, xw));
-        const T2 hz = cadd(cmul(iZd, xp), cmul(iZc, xm));
-        const T2 ax = csub(csub(cmul(dcur, x0), cmul(Zc, hx)), cmul(Xi, hz));
-        r = csub(bcur, ax);
+    const T2 xnA = more ? ldA(j + 2) : zero;
+    const T2 xnB = more ? ldB(j + 2) : zero;
+    const T2 bnA = more ? ldbA(j + 1) : zero, bnB = more ? ldbB(j + 1) : zero;
+    const T2 xE = shfl_down1(x0A);                    // cA of lane l + 1: east of cB
+    const T2 xW = shfl_up1(x0B);                      // cB of lane l - 1: west of cA
+    T2 resA = zero, resB = zero;
+    if (j < nz && (rA || rB)) {
+      const T2 Zj = cmaybe_conj(Zr[j], CJ), iZn = cmaybe_conj(iZh[j], CJ), iZs = cmaybe_conj(iZh[j + 1], CJ);
+      if (rA) {
+        const T2 dA = lddA(j);
+        const T2 hx = cadd(cmul(iw, xW), cmul(im, x0B));
+        const T2 hz = cadd(cmul(iZs, xpA), cmul(iZn, xmA));
+        resA = csub(bA, csub(csub(cmul(cmaybe_conj(dA, CJ), x0A), cmul(Zj, hx)), cmul(XA, hz)));
+      }
+      if (rB) {
+        const T2 dB = lddB(j);
+        const T2 hx = cadd(cmul(im, x0A), cmul(ie, xE));
+        const T2 hz = cadd(cmul(iZs, xpB), cmul(iZn, xmB));
+        resB = csub(bB, csub(csub(cmul(cmaybe_conj(dB, CJ), x0B), cmul(Zj, hx)), cmul(XB, hz)));
       }
     }
-    bcur = bnx; dcur = dnx; Zc = Znx; iZc = iZd; iZd = iZnx;
-    // horizontal weights at the centre lanes: (r[l-1] + r[l+1]) / 2 + r[l]
-    const T2 re = shfl_down1(r), rw = shfl_up1(r);
-    const T2 h = cadd(r, cscale(cadd(re, rw), (T)0.5));
+    bA = bnA; bB = bnB;
+    // horizontal weights of coarse column I = C0 + l: r(2I)/2 + r(2I+1) + r(2I+2)/2
+    const T2 hB = cscale(resB, (T)0.5);
+    const T2 h = cadd(hB, shfl_down1(cadd(resA, hB)));
     // fine row j = 2J: first (half) term of coarse row J, last (half) term of J - 1;
     // j = 2J + 1: middle term of coarse row J
     if (!(j & 1)) {
@@ -576,48 +588,59 @@ k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>:
     } else {
       acc0 = cadd(acc0, h);
     }
-    xm = x0; x0 = xp; xp = xn;
+    xmA = x0A; x0A = xpA; xpA = xnA;
+    xmB = x0B; x0B = xpB; xpB = xnB;
   }
 }
 
-// x_f += P x_c (bilinear; fine i odd -> coarse (i-1)/2, i even -> mean of coarse i/2-1, i/2).
+// x_f += P x_c by column strips, bilinear: fine 2I + 1 <- coarse I, fine 2I <-
+// (coarse I - 1 + coarse I) / 2 in each direction.  A warp owns the coarse columns C0 - 1 .. C0 + 30 (lane l: I = C0 - 1 + l)
+// and the coarse rows J0 .. J1 - 1 of one block; for J = J0 .. J1 - 1 lanes
+// 1 .. 31 update the fine columns 2I, 2I + 1 of the fine rows 2J, 2J + 1
+// (lane 0 only supplies coarse column C0 - 1).  Each coarse value is read once
+// and kept for the next row pair; one shuffle per coarse row gives column
+// I - 1.  Coarse indices outside the coarse grid contribute zero.
 template <typename T>
-__global__ void __launch_bounds__(TILE_THREADS)
-k_prolong_add(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__restrict__ xc,
-              typename cplx<T>::t *__restrict__ xf) {
+__global__ void __launch_bounds__(MARCH_THREADS)
+k_prolong_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__restrict__ xc,
+                typename cplx<T>::t *__restrict__ xf, const StripDev *__restrict__ pstrips, int n_pstrips) {
   typedef typename cplx<T>::t T2;
-  const TileDev t = Lf.tiles[blockIdx.x];
-  if (Lf.skip && Lf.skip[t.blk]) return;
-  const BlkDev bkf = Lf.blks[t.blk];
+  const int gw = blockIdx.x * (MARCH_THREADS / 32) + (threadIdx.x >> 5);
+  if (gw >= n_pstrips) return;                        // whole warps leave together
+  const StripDev s = pstrips[gw];
+  if (Lf.skip && Lf.skip[s.blk]) return;
+  const BlkDev bkf = Lf.blks[s.blk];
   const OpDev opf = Lf.ops[bkf.op];
-  const BlkDev bkc = Lc.blks[t.blk];
+  const BlkDev bkc = Lc.blks[s.blk];
   const OpDev opc = Lc.ops[bkc.op];
-  const int j = t.row0 + (threadIdx.x >> 5);
-  if (j >= opf.nz) return;
-  const T2 *cb = xc + bkc.off;
-  int J0, J1; T wz0, wz1;
-  if (j & 1) { J0 = (j - 1) >> 1; J1 = -1; wz0 = 1; wz1 = 0; }
-  else { J0 = (j >> 1) - 1; J1 = j >> 1; wz0 = 0.5; wz1 = 0.5; }
-  for (int i = threadIdx.x & 31; i < opf.nx; i += 32) {
-    int I0, I1; T wx0, wx1;
-    if (i & 1) { I0 = (i - 1) >> 1; I1 = -1; wx0 = 1; wx1 = 0; }
-    else { I0 = (i >> 1) - 1; I1 = i >> 1; wx0 = 0.5; wx1 = 0.5; }
-    T2 acc = mk<T2>(0, 0);
-    int Js[2] = {J0, J1}; T wzs[2] = {wz0, wz1};
-    int Is[2] = {I0, I1}; T wxs[2] = {wx0, wx1};
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      int J = Js[q];
-      if (J < 0 || J >= opc.nz) continue;
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        int I = Is[p];
-        if (I < 0 || I >= opc.nx) continue;
-        acc = cadd(acc, cscale(cb[(long long)J * opc.nx + I], wzs[q] * wxs[p]));
-      }
-    }
-    long long k = bkf.off + (long long)j * opf.nx + i;
-    xf[k] = cadd(xf[k], acc);
+  const int nx = opf.nx, nz = opf.nz, ncx = opc.nx, ncz = opc.nz;
+  const int lane = threadIdx.x & 31;
+  const int I = s.col0 - 1 + lane;
+  const bool cin = I >= 0 && I < ncx;                 // the coarse column exists
+  const bool wE = lane >= 1 && 2 * I < nx;            // fine column 2I of this lane
+  const bool wO = lane >= 1 && 2 * I + 1 < nx;        // fine column 2I + 1
+  const T2 zero = mk<T2>(0, 0);
+  const T2 *pc = xc + bkc.off + (long long)I;         // dereferenced only where cin
+  T2 *pf = xf + bkf.off + 2LL * I;                    // dereferenced only where wE / wO
+  auto ldc = [&](int J) -> T2 { return (cin && J >= 0 && J < ncz) ? pc[(long long)J * ncx] : zero; };
+  T2 cp = ldc(s.row0 - 1);                            // coarse row J - 1 at column I
+  T2 cpw = shfl_up1(cp);                              // ... at column I - 1
+  for (int J = s.row0; J < s.row1; ++J) {
+    const int j0 = 2 * J, j1 = 2 * J + 1;
+    const bool r0 = j0 < nz, r1 = j1 < nz;
+    T2 *row0 = pf + (long long)j0 * nx, *row1 = row0 + nx;
+    // every load of the row pair first (the four fine values do not alias
+    // the coarse vector), then the four updates
+    const T2 cn = ldc(J);
+    const T2 f0E = (r0 && wE) ? row0[0] : zero, f0O = (r0 && wO) ? row0[1] : zero;
+    const T2 f1E = (r1 && wE) ? row1[0] : zero, f1O = (r1 && wO) ? row1[1] : zero;
+    const T2 cnw = shfl_up1(cn);
+    const T2 vs = cadd(cp, cn);                       // fine row 2J: mean of coarse rows J - 1, J
+    if (r0 && wE) row0[0] = cadd(f0E, cscale(cadd(vs, cadd(cpw, cnw)), (T)0.25));
+    if (r0 && wO) row0[1] = cadd(f0O, cscale(vs, (T)0.5));
+    if (r1 && wE) row1[0] = cadd(f1E, cscale(cadd(cn, cnw), (T)0.5));   // fine row 2J + 1: coarse row J
+    if (r1 && wO) row1[1] = cadd(f1O, cn);
+    cp = cn; cpw = cnw;
   }
 }
 
@@ -753,25 +776,29 @@ struct SmemCycle {
       }
     }
     __syncthreads();
+    // full weighting: a warp per coarse row J (fine rows 2J .. 2J + 2), lanes
+    // over the coarse columns I (fine columns 2I .. 2I + 2; 2J + 2 and 2I + 2
+    // may fall outside the fine grid for even sizes)
     const int onx = L.nx, onz = L.nz;
     const int cnx = lvl[l + 1].nx, cnz = lvl[l + 1].nz;
     T2 *bc = lvl[l + 1].b;
-    const int nc = cnx * cnz;
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-      const int J = k / cnx, I = k - J * cnx;
-      T2 acc = mk<T2>(0, 0);
-      for (int db = -1; db <= 1; ++db) {
-        const int j = 2 * J + 1 + db;
-        if (j < 0 || j >= onz) continue;
-        const T wz = db == 0 ? T(1) : T(0.5);
-        for (int da = -1; da <= 1; ++da) {
-          const int i = 2 * I + 1 + da;
-          if (i < 0 || i >= onx) continue;
-          const T wx = da == 0 ? T(1) : T(0.5);
-          acc = cadd(acc, cscale(ts[j * onx + i], wz * wx));
+    for (int J = threadIdx.x >> 5; J < cnz; J += nw) {
+      const T2 *r0 = ts + (2 * J) * onx, *r1 = r0 + onx, *r2 = r1 + onx;
+      const bool last = 2 * J + 2 < onz;
+      for (int I = lane; I < cnx; I += 32) {
+        const int i = 2 * I;
+        const bool east = i + 2 < onx;
+        T2 h0 = cadd(cscale(r0[i], (T)0.5), r0[i + 1]);
+        T2 h1 = cadd(cscale(r1[i], (T)0.5), r1[i + 1]);
+        T2 h2 = mk<T2>(0, 0);
+        if (last) h2 = cadd(cscale(r2[i], (T)0.5), r2[i + 1]);
+        if (east) {
+          h0 = cadd(h0, cscale(r0[i + 2], (T)0.5));
+          h1 = cadd(h1, cscale(r1[i + 2], (T)0.5));
+          if (last) h2 = cadd(h2, cscale(r2[i + 2], (T)0.5));
         }
+        bc[J * cnx + I] = cadd(cscale(cadd(h0, h2), (T)0.5), h1);
       }
-      bc[k] = acc;
     }
     __syncthreads();
   }
@@ -780,24 +807,28 @@ struct SmemCycle {
     const int cnx = lvl[l + 1].nx, cnz = lvl[l + 1].nz;
     T2 *xf = X_(l);
     const T2 *xc = X_(l + 1);
-    const int n = fnx * fnz;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const int j = k / fnx, i = k - j * fnx;
-      T2 acc = mk<T2>(0, 0);
-      for (int q = 0; q < 2; ++q) {
-        int J; T wz;
-        if (j & 1) { if (q) continue; J = (j - 1) >> 1; wz = 1; }
-        else { J = (j >> 1) - 1 + q; wz = 0.5; }
-        if (J < 0 || J >= cnz) continue;
-        for (int p = 0; p < 2; ++p) {
-          int I; T wx;
-          if (i & 1) { if (p) continue; I = (i - 1) >> 1; wx = 1; }
-          else { I = (i >> 1) - 1 + p; wx = 0.5; }
-          if (I < 0 || I >= cnx) continue;
-          acc = cadd(acc, cscale(xc[J * cnx + I], wz * wx));
-        }
+    const T2 zero = mk<T2>(0, 0);
+    // a warp per fine row j, lanes over the fine columns i: row j odd takes
+    // coarse row (j - 1)/2, row j even the mean of rows j/2 - 1 and j/2; the
+    // same across columns; coarse indices outside the grid give zero
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = threadIdx.x >> 5; j < fnz; j += nw) {
+      const int Ja = (j - 1) >> 1, Jb = j >> 1;     // j odd: Ja == Jb == (j - 1)/2
+      const bool odd = j & 1;
+      const T2 *ra = (Ja >= 0 && Ja < cnz) ? xc + Ja * cnx : nullptr;
+      const T2 *rb = (!odd && Jb < cnz) ? xc + Jb * cnx : nullptr;
+      const T wz = odd ? (T)1 : (T)0.5;
+      T2 *xr = xf + j * fnx;
+      for (int i = lane; i < fnx; i += 32) {
+        const int Ia = (i - 1) >> 1, Ib = i >> 1;
+        const bool iodd = i & 1;
+        const bool ia = Ia >= 0 && Ia < cnx, ib = !iodd && Ib < cnx;
+        T2 va = zero, vb = zero;
+        if (ra) { if (ia) va = ra[Ia]; if (ib) va = cadd(va, ra[Ib]); }
+        if (rb) { if (ia) vb = rb[Ia]; if (ib) vb = cadd(vb, rb[Ib]); }
+        const T wx = iodd ? (T)1 : (T)0.5;
+        xr[i] = cadd(xr[i], cscale(cadd(va, vb), wz * wx));
       }
-      xf[k] = cadd(xf[k], acc);
     }
     __syncthreads();
   }

@@ -201,17 +201,19 @@ struct Instance {
 struct LevelTables {
   std::vector<BlkDev> hM, hA;
   std::vector<TileDev> htiles;
-  std::vector<StripDev> hstrips, hstrips2, hrstrips;
+  std::vector<StripDev> hstrips, hstrips2, hrstrips, hpstrips;
   std::vector<int> ht0, ht1, hs0, hs1;
   DBuf<BlkDev> blksM, blksA;
   DBuf<TileDev> tiles;
   DBuf<StripDev> strips, strips2, rstrips;   // rstrips: coarse-column strips of the restriction to l + 1
+  DBuf<StripDev> pstrips;                    // coarse-column strips of the prolongation from l + 1
   DBuf<int> t0, t1, s0, s1;   // per block: its row tiles [t0, t1), its column strips [s0, s1)
   long long field = 0;  // complex elements of one field on this level
   int n_tiles = 0;
   int n_strips = 0;
   int n_strips2 = 0;
   int n_rstrips = 0;
+  int n_pstrips = 0;
 };
 
 template <typename T> struct Work {
@@ -417,6 +419,8 @@ struct Ctx {
                                     const BFuse<T> *fz = nullptr);
   template <typename T> void resid_restrict(int cj, int l, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
                                             typename cplx<T>::t *bc);
+  template <typename T> void prolong(int l, const LevelView<T> &Lf, const LevelView<T> &Lc,
+                                     const typename cplx<T>::t *xc, typename cplx<T>::t *xf);
   void timer_end(int streams, int pass_streams, size_t elem_bytes);
   template <typename T> void apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *y,
                                         const typename cplx<T>::t *a, int nd);
@@ -828,7 +832,7 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
     LevelTables &T = lv[l];
     T.hM.assign(B, BlkDev{0, 0, 0});
     T.hA.assign(B, BlkDev{0, 0, 0});
-    T.htiles.clear(); T.hstrips.clear(); T.hstrips2.clear(); T.hrstrips.clear(); T.ht0.assign(B, 0); T.ht1.assign(B, 0);
+    T.htiles.clear(); T.hstrips.clear(); T.hstrips2.clear(); T.hrstrips.clear(); T.hpstrips.clear(); T.ht0.assign(B, 0); T.ht1.assign(B, 0);
     T.hs0.assign(B, 0); T.hs1.assign(B, 0);
     long long off = 0;
     for (int b = 0; b < B; ++b) {
@@ -863,6 +867,12 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
         for (int J0 = 0; J0 < ncz; J0 += RM_ROWS)
           for (int C0 = 0; C0 < ncx; C0 += RM_COLS)
             T.hrstrips.push_back(StripDev{b, C0, J0, std::min(J0 + RM_ROWS, ncz)});
+        // prolongation: coarse indices J, I whose fine rows 2J, 2J + 1 and
+        // columns 2I, 2I + 1 meet the fine grid (up to ncz, ncx for odd sizes)
+        const int pcz = (nz + 1) / 2, pcx = (nx + 1) / 2;
+        for (int J0 = 0; J0 < pcz; J0 += PM_ROWS)
+          for (int C0 = 0; C0 < pcx; C0 += PM_COLS)
+            T.hpstrips.push_back(StripDev{b, C0, J0, std::min(J0 + PM_ROWS, pcz)});
       }
       off += (long long)nx * nz;
     }
@@ -874,6 +884,8 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
     T.strips2.upload(T.hstrips2, st);
     T.n_rstrips = (int)T.hrstrips.size();
     T.rstrips.upload(T.hrstrips, st);
+    T.n_pstrips = (int)T.hpstrips.size();
+    T.pstrips.upload(T.hpstrips, st);
     T.blksM.upload(T.hM, st);
     T.blksA.upload(T.hA, st);
     T.tiles.upload(T.htiles, st);
@@ -1095,6 +1107,18 @@ void Ctx::resid_restrict(int cj, int l, const typename cplx<T>::t *x, const type
   KCHECK();
 }
 
+// x_l += P x_{l+1} (bilinear) on every block.
+template <typename T>
+void Ctx::prolong(int l, const LevelView<T> &Lf, const LevelView<T> &Lc, const typename cplx<T>::t *xc,
+                  typename cplx<T>::t *xf) {
+  const int n = lv[l].n_pstrips;   // built with the restriction strips
+  if (n == 0) fail(FWI_E_INVAL, "internal: no prolongation strips on a global multigrid level");
+  const int grid = (n + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32);
+  KPROF("k_prolong_march", l, sizeof(typename cplx<T>::t) * (2.0 * lv[l].field + lv[l + 1].field), st);
+  k_prolong_march<T><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, xc, xf, lv[l].pstrips.p, n);
+  KCHECK();
+}
+
 template <typename T>
 void Ctx::block_dots(int nd, const typename cplx<T>::t *a0, const typename cplx<T>::t *b0,
                      const typename cplx<T>::t *a1, const typename cplx<T>::t *b1,
@@ -1174,9 +1198,7 @@ void Ctx::mg_cycle(const typename cplx<T>::t *b, typename cplx<T>::t *x, int cj,
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
       resid_restrict<T>(cj, l, cur, bl, w.lb[l + 1].p);
       T2 *xc = cyc(l + 1, w.lb[l + 1].p, w.lx[l + 1].p, w.lt[l + 1].p);
-      KPROF("k_prolong_add", l, sizeof(T2) * (2.0 * lv[l].field + lv[l + 1].field), st);
-      k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
-      KCHECK();
+      prolong<T>(l, Lf, Lc, xc, cur);
     }
     smooth<T>(o.nu2, false, cj, wj, bl, cur, oth, l);
     return cur;
@@ -1219,9 +1241,7 @@ void Ctx::mg_cycle_into(const typename cplx<T>::t *b, typename cplx<T>::t *x, in
       LevelView<T> Lf = viewM<T>(l), Lc = viewM<T>(l + 1);
       resid_restrict<T>(cj, l, cur, bl, lb[l + 1]);
       T2 *xc = cyc(l + 1, lb[l + 1], lx[l + 1], lt[l + 1]);
-      KPROF("k_prolong_add", l, sizeof(T2) * (2.0 * lv[l].field + lv[l + 1].field), st);
-      k_prolong_add<T><<<Lf.n_tiles, TILE_THREADS, 0, st>>>(Lf, Lc, xc, cur);
-      KCHECK();
+      prolong<T>(l, Lf, Lc, xc, cur);
     }
     smooth<T>(o.nu2, false, cj, wj, bl, cur, oth, l);
     return cur;
