@@ -279,7 +279,7 @@ def run_extra_case(args):
         o.max_outer = args.max_outer
         _, table = tune_kkt(f, o, (2, 4, 6, 8, 12, 16, 24, 48), (2,), (30,))
         out["sweep"] = [{"inner_solver": "bicgstab+multigrid", "inner_iters": n, "kkt_s": round(t, 3), "outer": k,
-                         "converged": ok} for n, wd, rs, t, k, ok, _, _ in table]
+                         "converged": ok} for n, wd, rs, t, k, ok, _, _, _ in table]
         # the paper's incomplete-LU block approximation (zero fill on the GPU):
         # applied once as A~, and as the preconditioner of BiCGStab
         for solver, iters in ((2, 1), (1, 4), (1, 8), (1, 16)):
@@ -396,7 +396,7 @@ def run_epsrule_case(args):
         best, table = tune_kkt(f, o, cands, (None,), (None,))
         chosen[eps] = best.inner_iters
         out.setdefault("autotune", []).append({"eps": eps, "table": [
-            {"inner_iters": n, "s": round(t, 3), "outer": k, "ok": ok} for n, wd, rs, t, k, ok, _, _ in table]})
+            {"inner_iters": n, "s": round(t, 3), "outer": k, "ok": ok} for n, wd, rs, t, k, ok, _, _, _ in table]})
     for eps in (eps_rule, EPS):
         o = P.Opts.from_buffer_copy(opts)
         o.eps = eps
@@ -641,13 +641,14 @@ def run_newton(args):
         from paper_2204_06489_gb300.autotune import tune_kkt
         f.set_model(0, wl.gamma_start)
         f.forward(opts, want_data=False)
-        opts, table = tune_kkt(f, opts, (4, 6, 8, 12, 16), (1, 2), (30,))
+        opts, table = tune_kkt(f, opts, (4, 6, 8, 12, 16), (1, 2), (30,), nus=(1, 2))
         # second stage at the chosen schedule: strip height x coarse-cycle CTA size, scored by
         # time per FGMRES iteration (the layout changes no arithmetic)
         opts, table2 = tune_kkt(f, opts, (opts.inner_iters,), (None,), (None,), (8, 16, 32), (512, 1024),
                                 per_iteration=True)
         tuned = [{"inner_iters": n, "wdepth": wd, "restart": rs, "strip_rows": sr, "coarse_threads": ct,
-                  "s": round(t, 3), "outer": o, "ok": ok} for n, wd, rs, t, o, ok, sr, ct in table + table2]
+                  "nu": nu, "s": round(t, 3), "outer": o, "ok": ok}
+                 for n, wd, rs, t, o, ok, sr, ct, nu in table + table2]
     g0 = torch.from_numpy(wl.gamma_start).cuda()
     ds_dev = torch.zeros(wl.grid.nx * wl.grid.nz, dtype=torch.float64, device="cuda")
 
@@ -782,7 +783,7 @@ def run_newton(args):
                       "tol": 1e-6, "restart": opts.restart, "inner_iters": opts.inner_iters,
                       "include_Ls_n": INCLUDE_LS_N, "strip_rows": opts.strip_rows,
                       "coarse_threads": opts.coarse_threads, "arnoldi_dots": opts.arnoldi_dots,
-                      "mg": f"W(2,2) to level {opts.mg_wdepth}, V below",
+                      "mg": f"W({opts.nu1},{opts.nu2}) to level {opts.mg_wdepth}, V below",
                       "steps": f"each timed step is one of the {NEWTON_STEPS} Gauss-Newton steps of the "
                                f"trajectory from the starting model (reset after {NEWTON_STEPS})",
                       "l2": "working set > L2 (packed KKT vector 153 MB, Krylov basis 9.4 GB)",

@@ -56,23 +56,26 @@ def tune_inner(fwi: FWI, b, base: Optional[Opts] = None, nus: Iterable[int] = (1
 def tune_kkt(fwi: FWI, base: Optional[Opts] = None, inner_iters: Iterable[int] = (4, 6, 8, 12),
              wdepths: Iterable[int] = (None,), restarts: Iterable[int] = (None,),
              strip_rows: Iterable[int] = (None,), coarse_threads: Iterable[int] = (None,),
-             per_iteration: bool = False):
+             per_iteration: bool = False, nus: Iterable[int] = (None,)):
     """Time one whole KKT solve (after ``fwi.forward``) per (inner-iteration
     count, W-cycle depth, FGMRES restart, column-strip height of the stencil
     kernels, threads per CTA of the shared-memory coarse cycle) and keep the
-    fastest that converges.  With ``per_iteration`` the score is the time per
+    fastest that converges (``nus``: Jacobi sweeps before and after each
+    coarse-grid correction, nu1 = nu2).  With ``per_iteration`` the score is the time per
     FGMRES iteration: for launch-layout parameters, which change no arithmetic,
     the iteration count differs between candidates only through rounding (a
     few iterations either way) and would otherwise decide the choice.
     Returns (best Opts, table of (inner_iters, wdepth, restart, seconds, outer
-    iterations, converged, strip_rows, coarse_threads))."""
+    iterations, converged, strip_rows, coarse_threads, nu))."""
     import torch
     base = base if base is not None else default_opts()
     table = []
     best, best_t = None, math.inf
-    for n, wd, rs, sr, ct in itertools.product(inner_iters, wdepths, restarts, strip_rows, coarse_threads):
+    for nu, n, wd, rs, sr, ct in itertools.product(nus, inner_iters, wdepths, restarts, strip_rows, coarse_threads):
         o = Opts.from_buffer_copy(base)
         o.inner_iters = n
+        if nu is not None:
+            o.nu1 = o.nu2 = nu
         if wd is not None:
             o.mg_wdepth = wd
         if rs is not None:
@@ -89,7 +92,7 @@ def tune_kkt(fwi: FWI, base: Optional[Opts] = None, inner_iters: Iterable[int] =
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         ok = st["rel_res"] <= o.tol
-        table.append((n, o.mg_wdepth, o.restart, dt, st["outer_iters"], ok, o.strip_rows, o.coarse_threads))
+        table.append((n, o.mg_wdepth, o.restart, dt, st["outer_iters"], ok, o.strip_rows, o.coarse_threads, o.nu1))
         score = dt / max(st["outer_iters"], 1) if per_iteration else dt
         if ok and score < best_t:
             best, best_t = o, score

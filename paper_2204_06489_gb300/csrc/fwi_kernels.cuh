@@ -1471,7 +1471,7 @@ k_bicg_update(LevelView<T> L, const BiState *S, typename cplx<T>::t *y, const ty
 // The last update of a BiCGStab iteration fused with the dots that follow it:
 //   x += alpha ph + omega sh;  r = s - omega t;
 //   partial[tile][0] = <r, r>,  partial[tile][1] = <rh, r>   (new r)
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_bicg_xr(LevelView<T> L, const BiState *S, typename cplx<T>::t *__restrict__ x,
           const typename cplx<T>::t *__restrict__ ph, const typename cplx<T>::t *__restrict__ sh,
@@ -1483,29 +1483,64 @@ k_bicg_xr(LevelView<T> L, const BiState *S, typename cplx<T>::t *__restrict__ x,
   if (L.skip && L.skip[tl.blk]) return;               // whole CTA
   const BlkDev bk = L.blks[tl.blk];
   const OpDev op = L.ops[bk.op];
-  const int j = tl.row0 + (threadIdx.x >> 5);
   double tre[3] = {0, 0, 0}, tim[3] = {0, 0, 0};
   T rre[3] = {0, 0, 0}, rim[3] = {0, 0, 0};
-  if (j < op.nz) {
-    const BiState st = S[tl.blk];
-    const T2 al = mk<T2>(st.alpha.x, st.alpha.y), om = mk<T2>(st.omega.x, st.omega.y);
-    const long long base = bk.off + (long long)j * op.nx;
-    int cnt = 0;
-#pragma unroll 2
-    for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
-      const long long k = base + i;
-      x[k] = cadd(x[k], cadd(cmul(al, ph[k]), cmul(om, sh[k])));
-      const T2 rn = csub(sv[k], cmul(om, t[k]));
-      r[k] = rn;
-      const T2 a = rh[k];
-      rre[0] = tfma(rn.x, rn.x, tfma(rn.y, rn.y, rre[0]));
-      rre[1] = tfma(a.x, rn.x, tfma(a.y, rn.y, rre[1]));
-      rim[1] = tfma(a.x, rn.y, tfma(-a.y, rn.x, rim[1]));
-      if (sizeof(T) == 4 && ++cnt == DOT_RUN) {
+  const BiState st = S[tl.blk];
+  const T2 al = mk<T2>(st.alpha.x, st.alpha.y), om = mk<T2>(st.omega.x, st.omega.y);
+  int cnt = 0;
+  // one node: the update, then <r, r> and <rh, r> (FP32 runs of DOT_RUN terms)
+  auto node = [&](T2 &xk, T2 phk, T2 shk, T2 svk, T2 tk, T2 a) -> T2 {
+    xk = cadd(xk, cadd(cmul(al, phk), cmul(om, shk)));
+    const T2 rn = csub(svk, cmul(om, tk));
+    rre[0] = tfma(rn.x, rn.x, tfma(rn.y, rn.y, rre[0]));
+    rre[1] = tfma(a.x, rn.x, tfma(a.y, rn.y, rre[1]));
+    rim[1] = tfma(a.x, rn.y, tfma(-a.y, rn.x, rim[1]));
+    if (sizeof(T) == 4 && ++cnt == DOT_RUN) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) { tre[q] += rre[q]; tim[q] += rim[q]; rre[q] = 0; rim[q] = 0; }
-        cnt = 0;
+      for (int q = 0; q < 2; ++q) { tre[q] += rre[q]; tim[q] += rim[q]; rre[q] = 0; rim[q] = 0; }
+      cnt = 0;
+    }
+    return rn;
+  };
+  auto scalar = [&](long long k) {
+    T2 xk = x[k];
+    r[k] = node(xk, ph[k], sh[k], sv[k], t[k], rh[k]);
+    x[k] = xk;
+  };
+  static_assert(!VEC || sizeof(T) == 4, "the vector path is for complex64");
+  if constexpr (VEC) {
+    // complex64 with every vector 16-byte aligned: the tile's rows are one
+    // contiguous range; a lane moves two nodes per float4 access
+    const int rows = min(TILE_ROWS, op.nz - tl.row0);
+    if (rows > 0) {
+      const long long base = bk.off + (long long)tl.row0 * op.nx;
+      const long long len = (long long)rows * op.nx;
+      const long long head = base & 1;                 // one node up to the 16-byte boundary
+      const long long np = (len - head) >> 1;
+      if (threadIdx.x == 0 && head) scalar(base);
+      if (threadIdx.x == 1 && ((len - head) & 1)) scalar(base + len - 1);
+      const long long k0 = base + head;
+      const float4 *ph4 = reinterpret_cast<const float4 *>(ph + k0), *sh4 = reinterpret_cast<const float4 *>(sh + k0);
+      const float4 *sv4 = reinterpret_cast<const float4 *>(sv + k0), *t4 = reinterpret_cast<const float4 *>(t + k0);
+      const float4 *rh4 = reinterpret_cast<const float4 *>(rh + k0);
+      float4 *x4 = reinterpret_cast<float4 *>(x + k0), *r4 = reinterpret_cast<float4 *>(r + k0);
+      for (long long p = threadIdx.x; p < np; p += TILE_THREADS) {
+        const float4 X = x4[p], Ph = ph4[p], Sh = sh4[p], Sv = sv4[p], Tt = t4[p], Rh = rh4[p];
+        T2 xa = mk<T2>(X.x, X.y), xb = mk<T2>(X.z, X.w);
+        const T2 ra = node(xa, mk<T2>(Ph.x, Ph.y), mk<T2>(Sh.x, Sh.y), mk<T2>(Sv.x, Sv.y), mk<T2>(Tt.x, Tt.y),
+                           mk<T2>(Rh.x, Rh.y));
+        const T2 rb = node(xb, mk<T2>(Ph.z, Ph.w), mk<T2>(Sh.z, Sh.w), mk<T2>(Sv.z, Sv.w), mk<T2>(Tt.z, Tt.w),
+                           mk<T2>(Rh.z, Rh.w));
+        x4[p] = make_float4(xa.x, xa.y, xb.x, xb.y);
+        r4[p] = make_float4(ra.x, ra.y, rb.x, rb.y);
       }
+    }
+  } else {
+    const int j = tl.row0 + (threadIdx.x >> 5);
+    if (j < op.nz) {
+      const long long base = bk.off + (long long)j * op.nx;
+#pragma unroll 2
+      for (int i = threadIdx.x & 31; i < op.nx; i += 32) scalar(base + i);
     }
   }
   tile_dots_store<T>(2, rre, rim, tre, tim, partial);

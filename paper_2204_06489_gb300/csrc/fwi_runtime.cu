@@ -12,6 +12,8 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <initializer_list>
+#include <cstdint>
 #include <tuple>
 #include <map>
 #include <memory>
@@ -130,6 +132,13 @@ static void fail(int code, const std::string &m) { throw Err{code, m}; }
 // Every cudaMalloc / cudaMallocHost / cudaFree / cudaFreeHost the library makes
 // (diagnostics: fwi_memory_calls).
 static std::atomic<unsigned long long> g_memcalls{0};
+
+// Every pointer starts on a 16-byte boundary (vector-access kernel variants).
+static inline bool aligned16(std::initializer_list<const void *> ps) {
+  for (const void *p : ps)
+    if (reinterpret_cast<uintptr_t>(p) & 15u) return false;
+  return true;
+}
 
 template <typename T> struct DBuf {
   T *p = nullptr;
@@ -1402,8 +1411,12 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
     scal_s(3);
     // x += alpha ph + omega sh; r = s - omega t; <r, r>, <rh, r>
     KPROF("k_bicg_xr", 0, 8.0 * sizeof(typename cplx<T>::t) * F0, st);
-    k_bicg_xr<T><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, x, w.ph.p, w.sh.p, w.s.p, w.r.p, w.t.p, w.rh.p,
-                                              partial.p);
+    if (sizeof(T) == 4 && aligned16({x, w.ph.p, w.sh.p, w.s.p, w.r.p, w.t.p, w.rh.p}))
+      k_bicg_xr<T, sizeof(T) == 4><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, x, w.ph.p, w.sh.p, w.s.p, w.r.p, w.t.p,
+                                                                w.rh.p, partial.p);
+    else
+      k_bicg_xr<T, false><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, x, w.ph.p, w.sh.p, w.s.p, w.r.p, w.t.p, w.rh.p,
+                                                       partial.p);
     KCHECK();
     scal(5);                                                           // stage 4, then the next stage 1
     if (count) *count += B;

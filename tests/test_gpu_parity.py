@@ -98,8 +98,19 @@ def _oracle_hier(P, w, p, fidx, opts):
 
 @pytest.mark.parametrize("cycle,wdepth", [(1, 2), (2, 2), (2, 9)])
 def test_multigrid_cycle(setup, cycle, wdepth):
+    _check_cycle(setup, cycle, wdepth, 2, 2)
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (1, 3), (3, 0)])
+def test_multigrid_cycle_sweep_counts(setup, nu1, nu2):
+    """Odd and uneven sweep counts (single sweeps next to fused pairs, the
+    p-update fusion falling back, no post-smoothing)."""
+    _check_cycle(setup, 2, 2, nu1, nu2)
+
+
+def _check_cycle(setup, cycle, wdepth, nu1, nu2):
     P, f, wls, probs, _ = setup
-    opts = P.default_opts(mg_cycle=cycle, mg_wdepth=wdepth)
+    opts = P.default_opts(mg_cycle=cycle, mg_wdepth=wdepth, nu1=nu1, nu2=nu2)
     n = f.layout()["field_elems"]
     bt, b = _rand_field(n, 6)
     x = f.mg_cycle(bt, opts).cpu().numpy()
@@ -117,11 +128,13 @@ def test_multigrid_cycle(setup, cycle, wdepth):
 
 
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_inner_solve(setup, adjoint):
+@pytest.mark.parametrize("nu", [2, 1])
+def test_inner_solve(setup, adjoint, nu):
     """Batched BiCGStab + multigrid, 6 iterations, complex128, against the
-    oracle's same iteration per block."""
+    oracle's same iteration per block (nu = 1: single sweeps, the p update
+    outside the smoother)."""
     P, f, wls, probs, _ = setup
-    opts = P.default_opts(inner_iters=6)
+    opts = P.default_opts(inner_iters=6, nu1=nu, nu2=nu)
     n = f.layout()["field_elems"]
     bt, b = _rand_field(n, 7)
     x = f.inner_solve(bt, opts, adjoint=adjoint).cpu().numpy()
