@@ -106,7 +106,8 @@ typedef struct {
                              complex128 vectors always use FP64                  [COMP] */
   int check_orth;         /* measure max |I - V^T V| of every FGMRES basis into
                              fwi_stats.orth_loss (diagnostics, costs extra dots) [0]   */
-  int strip_rows;         /* rows per warp of the column-strip stencil kernels (2..64) [16]  */
+  int strip_rows;         /* rows per warp of the column-strip stencil kernels on level 0
+                             (2..64; half as many on the coarser global levels) [16]  */
   int coarse_threads;     /* threads per CTA of the shared-memory coarse cycle (512 | 1024) [512] */
   int fwd_warm;           /* start the forward solve from the previous forward wavefields
                              of this context (same tolerance; 0: from zero)      [1]    */

@@ -593,6 +593,134 @@ k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>:
   }
 }
 
+// Asynchronous global -> shared copies of 8 bytes (cp.async, tracked per
+// thread in commit groups): a thread waits only for its own copies, so a lane
+// that reads back only what it copied needs no barrier.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The residual-restriction of k_resid_restrict_march (same strips, lanes and
+// arithmetic) for complex64, with the rows of x, b and the diagonal staged in
+// shared memory by asynchronous copies RR_DEPTH rows ahead: a ring of
+// RR_DEPTH row slots per warp (x, b, diagonal of both columns of every lane),
+// refilled as the warp walks down, so the loads' latency overlaps the
+// arithmetic of the rows in between without holding registers.  Each lane
+// copies and reads back only its own two columns.
+#define RR_DEPTH 4
+template <typename T, bool CJ>
+__global__ void __launch_bounds__(MARCH_THREADS, 4)
+k_resid_restrict_stage(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>::t *__restrict__ xf,
+                       const typename cplx<T>::t *__restrict__ bf, typename cplx<T>::t *__restrict__ bc,
+                       const StripDev *__restrict__ rstrips, int n_rstrips) {
+  typedef typename cplx<T>::t T2;
+  static_assert(sizeof(T) == 4, "the staged variant is for complex64");
+  // [warp][slot][array: x, b, diagonal][column: 32 A lanes, then 32 B lanes]
+  __shared__ T2 ring[MARCH_THREADS / 32][RR_DEPTH][3][64];
+  const int wid = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (MARCH_THREADS / 32) + wid;
+  if (gw >= n_rstrips) return;                        // whole warps leave together
+  const StripDev s = rstrips[gw];
+  if (Lf.skip && Lf.skip[s.blk]) return;
+  const BlkDev bkf = Lf.blks[s.blk];
+  const OpDev op = Lf.ops[bkf.op];
+  const BlkDev bkc = Lc.blks[s.blk];
+  const OpDev opc = Lc.ops[bkc.op];
+  const int nx = op.nx, nz = op.nz;
+  const int lane = threadIdx.x & 31;
+  const int iA = 2 * s.col0 - 1 + 2 * lane, iB = iA + 1;
+  const bool gA = iA >= 0 && iA < nx;
+  const bool gB = lane <= 30 && iB < nx;
+  const bool rA = gA && lane >= 1 && lane <= 30;
+  const bool rB = gB;
+  const int I = s.col0 + lane;
+  const bool cown = lane < RM_COLS && I < opc.nx;
+  const T2 zero = mk<T2>(0, 0);
+  const T2 *X = Lf.st + op.st;
+  const T2 *iXh = X + nx;
+  const T2 *Zr = iXh + nx + 1;
+  const T2 *iZh = Zr + nz;
+  T2 XA = zero, XB = zero, iw = zero, im = zero, ie = zero;
+  if (rA) { XA = cmaybe_conj(X[iA], CJ); iw = cmaybe_conj(iXh[iA], CJ); }
+  if (rB) { XB = cmaybe_conj(X[iB], CJ); ie = cmaybe_conj(iXh[iB + 1], CJ); }
+  if (rA || rB) im = cmaybe_conj(iXh[iB], CJ);
+  const long long cA = (long long)iA;
+  const T2 *px = xf + bkf.off + cA;                   // dereferenced only where the column is in the grid
+  const T2 *pb = bf + bkf.off + cA;
+  const T2 *pd = Lf.dg + op.dg + cA;
+  const int jb = 2 * s.row0, je = 2 * s.row1;       // fine rows with residual: jb .. je
+  T2 (*rg)[3][64] = ring[wid];
+  // copy row r (x where the row exists, b and the diagonal where a residual is
+  // formed) into its slot; one commit group per row, empty ones included
+  auto stage = [&](int r) {
+    if (r >= 0 && r < nz) {
+      const int q = (r - (jb - 1)) % RR_DEPTH;
+      const long long k = (long long)r * nx;
+      if (gA) cp_async8(&rg[q][0][lane], px + k);
+      if (gB) cp_async8(&rg[q][0][32 + lane], px + k + 1);
+      if (r >= jb && r <= je) {
+        if (rA) { cp_async8(&rg[q][1][lane], pb + k); cp_async8(&rg[q][2][lane], pd + k); }
+        if (rB) { cp_async8(&rg[q][1][32 + lane], pb + k + 1); cp_async8(&rg[q][2][32 + lane], pd + k + 1); }
+      }
+    }
+    cp_async_commit();
+  };
+  auto slot = [&](int r) { return (r - (jb - 1)) % RR_DEPTH; };
+  auto rdA = [&](int r, int a, bool ok) -> T2 { return (ok && r >= 0 && r < nz) ? rg[slot(r)][a][lane] : zero; };
+  auto rdB = [&](int r, int a, bool ok) -> T2 { return (ok && r >= 0 && r < nz) ? rg[slot(r)][a][32 + lane] : zero; };
+#pragma unroll
+  for (int q = 0; q < RR_DEPTH; ++q) stage(jb - 1 + q);
+  cp_async_wait<RR_DEPTH - 2>();                      // rows jb - 1 and jb
+  T2 xmA = rdA(jb - 1, 0, gA), x0A = rdA(jb, 0, gA);
+  T2 xmB = rdB(jb - 1, 0, gB), x0B = rdB(jb, 0, gB);
+  T2 acc0 = zero;                // running sum of the coarse row being formed
+  T2 *cout = bc + bkc.off + (cown ? I : 0);
+  for (int j = jb; j <= je; ++j) {
+    cp_async_wait<RR_DEPTH - 3>();                    // row j + 1 (and everything before it)
+    const T2 xpA = rdA(j + 1, 0, gA), xpB = rdB(j + 1, 0, gB);
+    const T2 xE = shfl_down1(x0A);                    // cA of lane l + 1: east of cB
+    const T2 xW = shfl_up1(x0B);                      // cB of lane l - 1: west of cA
+    T2 resA = zero, resB = zero;
+    if (j < nz && (rA || rB)) {
+      const T2 Zj = cmaybe_conj(Zr[j], CJ), iZn = cmaybe_conj(iZh[j], CJ), iZs = cmaybe_conj(iZh[j + 1], CJ);
+      if (rA) {
+        const T2 dA = cmaybe_conj(rg[slot(j)][2][lane], CJ);
+        const T2 hx = cadd(cmul(iw, xW), cmul(im, x0B));
+        const T2 hz = cadd(cmul(iZs, xpA), cmul(iZn, xmA));
+        resA = csub(rg[slot(j)][1][lane], csub(csub(cmul(dA, x0A), cmul(Zj, hx)), cmul(XA, hz)));
+      }
+      if (rB) {
+        const T2 dB = cmaybe_conj(rg[slot(j)][2][32 + lane], CJ);
+        const T2 hx = cadd(cmul(im, x0A), cmul(ie, xE));
+        const T2 hz = cadd(cmul(iZs, xpB), cmul(iZn, xmB));
+        resB = csub(rg[slot(j)][1][32 + lane], csub(csub(cmul(dB, x0B), cmul(Zj, hx)), cmul(XB, hz)));
+      }
+    }
+    // the slot of row j - 1 is free: refill it with row j - 1 + RR_DEPTH
+    stage(j - 1 + RR_DEPTH);
+    const T2 hB = cscale(resB, (T)0.5);
+    const T2 h = cadd(hB, shfl_down1(cadd(resA, hB)));
+    if (!(j & 1)) {
+      const int J = (j >> 1) - 1;
+      if (j > jb) {
+        acc0 = cadd(acc0, cscale(h, (T)0.5));
+        if (cown && J < opc.nz) cout[(long long)J * opc.nx] = acc0;
+      }
+      acc0 = cscale(h, (T)0.5);
+    } else {
+      acc0 = cadd(acc0, h);
+    }
+    xmA = x0A; x0A = xpA;
+    xmB = x0B; x0B = xpB;
+  }
+  cp_async_wait<0>();                                 // no copy left in flight at exit
+}
+
 // x_f += P x_c by column strips, bilinear: fine 2I + 1 <- coarse I, fine 2I <-
 // (coarse I - 1 + coarse I) / 2 in each direction.  A warp owns the coarse columns C0 - 1 .. C0 + 30 (lane l: I = C0 - 1 + l)
 // and the coarse rows J0 .. J1 - 1 of one block; for J = J0 .. J1 - 1 lanes

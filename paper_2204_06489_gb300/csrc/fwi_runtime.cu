@@ -862,13 +862,17 @@ void Ctx::build_hierarchy(const fwi_opts &o) {
       // column strips of the register-marching stencil kernel (fine levels):
       // block-major, then row band, then column, so that neighbouring strips
       // (which share halo rows and columns) run close together
+      // Below level 0 the grids are 4x smaller while the work per strip is the
+      // same, so the stencil strips are half as high there (twice the warps in
+      // flight on an L2-resident level).
+      const int sr_l = l == 0 ? srows : std::max(2, srows / 2);
       T.hs0[b] = (int)T.hstrips.size();
       if (l < std::max(ls, 1))   // level 0 always (operator apply, dots), the other global levels
-        for (int r0 = 0; r0 < nz; r0 += srows) {
+        for (int r0 = 0; r0 < nz; r0 += sr_l) {
           for (int c0 = 0; c0 < nx; c0 += MARCH_COLS)
-            T.hstrips.push_back(StripDev{b, c0, r0, std::min(r0 + srows, nz)});
+            T.hstrips.push_back(StripDev{b, c0, r0, std::min(r0 + sr_l, nz)});
           for (int c0 = 0; c0 < nx; c0 += MARCH2_COLS)
-            T.hstrips2.push_back(StripDev{b, c0, r0, std::min(r0 + srows, nz)});
+            T.hstrips2.push_back(StripDev{b, c0, r0, std::min(r0 + sr_l, nz)});
         }
       T.hs1[b] = (int)T.hstrips.size();
       if (l < ls) {
@@ -1110,9 +1114,22 @@ void Ctx::resid_restrict(int cj, int l, const typename cplx<T>::t *x, const type
   const int n = lv[l].n_rstrips;   // built for every global level l < ls, the only levels that restrict
   if (n == 0) fail(FWI_E_INVAL, "internal: no restriction strips on a global multigrid level");
   const int grid = (n + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32);
-  KPROF("k_resid_restrict_march", l, sizeof(typename cplx<T>::t) * (2.0 * lv[l].field + lv[l + 1].field), st);
-  if (cj) k_resid_restrict_march<T, true><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
-  else k_resid_restrict_march<T, false><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
+  // complex64 level 0 (HBM-resident, latency of the row loads): rows staged in
+  // shared memory by asynchronous copies; the L2-resident coarser levels and
+  // complex128 keep the register pipeline (faster there)
+  const bool staged = sizeof(T) == 4 && l == 0;
+  KPROF(staged ? "k_resid_restrict_stage" : "k_resid_restrict_march", l,
+        sizeof(typename cplx<T>::t) * (2.0 * lv[l].field + lv[l + 1].field), st);
+  if constexpr (sizeof(T) == 4) {
+    if (staged) {
+      if (cj) k_resid_restrict_stage<T, true><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
+      else k_resid_restrict_stage<T, false><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
+    }
+  }
+  if (!staged) {
+    if (cj) k_resid_restrict_march<T, true><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
+    else k_resid_restrict_march<T, false><<<grid, MARCH_THREADS, 0, st>>>(Lf, Lc, x, b, bc, lv[l].rstrips.p, n);
+  }
   KCHECK();
 }
 
