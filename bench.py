@@ -227,7 +227,7 @@ def run_extra_case(args):
     P.load(build_if_missing=True)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    opts = P.default_opts(eps=args.eps or EPS, inner_iters=args.inner_iters or 8)
+    opts = P.default_opts(eps=args.eps or EPS, inner_iters=args.inner_iters or 8, include_Ls_n=INCLUDE_LS_N)
     if args.case == "batch3a":
         wls = [FI.batching_workload()]
     elif args.case == "batch3b":
