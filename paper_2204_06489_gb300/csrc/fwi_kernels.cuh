@@ -476,6 +476,18 @@ k_jacobi2_march(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
   }
 }
 
+// Asynchronous global -> shared copies of 8 bytes (cp.async, tracked per
+// thread in commit groups): a thread waits only for its own copies, so a lane
+// that reads back only what it copied needs no barrier.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Residual + restriction by column strips (R = P^T, 4x full weighting):
 //   bc[J][I] = sum_{a,b in -1..1} w_a w_b (bf - Op xf)[2J+1+b][2I+1+a],  w = (1/2, 1, 1/2).
 // A warp owns coarse columns C0 .. C0 + RM_COLS - 1 (RM_COLS = 30) and coarse
@@ -591,18 +603,6 @@ k_resid_restrict_march(LevelView<T> Lf, LevelView<T> Lc, const typename cplx<T>:
     xmA = x0A; x0A = xpA; xpA = xnA;
     xmB = x0B; x0B = xpB; xpB = xnB;
   }
-}
-
-// Asynchronous global -> shared copies of 8 bytes (cp.async, tracked per
-// thread in commit groups): a thread waits only for its own copies, so a lane
-// that reads back only what it copied needs no barrier.
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // The residual-restriction of k_resid_restrict_march (same strips, lanes and
@@ -1933,6 +1933,44 @@ __device__ __forceinline__ void multidot_body(long long n, int nv, const T *cons
   const long long stride = (long long)gridDim.x * FLAT_THREADS;
   int cnt = 0;
   long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x;
+  // float data with every vector 16-byte aligned: four elements per access,
+  // each added in element order exactly as the scalar loop would (the tail
+  // n % 4 by the scalar loop below)
+  bool vec = sizeof(T) == 4 && !(reinterpret_cast<uintptr_t>(w) & 15u);
+#pragma unroll
+  for (int v = 0; v < MD_CHUNK; ++v)
+    if (v < nv) vec = vec && !(reinterpret_cast<uintptr_t>(vp[v]) & 15u);
+  if constexpr (sizeof(T) == 4) {
+    if (vec && PM != DOT_RUNS) {
+      const long long n4 = n >> 2;
+      const float4 *w4 = reinterpret_cast<const float4 *>(w);
+      for (long long q = i; q < n4; q += stride) {
+        const float4 wv = w4[q];
+#pragma unroll
+        for (int v = 0; v < MD_CHUNK; ++v)
+          if (v < nv) {
+            const float4 av = reinterpret_cast<const float4 *>(vp[v])[q];
+            const float aa[4] = {av.x, av.y, av.z, av.w}, ww[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+            for (int e4 = 0; e4 < 4; ++e4) {
+              if (PM == DOT_FP64) {
+                tot[v] = tfma((double)aa[e4], (double)ww[e4], tot[v]);
+              } else {
+                const T a = aa[e4], wa = ww[e4];
+                const T p = tmul_rn(a, wa);
+                const T e = tfma(a, wa, -p);
+                const T t = tadd_rn(ra[v], p);
+                const T z = tsub_rn(t, ra[v]);
+                const T f = tadd_rn(tsub_rn(ra[v], tsub_rn(t, z)), tsub_rn(p, z));
+                ra[v] = t;
+                rb[v] = tadd_rn(rb[v], tadd_rn(f, e));
+              }
+            }
+          }
+      }
+      i = 4 * n4 + blockIdx.x * (long long)FLAT_THREADS + threadIdx.x;   // the tail
+    }
+  }
   if (PM == DOT_FP64 && sizeof(T) == 4) {
     for (; i < n; i += stride) {
       const double wa = (double)w[i];
@@ -2014,6 +2052,43 @@ __global__ void k_reduce_partials(int nv, int nb, const double *partial, double 
   if (threadIdx.x == 0) out[v] = accumulate ? out[v] + s : s;
 }
 
+// w[i] += sum_v c[v] vp[v][i]; float data with every vector 16-byte aligned
+// go four elements per access (the tail n % 4 by the scalar loop).
+template <typename T>
+__device__ __forceinline__ void multi_axpy_body(long long n, int nv, const T *const *vp, const T *c, T *w) {
+  const long long stride = (long long)gridDim.x * FLAT_THREADS;
+  long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x;
+  if constexpr (sizeof(T) == 4) {
+    bool vec = !(reinterpret_cast<uintptr_t>(w) & 15u);
+#pragma unroll
+    for (int v = 0; v < MD_CHUNK; ++v)
+      if (v < nv) vec = vec && !(reinterpret_cast<uintptr_t>(vp[v]) & 15u);
+    if (vec) {
+      const long long n4 = n >> 2;
+      float4 *w4 = reinterpret_cast<float4 *>(w);
+      for (long long q = i; q < n4; q += stride) {
+        float4 acc = w4[q];
+#pragma unroll
+        for (int v = 0; v < MD_CHUNK; ++v)
+          if (v < nv) {
+            const float4 a = reinterpret_cast<const float4 *>(vp[v])[q];
+            acc.x = tfma(c[v], a.x, acc.x); acc.y = tfma(c[v], a.y, acc.y);
+            acc.z = tfma(c[v], a.z, acc.z); acc.w = tfma(c[v], a.w, acc.w);
+          }
+        w4[q] = acc;
+      }
+      i = 4 * n4 + i;
+    }
+  }
+  for (; i < n; i += stride) {
+    T acc = w[i];
+#pragma unroll
+    for (int v = 0; v < MD_CHUNK; ++v)
+      if (v < nv) acc = tfma(c[v], vp[v][i], acc);
+    w[i] = acc;
+  }
+}
+
 // w += sign * sum_v coef[v] V_v  (coefficients from the device, FP64, applied
 // in the data precision T: the result is stored in T anyway)
 template <typename T>
@@ -2023,13 +2098,7 @@ k_multi_axpy(long long n, int nv, const T *const *V, const double *coef, double 
   const T *vp[MD_CHUNK];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) { c[v] = v < nv ? (T)(sign * coef[v]) : (T)0; vp[v] = v < nv ? V[v] : nullptr; }
-  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
-    T acc = w[i];
-#pragma unroll
-    for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) acc = tfma(c[v], vp[v][i], acc);
-    w[i] = acc;
-  }
+  multi_axpy_body<T>(n, nv, vp, c, w);
 }
 
 // partial[blockIdx.x] = sum x[i] y[i], FP64 across threads, fixed grid; PM as
@@ -2202,13 +2271,7 @@ k_multi_axpy_dev(long long n, const FgCtl *c, int which, int c0, const T *const 
   const T *vp[MD_CHUNK];
 #pragma unroll
   for (int v = 0; v < MD_CHUNK; ++v) { cf[v] = v < nv ? (T)(sign * coef[c0 + v]) : (T)0; vp[v] = v < nv ? V[c0 + v] : nullptr; }
-  for (long long i = blockIdx.x * (long long)FLAT_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * FLAT_THREADS) {
-    T acc = w[i];
-#pragma unroll
-    for (int v = 0; v < MD_CHUNK; ++v)
-      if (v < nv) acc = tfma(cf[v], vp[v][i], acc);
-    w[i] = acc;
-  }
+  multi_axpy_body<T>(n, nv, vp, cf, w);
 }
 
 // a[i] += b[i] for i <= j

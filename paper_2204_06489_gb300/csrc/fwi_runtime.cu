@@ -15,6 +15,7 @@
 #include <initializer_list>
 #include <cstdint>
 #include <tuple>
+#include <type_traits>
 #include <map>
 #include <memory>
 #include <string>
@@ -1069,21 +1070,23 @@ void Ctx::apply_dots(int cj, const typename cplx<T>::t *x, typename cplx<T>::t *
 template <typename T>
 void Ctx::jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cplx<T>::t *b,
                   typename cplx<T>::t *y, int level, const BFuse<T> *fz) {
+  typedef typename cplx<T>::t T2c;
   LevelView<T> L = viewM<T>(level);
   const bool timed = timer_begin<T>(level, L);
   const int grid = std::max(1, (L.n_strips2 + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
+  auto launch = [&](auto zero_t, auto bf_t, const T2c *xx, const T2c *bbv) {
+    constexpr bool Z = decltype(zero_t)::value;
+    constexpr int F = decltype(bf_t)::value;
+    if (cj) k_jacobi2_march<T, true, Z, F><<<grid, MARCH_THREADS, 0, st>>>(L, wj, xx, bbv, y, fz ? *fz : BFuse<T>{});
+    else k_jacobi2_march<T, false, Z, F><<<grid, MARCH_THREADS, 0, st>>>(L, wj, xx, bbv, y, fz ? *fz : BFuse<T>{});
+  };
   if (fz) {
     // first pass from zero with the BiCGStab update formed on the fly (b = fz->out)
     const int bf = fz->pold ? 1 : 2;
     KPROF(bf == 1 ? "k_jacobi2_march+p_update" : "k_jacobi2_march+s_update", level,
           (5.0 + (bf == 1 ? 4.0 : 3.0)) * sizeof(typename cplx<T>::t) * lv[level].field, st);
-    if (bf == 1) {
-      if (cj) k_jacobi2_march<T, true, true, 1><<<grid, MARCH_THREADS, 0, st>>>(L, wj, nullptr, nullptr, y, *fz);
-      else k_jacobi2_march<T, false, true, 1><<<grid, MARCH_THREADS, 0, st>>>(L, wj, nullptr, nullptr, y, *fz);
-    } else {
-      if (cj) k_jacobi2_march<T, true, true, 2><<<grid, MARCH_THREADS, 0, st>>>(L, wj, nullptr, nullptr, y, *fz);
-      else k_jacobi2_march<T, false, true, 2><<<grid, MARCH_THREADS, 0, st>>>(L, wj, nullptr, nullptr, y, *fz);
-    }
+    if (bf == 1) launch(std::true_type{}, std::integral_constant<int, 1>{}, nullptr, nullptr);
+    else launch(std::true_type{}, std::integral_constant<int, 2>{}, nullptr, nullptr);
     KCHECK();
     // algorithmic bytes per node: the update's operands (r, v, old p) and result,
     // then the two sweeps (b and the result, x and b and the result); the pass
@@ -1092,13 +1095,8 @@ void Ctx::jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cpl
     return;
   }
   KPROF("k_jacobi2_march", level, (x == nullptr ? 5.0 : 6.0) * sizeof(typename cplx<T>::t) * lv[level].field, st);
-  if (x == nullptr) {
-    if (cj) k_jacobi2_march<T, true, true><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
-    else k_jacobi2_march<T, false, true><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
-  } else {
-    if (cj) k_jacobi2_march<T, true, false><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
-    else k_jacobi2_march<T, false, false><<<grid, MARCH_THREADS, 0, st>>>(L, wj, x, b, y);
-  }
+  if (x == nullptr) launch(std::true_type{}, std::integral_constant<int, 0>{}, x, b);
+  else launch(std::false_type{}, std::integral_constant<int, 0>{}, x, b);
   KCHECK();
   // algorithmic bytes per node: x, b and the result of each of the two sweeps
   // (the first sweep from zero reads no x); the fused pass itself reads b
