@@ -488,6 +488,220 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// The two-sweep smoother of k_jacobi2_march (same strips, lanes, variants and
+// arithmetic) for complex64, with the input rows staged in shared memory by
+// asynchronous copies J2_DEPTH rows ahead instead of held in registers one row
+// ahead: a ring of J2_DEPTH row slots per warp with the arrays the variant
+// reads (x, b, diagonal, inverse diagonal; or r, v, old p, diagonal, inverse
+// diagonal when the BiCGStab update is formed on the fly).  Each lane copies
+// and reads back only its own two columns (no barrier); dynamic shared memory
+// of j2_stage_bytes<ZERO, BF>() per CTA.
+#define J2_DEPTH 4
+template <bool ZERO, int BF> __host__ __device__ constexpr int j2_stage_arrays() {
+  return (ZERO ? 0 : 1) + (BF == 0 ? 1 : BF == 1 ? 3 : 2) + 2;   // x?, b or (r, v[, p]), d, 1/d
+}
+template <bool ZERO, int BF> __host__ __device__ constexpr size_t j2_stage_bytes() {
+  return (size_t)(MARCH_THREADS / 32) * J2_DEPTH * j2_stage_arrays<ZERO, BF>() * 64 * sizeof(float2);
+}
+template <typename T, bool CJ, bool ZERO, int BF = 0>
+__global__ void __launch_bounds__(MARCH_THREADS, 2)
+k_jacobi2_stage(LevelView<T> L, T w, const typename cplx<T>::t *__restrict__ x,
+                const typename cplx<T>::t *__restrict__ b, typename cplx<T>::t *__restrict__ y,
+                BFuse<T> fz = BFuse<T>{}) {
+  typedef typename cplx<T>::t T2;
+  static_assert(sizeof(T) == 4, "the staged variant is for complex64");
+  static_assert(BF == 0 || ZERO, "the update is fused into a pass that starts from zero");
+  constexpr int NA = j2_stage_arrays<ZERO, BF>();
+  // array indices in a slot
+  constexpr int AX = 0, AB = ZERO ? 0 : 1;            // x (when read), then b or r
+  constexpr int AV = AB + 1, AP = AB + 2;             // v, old p (when the update is fused)
+  constexpr int AD = NA - 2, ADI = NA - 1;            // diagonal, inverse diagonal
+  extern __shared__ __align__(16) unsigned char j2_smem[];
+  const int wid = threadIdx.x >> 5;
+  T2 (*rg)[NA][64] = reinterpret_cast<T2 (*)[NA][64]>(j2_smem) + (size_t)wid * J2_DEPTH;
+  const int gw = blockIdx.x * (MARCH_THREADS / 32) + wid;
+  if (gw >= L.n_strips2) return;                      // whole warps leave together
+  const StripDev s = L.strips2[gw];
+  if (L.skip && L.skip[s.blk]) return;
+  const BlkDev bk = L.blks[s.blk];
+  const OpDev op = L.ops[bk.op];
+  const int nx = op.nx, nz = op.nz;
+  const int lane = threadIdx.x & 31;
+  const int ii[2] = {s.col0 - 2 + lane, s.col0 + 30 + lane};
+  bool in[2], mid[2], own[2];
+  in[0] = ii[0] >= 0 && ii[0] < nx;
+  in[1] = ii[1] < nx;
+  mid[0] = lane >= 1 && in[0];
+  mid[1] = lane <= 30 && in[1];
+  own[0] = lane >= 2 && in[0];
+  own[1] = lane <= 29 && in[1];
+  if (L.work && s.col0 == 0 && lane == 0)
+    atomicAdd(L.work, (unsigned long long)(s.row1 - s.row0) * nx);
+  const T2 zero = mk<T2>(0, 0);
+  const T2 *X = L.st + op.st;
+  const T2 *iXh = X + nx;
+  const T2 *Zr = iXh + nx + 1;
+  const T2 *iZh = Zr + nz;
+  T2 Xi[2], iw[2], ie[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    Xi[c] = iw[c] = ie[c] = zero;
+    if (mid[c]) {
+      Xi[c] = cmaybe_conj(X[ii[c]], CJ);
+      iw[c] = cmaybe_conj(iXh[ii[c]], CJ);
+      ie[c] = cmaybe_conj(iXh[ii[c] + 1], CJ);
+    }
+  }
+  // column pointers (row 0); column 1 is 32 elements to the right of column 0
+  const int ic = in[0] ? ii[0] : (in[1] ? ii[1] - 32 : 0);
+  const T2 *xb = ZERO ? nullptr : x + bk.off + ic;
+  const T2 *bb = BF ? nullptr : b + bk.off + ic;
+  const T2 *rb = BF ? fz.r + bk.off + ic : nullptr;
+  const T2 *vb = BF ? fz.v + bk.off + ic : nullptr;
+  const T2 *pb = BF == 1 ? fz.pold + bk.off + ic : nullptr;
+  T2 *ob = BF ? fz.out + bk.off + ic : nullptr;
+  T2 f_al = zero, f_om = zero, f_be = zero;
+  if (BF) {
+    const BiState sc = fz.S[s.blk];
+    f_al = mk<T2>(sc.alpha.x, sc.alpha.y); f_om = mk<T2>(sc.omega.x, sc.omega.y); f_be = mk<T2>(sc.beta.x, sc.beta.y);
+  }
+  T2 *yb = y + bk.off + ic;
+  const T2 *db = L.dg + op.dg + ic;
+  const T2 *dib = L.dgi + op.dg + ic;
+  const int kb = s.row0 - 1, ke = s.row1;          // x1 rows formed: kb .. ke
+  {
+    // L2 prefetch of the strip's band, as in the register version: the copies
+    // below then wait on L2, not on DRAM
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (!ZERO && in[c])
+        for (int r = max(kb - 1, 0); r < min(ke + 2, nz); ++r) prefetch_l2(xb + 32 * c + (long long)r * nx);
+      if (mid[c])
+        for (int r = max(kb, 0); r < min(ke + 1, nz); ++r) {
+          if (BF) {
+            prefetch_l2(rb + 32 * c + (long long)r * nx);
+            prefetch_l2(vb + 32 * c + (long long)r * nx);
+            if (BF == 1) prefetch_l2(pb + 32 * c + (long long)r * nx);
+          } else {
+            prefetch_l2(bb + 32 * c + (long long)r * nx);
+          }
+        }
+    }
+  }
+  auto inside = [&](int k) { return k >= 0 && k < nz; };
+  auto slot = [&](int r) { return (r - (kb - 1)) % J2_DEPTH; };
+  // copy row r into its slot: x where the column is in the grid, the
+  // right-hand side's operands and the diagonals on rows kb .. ke of the
+  // computing lanes; one commit group per row, empty ones included
+  auto stage = [&](int r) {
+    if (inside(r)) {
+      const int q = slot(r);
+      const long long o = (long long)r * nx;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        T2 *dst = &rg[q][0][32 * c + lane];
+        if (!ZERO && in[c]) cp_async8(dst + AX * 64, xb + 32 * c + o);
+        if (mid[c] && r >= kb && r <= ke) {
+          if (BF) {
+            cp_async8(dst + AB * 64, rb + 32 * c + o);
+            cp_async8(dst + AV * 64, vb + 32 * c + o);
+            if (BF == 1) cp_async8(dst + AP * 64, pb + 32 * c + o);
+          } else {
+            cp_async8(dst + AB * 64, bb + 32 * c + o);
+          }
+          cp_async8(dst + AD * 64, db + 32 * c + o);
+          cp_async8(dst + ADI * 64, dib + 32 * c + o);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  auto rdx = [&](int r, int c) -> T2 {
+    return (!ZERO && in[c] && inside(r)) ? rg[slot(r)][AX][32 * c + lane] : zero;
+  };
+  // one damped-Jacobi update at a node of column c
+  auto jac = [&](int c, T2 u, T2 uw, T2 ue, T2 un, T2 us, T2 bv, T2 d, T2 dinv, T2 Zj, T2 iZn, T2 iZs) -> T2 {
+    const T2 hx = cadd(cmul(ie[c], ue), cmul(iw[c], uw));
+    const T2 hz = cadd(cmul(iZs, us), cmul(iZn, un));
+    const T2 au = csub(csub(cmul(d, u), cmul(Zj, hx)), cmul(Xi[c], hz));
+    return cadd(u, cscale(cmul(csub(bv, au), dinv), w));
+  };
+#pragma unroll
+  for (int q = 0; q < J2_DEPTH; ++q) stage(kb - 1 + q);
+  cp_async_wait<J2_DEPTH - 2>();                      // rows kb - 1 and kb
+  T2 xm[2], x0[2], bm[2], dm[2], dim[2], ym2[2], ym1[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    xm[c] = rdx(kb - 1, c);
+    x0[c] = rdx(kb, c);
+    bm[c] = dm[c] = dim[c] = ym2[c] = ym1[c] = zero;
+  }
+  T2 Zm = zero, Z0 = inside(kb) ? cmaybe_conj(Zr[kb], CJ) : zero;
+  T2 iZm = zero;
+  T2 iZ0 = (kb >= 0 && kb <= nz) ? cmaybe_conj(iZh[kb], CJ) : zero;         // 1/Z at half row k - 1/2
+  T2 iZ1 = (kb + 1 >= 0 && kb + 1 <= nz) ? cmaybe_conj(iZh[kb + 1], CJ) : zero;   // k + 1/2
+  for (int k = kb; k <= ke; ++k) {
+    cp_async_wait<J2_DEPTH - 3>();                    // row k + 1 (and everything before it)
+    const bool rk = inside(k);
+    const int q = slot(k);
+    // x on row k + 1; the right-hand side and the diagonals of row k
+    T2 xp[2], b0[2], d0[2], di0[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      xp[c] = rdx(k + 1, c);
+      const bool okr = mid[c] && rk;
+      const int e = 32 * c + lane;
+      b0[c] = d0[c] = di0[c] = zero;
+      if (okr) {
+        if (BF == 1) b0[c] = cadd(rg[q][AB][e], cmul(f_be, csub(rg[q][AP][e], cmul(f_om, rg[q][AV][e]))));
+        else if (BF == 2) b0[c] = csub(rg[q][AB][e], cmul(f_al, rg[q][AV][e]));
+        else b0[c] = rg[q][AB][e];
+        d0[c] = cmaybe_conj(rg[q][AD][e], CJ);
+        di0[c] = cmaybe_conj(rg[q][ADI][e], CJ);
+        if (BF && own[c] && k >= s.row0 && k < s.row1) ob[32 * c + (long long)k * nx] = b0[c];
+      }
+    }
+    const bool more = k < ke;
+    const T2 Zn = (more && inside(k + 1)) ? cmaybe_conj(Zr[k + 1], CJ) : zero;
+    const T2 iZ2 = (more && k + 2 <= nz) ? cmaybe_conj(iZh[k + 2], CJ) : zero;
+    // x1 on row k
+    T2 y1[2];
+    if (ZERO) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) y1[c] = (mid[c] && rk) ? cscale(cmul(b0[c], di0[c]), w) : zero;
+    } else {
+      T2 xe[2], xw[2];
+      pair_neighbours(x0, lane, xe, xw);
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+        y1[c] = (mid[c] && rk) ? jac(c, x0[c], xw[c], xe[c], xm[c], xp[c], b0[c], d0[c], di0[c], Z0, iZ0, iZ1)
+                               : zero;
+    }
+    // y on row k - 1
+    {
+      T2 ye[2], yw[2];
+      pair_neighbours(ym1, lane, ye, yw);
+      if (k - 1 >= s.row0) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          if (own[c])
+            yb[32 * c + (long long)(k - 1) * nx] =
+                jac(c, ym1[c], yw[c], ye[c], ym2[c], y1[c], bm[c], dm[c], dim[c], Zm, iZm, iZ0);
+      }
+    }
+    stage(k - 1 + J2_DEPTH);                          // the slot of row k - 1 is free
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      xm[c] = x0[c]; x0[c] = xp[c];
+      bm[c] = b0[c]; dm[c] = d0[c]; dim[c] = di0[c];
+      ym2[c] = ym1[c]; ym1[c] = y1[c];
+    }
+    Zm = Z0; Z0 = Zn;
+    iZm = iZ0; iZ0 = iZ1; iZ1 = iZ2;
+  }
+  cp_async_wait<0>();                                 // no copy left in flight at exit
+}
+
 // Residual + restriction by column strips (R = P^T, 4x full weighting):
 //   bc[J][I] = sum_{a,b in -1..1} w_a w_b (bf - Op xf)[2J+1+b][2I+1+a],  w = (1/2, 1, 1/2).
 // A warp owns coarse columns C0 .. C0 + RM_COLS - 1 (RM_COLS = 30) and coarse

@@ -1074,11 +1074,30 @@ void Ctx::jacobi2(int cj, T wj, const typename cplx<T>::t *x, const typename cpl
   LevelView<T> L = viewM<T>(level);
   const bool timed = timer_begin<T>(level, L);
   const int grid = std::max(1, (L.n_strips2 + MARCH_THREADS / 32 - 1) / (MARCH_THREADS / 32));
+  // complex64 passes that form the BiCGStab update on the fly (three or four
+  // input streams): the input rows staged in shared memory by asynchronous
+  // copies (k_jacobi2_stage, 147 -> 99 us per level-0 launch); the other
+  // passes and complex128: the register pipeline (k_jacobi2_march), which is
+  // faster for them (85 vs 93 us at level 0, 30.5 vs 33.4 us at level 1)
   auto launch = [&](auto zero_t, auto bf_t, const T2c *xx, const T2c *bbv) {
     constexpr bool Z = decltype(zero_t)::value;
     constexpr int F = decltype(bf_t)::value;
-    if (cj) k_jacobi2_march<T, true, Z, F><<<grid, MARCH_THREADS, 0, st>>>(L, wj, xx, bbv, y, fz ? *fz : BFuse<T>{});
-    else k_jacobi2_march<T, false, Z, F><<<grid, MARCH_THREADS, 0, st>>>(L, wj, xx, bbv, y, fz ? *fz : BFuse<T>{});
+    if constexpr (sizeof(T) == 4 && F != 0) {
+      constexpr size_t sm = j2_stage_bytes<Z, F>();
+      // the dynamic shared-memory limit is raised once per device and variant
+      static std::atomic<unsigned long long> attr[2];
+      const unsigned long long bit = 1ull << (dev & 63);
+      if (!(attr[cj ? 1 : 0].load() & bit)) {
+        if (cj) CK(cudaFuncSetAttribute(k_jacobi2_stage<T, true, Z, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        else CK(cudaFuncSetAttribute(k_jacobi2_stage<T, false, Z, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr[cj ? 1 : 0].fetch_or(bit);
+      }
+      if (cj) k_jacobi2_stage<T, true, Z, F><<<grid, MARCH_THREADS, sm, st>>>(L, wj, xx, bbv, y, fz ? *fz : BFuse<T>{});
+      else k_jacobi2_stage<T, false, Z, F><<<grid, MARCH_THREADS, sm, st>>>(L, wj, xx, bbv, y, fz ? *fz : BFuse<T>{});
+    } else {
+      if (cj) k_jacobi2_march<T, true, Z, F><<<grid, MARCH_THREADS, 0, st>>>(L, wj, xx, bbv, y, fz ? *fz : BFuse<T>{});
+      else k_jacobi2_march<T, false, Z, F><<<grid, MARCH_THREADS, 0, st>>>(L, wj, xx, bbv, y, fz ? *fz : BFuse<T>{});
+    }
   };
   if (fz) {
     // first pass from zero with the BiCGStab update formed on the fly (b = fz->out)
