@@ -1784,29 +1784,61 @@ k_bicg_scalars(int n_blocks, const int *tile0, const int *tile1, const double2 *
 //  op 1: s = r - alpha v
 //  op 3: y = a (copy)            op 4: y = 0
 // (the x / r update is k_bicg_xr, fused with the dots that follow it)
-template <typename T, int OPK>
+template <typename T, int OPK, bool VEC = false>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_bicg_update(LevelView<T> L, const BiState *S, typename cplx<T>::t *y, const typename cplx<T>::t *a,
               const typename cplx<T>::t *c) {
   typedef typename cplx<T>::t T2;
+  static_assert(!VEC || sizeof(T) == 4, "the vector path is for complex64");
   const TileDev t = L.tiles[blockIdx.x];
   if (L.skip && L.skip[t.blk]) return;
   const BlkDev bk = L.blks[t.blk];
   const OpDev op = L.ops[bk.op];
-  const int j = t.row0 + (threadIdx.x >> 5);
-  if (j >= op.nz) return;
   T2 al = mk<T2>(0, 0), om = al, be = al;
   if (OPK <= 1) {
     const BiState s = S[t.blk];
     al = mk<T2>(s.alpha.x, s.alpha.y); om = mk<T2>(s.omega.x, s.omega.y); be = mk<T2>(s.beta.x, s.beta.y);
   }
-  const long long base = bk.off + (long long)j * op.nx;
-  for (int i = threadIdx.x & 31; i < op.nx; i += 32) {
-    const long long k = base + i;
-    if (OPK == 0) y[k] = cadd(a[k], cmul(be, csub(y[k], cmul(om, c[k]))));
-    else if (OPK == 1) y[k] = csub(a[k], cmul(al, c[k]));
-    else if (OPK == 3) y[k] = a[k];
-    else y[k] = mk<T2>(0, 0);
+  auto one = [&](T2 yk, T2 ak, T2 ck) -> T2 {
+    if (OPK == 0) return cadd(ak, cmul(be, csub(yk, cmul(om, ck))));
+    if (OPK == 1) return csub(ak, cmul(al, ck));
+    if (OPK == 3) return ak;
+    return mk<T2>(0, 0);
+  };
+  auto scalar = [&](long long k) {
+    const T2 yk = OPK == 0 ? y[k] : mk<T2>(0, 0);
+    const T2 ak = OPK <= 3 && OPK != 2 ? a[k] : mk<T2>(0, 0);
+    const T2 ck = OPK <= 1 ? c[k] : mk<T2>(0, 0);
+    y[k] = one(yk, ak, ck);
+  };
+  if constexpr (VEC) {
+    // complex64 with every vector 16-byte aligned: the tile's rows are one
+    // contiguous range, two nodes per float4 access (as in k_bicg_xr)
+    const int rows = min(TILE_ROWS, op.nz - t.row0);
+    if (rows <= 0) return;
+    const long long base = bk.off + (long long)t.row0 * op.nx;
+    const long long len = (long long)rows * op.nx;
+    const long long head = base & 1;
+    const long long np = (len - head) >> 1;
+    if (threadIdx.x == 0 && head) scalar(base);
+    if (threadIdx.x == 1 && ((len - head) & 1)) scalar(base + len - 1);
+    const long long k0 = base + head;
+    float4 *y4 = reinterpret_cast<float4 *>(y + k0);
+    const float4 *a4 = OPK <= 3 ? reinterpret_cast<const float4 *>(a + k0) : nullptr;
+    const float4 *c4 = OPK <= 1 ? reinterpret_cast<const float4 *>(c + k0) : nullptr;
+    for (long long p = threadIdx.x; p < np; p += TILE_THREADS) {
+      const float4 Y = OPK == 0 ? y4[p] : make_float4(0, 0, 0, 0);
+      const float4 A = OPK <= 3 ? a4[p] : make_float4(0, 0, 0, 0);
+      const float4 C = OPK <= 1 ? c4[p] : make_float4(0, 0, 0, 0);
+      const T2 r0 = one(mk<T2>(Y.x, Y.y), mk<T2>(A.x, A.y), mk<T2>(C.x, C.y));
+      const T2 r1 = one(mk<T2>(Y.z, Y.w), mk<T2>(A.z, A.w), mk<T2>(C.z, C.w));
+      y4[p] = make_float4(r0.x, r0.y, r1.x, r1.y);
+    }
+  } else {
+    const int j = t.row0 + (threadIdx.x >> 5);
+    if (j >= op.nz) return;
+    const long long base = bk.off + (long long)j * op.nx;
+    for (int i = threadIdx.x & 31; i < op.nx; i += 32) scalar(base + i);
   }
 }
 

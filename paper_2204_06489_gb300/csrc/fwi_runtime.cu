@@ -1385,10 +1385,22 @@ void Ctx::inner_solve(const typename cplx<T>::t *b, typename cplx<T>::t *x, int 
   const int sb = (B + BICG_WARPS - 1) / BICG_WARPS;
   auto upd = [&](int opk, T2 *y, const T2 *a, const T2 *c) {
     KPROF("k_bicg_update", opk, (opk == 0 ? 4.0 : opk == 1 ? 3.0 : opk == 3 ? 2.0 : 1.0) * sizeof(T2) * F0, st);
-    if (opk == 0) k_bicg_update<T, 0><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
-    else if (opk == 1) k_bicg_update<T, 1><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
-    else if (opk == 3) k_bicg_update<T, 3><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
-    else k_bicg_update<T, 4><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+    // complex64 with 16-byte aligned vectors: two nodes per access over each row tile
+    constexpr bool V4 = sizeof(T) == 4;
+    const bool vec = V4 && aligned16({y, a, c});
+    if (opk == 0) {
+      if (vec) k_bicg_update<T, 0, V4><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+      else k_bicg_update<T, 0><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+    } else if (opk == 1) {
+      if (vec) k_bicg_update<T, 1, V4><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+      else k_bicg_update<T, 1><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+    } else if (opk == 3) {
+      if (vec) k_bicg_update<T, 3, V4><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+      else k_bicg_update<T, 3><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+    } else {
+      if (vec) k_bicg_update<T, 4, V4><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+      else k_bicg_update<T, 4><<<nt, TILE_THREADS, 0, st>>>(L, w.bst.p, y, a, c);
+    }
     KCHECK();
   };
   auto scal = [&](int stage) {
