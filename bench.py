@@ -120,11 +120,18 @@ def _peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum of the level-0 smoother launches
 # per byte of the pass itself (b and the result, plus x unless it starts from
 # zero, plus r, v and the old p when it forms the p update), from the ncu
-# capture of its three variants summarised under profiles/, weighted as the
-# timed forward solves launch them (per BiCGStab iteration: one with the p
-# update, one from zero, two from x): (364.3 + 115.5 + 2 x 206.8) MB over
-# (383.2 + 153.3 + 2 x 229.9) MB.  None once the kernel changes.
-TRAFFIC_PER_FUSED_BYTE = (364.3 + 115.5 + 2 * 206.8) / (383.2 + 153.3 + 2 * 229.9)
+# captures of its three variants summarised under profiles/ (the p-update pass
+# is k_jacobi2_stage, the others k_jacobi2_march), weighted as the timed
+# forward solves launch them (per BiCGStab iteration: one with the p update,
+# one from zero, two from x): (356.9 + 115.5 + 2 x 206.8) MB over
+# (383.2 + 153.3 + 2 x 229.9) MB.  None once a kernel changes.
+TRAFFIC_PER_FUSED_BYTE = (356.9 + 115.5 + 2 * 206.8) / (383.2 + 153.3 + 2 * 229.9)
+# warp instructions of one k_coarse_cycle<float, 0, 512> launch on the
+# benchmark workload (120 blocks, levels 110x45 .. 13x5, W(2,2) to level 2),
+# smsp__inst_executed.sum of the ncu capture summarised under profiles/; the
+# kernel is latency-bound, so its roofline is the instruction issue rate of
+# the chip (152 SMs x 4 schedulers x the SM clock).  None once it changes.
+COARSE_CYCLE_WARP_INSTS = 26.98e6
 
 
 def _roofline(ms, nbytes, n, peaks, fused_bytes=None):
@@ -142,8 +149,8 @@ def _roofline(ms, nbytes, n, peaks, fused_bytes=None):
         return None
     ach = nbytes / (ms / 1e3) / 1e9
     per_launch = nbytes / n
-    out = {"kernel": "k_jacobi2_march<float> at level 0 (two fused damped-Jacobi sweeps of the "
-                     "shifted 5-point PML stencil, all blocks)",
+    out = {"kernel": "k_jacobi2_march / k_jacobi2_stage <float> at level 0 (two fused damped-Jacobi sweeps of "
+                     "the shifted 5-point PML stencil, all blocks, all three passes)",
            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
            "peak_source": src, "launches_timed": n, "avg_launch_us": ms / n * 1e3,
            "algorithmic_bytes_per_launch": per_launch,
@@ -755,6 +762,20 @@ def run_newton(args):
         if args.steps >= NEWTON_STEPS:
             kt["gap_share_of_graph_steps"] = round(1.0 - kt["kernel_ms"] / traj_ms, 4)
         extras["kernel_table"] = kt
+        # issue-rate roofline of the shared-memory coarse cycle (the largest
+        # single kernel; latency-bound, about 1 % of HBM)
+        cc = [r for r in kt["rows"] if r["kernel"].startswith("k_coarse_cycle")]
+        if cc and COARSE_CYCLE_WARP_INSTS:
+            mhz = (ck or {}).get("sm_mhz") or 2070.0
+            peak_i = 152 * 4 * mhz * 1e6 / 1e9
+            ach_i = COARSE_CYCLE_WARP_INSTS / (cc[0]["avg_us"] * 1e-6) / 1e9
+            extras["roofline_coarse_cycle"] = {
+                "kernel": "k_coarse_cycle<float> (levels 2-5 in shared memory, one CTA per block)",
+                "bound": "issue", "achieved": round(ach_i, 1), "peak": round(peak_i, 1),
+                "unit": "G warp-instructions/s", "frac": round(ach_i / peak_i, 3),
+                "avg_launch_us": cc[0]["avg_us"],
+                "accounting": "ncu warp instructions per launch (profiles/) over the live average launch time; "
+                              "peak = 152 SMs x 4 schedulers x the sampled SM clock"}
         # (c) the three forms of the Arnoldi inner products (0 FP32 runs, 1 FP64
         # products, 2 compensated Dot2), with the measured loss of orthogonality
         # of the complex64 basis (max |I - V^T V|)
