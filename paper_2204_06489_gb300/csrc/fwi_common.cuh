@@ -46,6 +46,48 @@ template <typename T2> __host__ __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
 template <typename T2, typename S> __host__ __device__ __forceinline__ T2 cscale(T2 a, S s) {
   a.x *= s; a.y *= s; return a;
 }
+// complex64 sums, differences and real scalings as one paired FP32
+// instruction each (add / sub / mul .rn.f32x2 of the Blackwell ISA; each
+// half rounds exactly like the scalar instruction) in device code.
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  unsigned long long A, B, C;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b.x), "f"(b.y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(C) : "l"(A), "l"(B));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(C));
+  return r;
+#else
+  a.x += b.x; a.y += b.y; return a;
+#endif
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  unsigned long long A, B, C;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(C) : "l"(A), "l"(B));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(C));
+  return r;
+#else
+  a.x -= b.x; a.y -= b.y; return a;
+#endif
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
+#if defined(__CUDA_ARCH__)
+  unsigned long long A, S, C;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(S) : "f"(s));
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(C) : "l"(A), "l"(S));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(C));
+  return r;
+#else
+  a.x *= s; a.y *= s; return a;
+#endif
+}
 // a / b by the textbook formula conj(b) a / |b|^2 (operands here are O(1)).
 template <typename T2> __host__ __device__ __forceinline__ T2 cdiv(T2 a, T2 b) {
   auto d = b.x * b.x + b.y * b.y;
